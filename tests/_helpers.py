@@ -1,0 +1,35 @@
+"""Shared test helpers: tiny custom problems for oracle pins and parity."""
+import numpy as np
+import torch
+
+import oracle
+import workloads
+
+F64 = torch.float64
+
+
+def tiny_workload(**kw):
+    """8x6 grid, 4 steps, 2x2x2 subdomains, overlap 1 / 1, random obs, RF B."""
+    base = dict(name="tiny", nlon=8, nlat=6, nsteps=4, P1=2, P2=2, Q=2, o_lon=1, o_lat=1,
+                o_t=1, obs_kind="random", obs_vars=(0, 1, 2), obs_count=40, obs_every=1,
+                corr_len=1.5, rf_passes=2)
+    base.update(kw)
+    return workloads.Workload(**base)
+
+
+def perturbed_state(st, seed=11, scale=0.3):
+    """A non-trivial outer-iteration state: B and the neighbour trajectories
+    are the background trajectory plus smooth-ish noise (sigma_b units)."""
+    g = torch.Generator().manual_seed(seed)
+    sb = torch.as_tensor(st.sigma_b, dtype=F64)[None, :, None, None]
+    B = st.xb_traj + scale * sb * torch.randn(st.xb_traj.shape, generator=g, dtype=F64)
+    prev = []
+    for lp in st.locals:
+        tr = lp.restrict_traj(st.xb_traj)
+        prev.append(tr + scale * sb * torch.randn(tr.shape, generator=g, dtype=F64))
+    return B, prev
+
+
+def rand_w(n, seed=3, scale=0.5):
+    g = torch.Generator().manual_seed(seed)
+    return scale * torch.randn(n, generator=g, dtype=F64)

@@ -1,0 +1,137 @@
+"""Pins of the oracle's decomposition (Sec. 3.1-3.2: DD, RO, EO, Eq. rest,
+Eq. restJ) and of the overlap term (Eqs. overl-otime)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from _helpers import tiny_workload
+
+F64 = torch.float64
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _read_golden(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append([float(t) for t in line.split()])
+    return np.array(rows)
+
+
+def test_small_config_boxes_follow_nloc_rule():
+    """Sec. 7, Eq. nlocx: nloc = n/p + 2o per side, lat and time clipped."""
+    st, inp, _ = oracle.build_setup(workloads.preset("small"))
+    boxes = sorted({(s.nx, s.ny, s.a, s.b) for s in st.dec.subs})
+    assert boxes == [(20, 10, 0, 10), (20, 10, 6, 16)]
+
+
+def test_restriction_weights_hand_derived_small_config():
+    """Golden values: RO weights 1, 1/2, 1/4, 1/8 at hand-chosen points of
+    the small config (Definition 'Restriction of a function')."""
+    st, inp, _ = oracle.build_setup(workloads.preset("small"))
+    cnt = st.dec.cover_count()
+    for n, j, i, wgt in _read_golden("small_restriction_weights.txt"):
+        assert 1.0 / cnt[int(n), int(j), int(i)] == wgt
+
+
+@pytest.mark.parametrize("name", ["small", "ragged"])
+def test_partition_of_unity(name):
+    """Eq. rest: the weights of every point and every observation sum to 1."""
+    st, inp, _ = oracle.build_setup(workloads.preset(name))
+    cnt = st.dec.cover_count()
+    assert cnt.min() >= 1
+    tot = np.zeros_like(cnt, dtype=np.float64)
+    for s in st.dec.subs:
+        tot[s.a:s.b + 1, s.j0:s.j0 + s.ny][:, :, s.cols()] += 1.0 / cnt[s.a:s.b + 1, s.j0:s.j0 + s.ny][:, :, s.cols()]
+    assert np.allclose(tot, 1.0, rtol=0, atol=1e-15)
+    per_obs = np.zeros(len(st.obs))
+    for k, m in enumerate(st.obs_members):
+        per_obs[k] = len(m) * st.obs_weight[k]
+    assert np.allclose(per_obs, 1.0, atol=1e-15)
+
+
+def test_extension_of_restrictions_is_identity():
+    """Eqs. rest / Eq_ROprop: sum_s EO[RO_s u] = u for any trajectory."""
+    st, inp, _ = oracle.build_setup(workloads.preset("ragged"))
+    X = torch.randn(st.xb_traj.shape, dtype=F64, generator=torch.Generator().manual_seed(0))
+    back = oracle.assemble(st, [lp.restrict_traj(X) for lp in st.locals])
+    assert float((back - X).abs().max()) <= 1e-15 * float(X.abs().max()) * 4
+
+
+def test_obs_term_decomposes_exactly_in_time():
+    """Eq. restJ (J = sum_s J^EO_s), time-only decomposition: with B and
+    every local initial state taken from one global trajectory X, the
+    weighted local observation terms add up to the global one."""
+    wl = tiny_workload(P1=1, P2=1, Q=3, nsteps=9, o_t=1, nlon=12, nlat=8, corr_len=0.0,
+                       obs_count=120, obs_every=1)
+    st, inp, truth = oracle.build_setup(wl)
+    X = truth
+    Jo_sum = 0.0
+    for lp in st.locals:
+        s = lp.sub
+        w = ((lp.restrict_traj(X)[0] - lp.xb_a) / torch.as_tensor(st.sigma_b, dtype=F64)[:, None, None]).reshape(-1)
+        _, _, Jo, _ = lp.J_parts(w, X, [lp2.restrict_traj(X) for lp2 in st.locals])
+        Jo_sum += float(Jo)
+    ob = st.obs
+    d = oracle.observe(wl.nlon, X, ob.level, ob.var, ob.fi, ob.fj) - ob.value
+    Jo_glob = 0.5 * float(np.sum(d * d / ob.sigma_o ** 2))
+    assert abs(Jo_sum - Jo_glob) <= 1e-12 * Jo_glob
+
+
+def test_overlap_term_closed_form_time_and_space():
+    """Overlap operator, cases 1 and 2 of Sec. 3.3: with the own trajectory
+    equal to X and every neighbour trajectory X + delta (h only), J_mu is
+    1/2 * (number of shared level-points, counted per neighbour) * delta^2 / sigma_h^2."""
+    delta = 0.5
+    for kw, count in (
+        (dict(P1=1, P2=1, Q=2, nsteps=8, o_t=2), lambda w: (2 * w.o_t + 1) * w.nlon * w.nlat),
+        # one level: lateral ghosts play no part, so x_s = X exactly
+        (dict(P1=2, P2=1, Q=1, nsteps=0, o_lon=2), lambda w: 2 * (2 * w.o_lon) * w.nlat),
+    ):
+        wl = tiny_workload(nlon=16, nlat=6, corr_len=0.0, **kw)
+        st, inp, truth = oracle.build_setup(wl)
+        X = truth
+        prev = [lp.restrict_traj(X) for lp in st.locals]
+        for p in prev:
+            p[:, 0] += delta
+        for lp in st.locals:
+            s = lp.sub
+            w = ((lp.restrict_traj(X)[0] - lp.xb_a) / torch.as_tensor(st.sigma_b, dtype=F64)[:, None, None]).reshape(-1)
+            _, _, _, Jm = lp.J_parts(w, X, prev)
+            expect = 0.5 * count(wl) * delta ** 2 / st.sigma_b[0] ** 2
+            assert abs(float(Jm) - expect) <= 1e-9 * expect
+
+
+def test_overlap_pairs_match_cover_count():
+    """Invariant: the (level, point, neighbour) triples of a subdomain's
+    overlap term number sum over its window x box of (cover count - 1)."""
+    st, inp, _ = oracle.build_setup(workloads.preset("ragged"))
+    cnt = st.dec.cover_count()
+    for lp in st.locals:
+        s = lp.sub
+        n_pairs = sum(len(ov.levels) * len(ov.rows_s) for ov in lp.overlaps)
+        c = cnt[s.a:s.b + 1, s.j0:s.j0 + s.ny][:, :, s.cols()]
+        assert n_pairs == int((c - 1).sum())
+
+
+def test_table3_problem_sizes():
+    """Golden values of Table 3: the spatial problem size 3 * nloc^2 * QP for
+    nloc = 32 and QP = 2 .. 64 (the state count of QP local problems with
+    32 x 32 extended boxes, Eqs. Eq-r, nlocx)."""
+    for qp, printed in _read_golden("table3_problem_size.txt"):
+        qp = int(qp)
+        # QP spatial subdomains of 32 x 32 extended points each (o = 4, core 24)
+        P1 = {2: 2, 4: 2, 8: 4, 16: 4, 32: 8, 64: 8}[qp]
+        P2 = qp // P1
+        dec = oracle.Decomposition.make(24 * P1, 24 * P2 + 8, 1, P1, P2, 1,
+                                        [24 * k for k in range(P1 + 1)],
+                                        [4 + 24 * k for k in range(P2)] + [24 * P2 + 8] if P2 > 1 else [0, 24 * P2 + 8],
+                                        [0, 1], 4, 4, 0)
+        size = sum(3 * s.nx * s.ny for s in dec.subs)
+        assert size == 3 * 32 * 32 * qp
+        assert abs(size - printed) <= 0.05 * printed
