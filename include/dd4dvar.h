@@ -1,0 +1,276 @@
+/*
+ * dd4dvar.h -- C interface of the GB300 (sm_103a) library for space-time
+ * domain-decomposed strong-constraint 4D-Var (DD-4DVar) on the shallow-water
+ * equations on the sphere.
+ *
+ * Method: D'Amore, Constantinescu & Carracciuolo, "A scalable space-time
+ * domain decomposition approach for solving large-scale nonlinear regularized
+ * inverse ill-posed problems in 4D variational data assimilation"
+ * (arXiv 2205.06649).  Section, equation and algorithm numbers below refer to
+ * that paper.  The calls follow Algorithm 1's signature
+ * DD-4DVar(in: M, u0b, {R_k}, B, H, v, Delta_M, Omega_K; out: u^DA):
+ * set the model and grid, the background, B and the observations (with R),
+ * set the decomposition and overlap, then evaluate the local functionals and
+ * gradients or run the outer loop.
+ *
+ * Conventions (all calls)
+ *   - Return value: dd4dv_status.  0 = success, negative = error (nothing
+ *     of the requested output is valid), DD4DV_NOTCONV = finished without
+ *     meeting the stopping test (outputs valid).  dd4dv_last_error() gives a
+ *     message.  No C++ exception crosses this interface.
+ *   - Ownership: the library copies every input at the call; the caller owns
+ *     every buffer it passes and keeps ownership; outputs are written into
+ *     caller buffers.  The context owns its device memory (cudaMalloc) and
+ *     frees it in dd4dv_destroy.
+ *   - Pointers: "host" arguments are ordinary host memory.  Where an entry
+ *     point takes `device_ptrs`, 1 means every array argument of that call
+ *     is CUDA device memory of the current device, read and written in
+ *     stream order on the context's stream, and the call returns once the
+ *     work is enqueued; 0 means host memory (the call copies in, runs, copies
+ *     out and synchronises before it returns).
+ *   - State layout: a state is [3][nlat][nlon] doubles, variables (h, u, v)
+ *     in that order, row = latitude index j (south to north), column =
+ *     longitude index i (eastward).  Trajectories are [nsteps+1][3][nlat][nlon].
+ *   - Call order: create -> set_background, set_background_error,
+ *     set_observations (any order) -> set_decomposition -> eval/run...
+ *     A call made too early returns DD4DV_ESTATE.  Any set_* call after
+ *     set_decomposition invalidates it (call set_decomposition again).
+ *   - Threading: a context may be used by one host thread at a time.
+ */
+#ifndef DD4DVAR_H
+#define DD4DVAR_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd4dv_ctx dd4dv_ctx;      /* opaque, library-owned */
+
+typedef enum {
+  DD4DV_OK = 0,
+  DD4DV_EINVAL = -1,       /* bad argument (size, range, NULL, layout)     */
+  DD4DV_ENOMEM = -2,       /* device or pinned host allocation failed      */
+  DD4DV_ECUDA = -3,        /* CUDA runtime error (message has the details) */
+  DD4DV_ESTATE = -4,       /* call made before its prerequisites           */
+  DD4DV_ETIMEOUT = -5,     /* a bounded device wait ran out                */
+  DD4DV_ENONFINITE = -6,   /* NaN or Inf in an input                       */
+  DD4DV_NOTCONV = 1        /* warning: stopping test not met, outputs valid */
+} dd4dv_status;
+
+/*
+ * Model and grid (Sec. 7, Eqs. EquU-EquH; Definition "DA problem setup",
+ * Sec. 2).  Regular lon-lat grid of nlon x nlat cell centres, periodic in
+ * longitude, reflecting walls at lat_min_deg and lat_max_deg (the cell faces).
+ * Centred second-order differences, flux-form continuity, SSP-RK3 steps of
+ * dt seconds, nsteps steps in the assimilation window (levels 0..nsteps).
+ * precision: 0 = FP64 state; 1 = FP32 state (h stored as h - h_ref) with
+ * FP64 control, gradients, J and all reductions.
+ */
+typedef struct {
+  int nlon, nlat;
+  double lat_min_deg, lat_max_deg;
+  double radius, gravity, omega;
+  double dt;
+  int nsteps;
+  int precision;
+  double h_ref;            /* FP32 path: reference depth removed from h   */
+} dd4dv_model;
+
+/*
+ * Space-time decomposition DD(Delta x Omega) (Sec. 3.1, Eqs. DDOmega-decomall;
+ * sizes per Sec. 7 Eq. nlocx: core block extended by o on each side).
+ * P1 lon blocks x P2 lat blocks x Q time windows.  Cuts are core-block
+ * boundaries (P1+1, P2+1, Q+1 increasing values from 0 to nlon / nlat /
+ * nsteps), or NULL for equal blocks.  Requirements: every core lon/lat block
+ * >= 2*o and >= 2 points, every core window > 2*o_t steps, o >= 1 where
+ * the axis is split, extended lon box < nlon.  Subdomain numbering:
+ * s = (q * P2 + p2) * P1 + p1.
+ * mu, lambda: weights of the overlap and observation terms (Eq.
+ * eq:cost:parallel1).  weight_obs = 1 weights each observation by
+ * 1/(number of subdomains containing it), the restriction weights of
+ * Definition "Restriction of a function"; 0 gives weight 1.
+ * cluster: CTAs per subdomain in the sweep kernels (0 = choose automatically).
+ * ckpt_k: store the trajectory every ckpt_k steps and recompute segments in
+ * the adjoint (0 = store every level).
+ */
+typedef struct {
+  int P1, P2, Q;
+  const int* lon_cuts;
+  const int* lat_cuts;
+  const int* t_cuts;
+  int o_lon, o_lat, o_t;
+  double mu, lambda;
+  int weight_obs;
+  int cluster;
+  int ckpt_k;
+} dd4dv_decomp;
+
+/*
+ * Local minimiser settings (Algorithm 2/3 with L-BFGS, Remark after
+ * Algorithm 5) and outer loop (Algorithm 1).
+ */
+typedef struct {
+  int lbfgs_m;             /* memory pairs (5)                             */
+  int max_local_iters;     /* L-BFGS iterations per outer iteration (20)   */
+  int max_trials;          /* Armijo trials per iteration (20)             */
+  int max_outer;           /* outer iterations (10)                        */
+  double eps_outer;        /* stop when max_s ||w_s^l - w_s^(l-1)||_inf < eps */
+  double gtol_rel;         /* local stop when ||g|| / ||g_0|| < gtol       */
+  double c1;               /* Armijo constant (1e-4)                       */
+} dd4dv_solver;
+
+typedef struct {
+  int outer_iters;         /* outer iterations done                        */
+  long long evals;         /* batched J/grad evaluations                   */
+  long long sub_evals;     /* subdomain evaluations (active subdomains)    */
+  long long pt_steps;      /* grid-point steps, forward+adjoint, all evals */
+  double dw_inf;           /* last max_s ||w^l - w^(l-1)||_inf             */
+  double J_sum;            /* sum over subdomains of the final local J     */
+  double gnorm_rel_max;    /* max_s ||g|| / ||g_0|| at the end             */
+  int n_linesearch_fail;   /* local solves stopped by a failed line search */
+} dd4dv_stats;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t to
+ * order all work on (NULL = the context creates its own).  Errors: EINVAL
+ * (sizes, dt <= 0, nsteps < 0, lat range), ECUDA, ENOMEM. */
+dd4dv_status dd4dv_create(const dd4dv_model* model, void* cuda_stream, dd4dv_ctx** out);
+
+/* Free the context and all its device memory.  NULL is accepted. */
+dd4dv_status dd4dv_destroy(dd4dv_ctx* ctx);
+
+/* Background initial state u_0^b (Definition "DA problem setup"): host array
+ * [3][nlat][nlon].  Runs the background forecast u^b = M(u_0^b) over the
+ * window on the device (Algorithm 1, background step).  ENONFINITE on NaN/Inf. */
+dd4dv_status dd4dv_set_background(dd4dv_ctx* ctx, const double* xb0);
+
+/* Background-error covariance B = V V^T (Sec. 4, Eq. EqV).  sigma_b[3]:
+ * standard deviations of (h, u, v), > 0.  corr_len_cells = 0: diagonal B;
+ * > 0: V = diag(sigma_b) L_lat L_lon with L a recursive filter of rf_passes
+ * (1..8) forward/backward passes matched to a Gaussian of that length. */
+dd4dv_status dd4dv_set_background_error(dd4dv_ctx* ctx, const double sigma_b[3],
+                                        double corr_len_cells, int rf_passes);
+
+/* Observations v and diagonal R_k (Definition "DA problem setup"; the
+ * observation term of Eq. min3sec).  n records, host arrays: level in
+ * [0, nsteps], var in {0,1,2} (h,u,v), fractional grid indices
+ * fi in [0, nlon), fj in [0, nlat-1], value, sigma_o > 0.  H is bilinear
+ * interpolation in index space, periodic in longitude. */
+dd4dv_status dd4dv_set_observations(dd4dv_ctx* ctx, long long n, const int* level,
+                                    const int* var, const double* fi, const double* fj,
+                                    const double* value, const double* sigma_o);
+
+/* Set the space-time decomposition and overlap (see dd4dv_decomp); builds
+ * all device tables, puts the exchange state at l = 0 (boundary trajectory =
+ * background trajectory, neighbour trajectories = background) and sets every
+ * local control to 0. */
+dd4dv_status dd4dv_set_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp* dec);
+
+/* Number of subdomains P1*P2*Q. */
+dd4dv_status dd4dv_num_subdomains(const dd4dv_ctx* ctx, int* n);
+
+/* Packed control layout.  offsets[n+1]: start of each subdomain's control
+ * w_s (3*ny*nx doubles, layout [3][ny][nx]) in the packed vector, offsets[n]
+ * = total.  boxes[6*n] (may be NULL): i0, nx, j0, ny, a, b per subdomain
+ * (first global lon column, width, first lat row, height, window levels). */
+dd4dv_status dd4dv_control_layout(const dd4dv_ctx* ctx, long long* offsets, int* boxes);
+
+/* Evaluate every local functional J_s(w_s) (Sec. 3.3, Eq. eq:cost:parallel1
+ * with halves of squared norms) and, when grad_all != NULL, its gradient
+ * with respect to w_s (discrete adjoint, Algorithm 6 ADJ), with the current
+ * boundary trajectory and neighbour data held fixed.
+ *   w_all[total], grad_all[total]: packed controls (dd4dv_control_layout);
+ *   J_all[n]; parts (may be NULL) [3*n]: J_b, J_o, J_mu per subdomain with
+ *   J_s = J_b + lambda J_o + mu J_mu.
+ * device_ptrs as in the conventions.  One batched launch per sweep covers
+ * all subdomains. */
+dd4dv_status dd4dv_eval(dd4dv_ctx* ctx, const double* w_all, double* J_all, double* grad_all,
+                        double* parts, int device_ptrs);
+
+/* Split evaluation for reverse-mode frameworks: dd4dv_eval_forward computes
+ * J (and parts) and keeps what the adjoint needs; dd4dv_eval_backward then
+ * writes grad_all = scale[s] * dJ_s/dw_s for that same w (scale: n doubles,
+ * NULL = all ones).  ESTATE if no forward is pending. */
+dd4dv_status dd4dv_eval_forward(dd4dv_ctx* ctx, const double* w_all, double* J_all,
+                                double* parts, int device_ptrs);
+dd4dv_status dd4dv_eval_backward(dd4dv_ctx* ctx, const double* scale, double* grad_all,
+                                 int device_ptrs);
+
+/* Tangent-linear model (Algorithm 6, TLM) of the map w -> local trajectory,
+ * for every subdomain at once: dx_all = (d x_s / d w_s) dw_s.  dx_all is the
+ * packed trajectory layout (dd4dv_traj_layout), FP64, full h. */
+dd4dv_status dd4dv_tlm(dd4dv_ctx* ctx, const double* w_all, const double* dw_all,
+                       double* dx_all, int device_ptrs);
+
+/* Adjoint of the same map (Eq. Eq_propAdj): dw_all = (d x_s / d w_s)^T y_all
+ * for a packed trajectory-shaped y_all, every subdomain at once. */
+dd4dv_status dd4dv_adjoint(dd4dv_ctx* ctx, const double* w_all, const double* y_all,
+                           double* dw_all, int device_ptrs);
+
+/* Packed trajectory layout: offsets[n+1] of each subdomain's trajectory
+ * [b-a+1][3][ny][nx] (doubles) in a packed vector; offsets[n] = total. */
+dd4dv_status dd4dv_traj_layout(const dd4dv_ctx* ctx, long long* offsets);
+
+/* Local trajectories at w_all (forward model only), packed layout, FP64, full h. */
+dd4dv_status dd4dv_trajectories(dd4dv_ctx* ctx, const double* w_all, double* traj_all,
+                                int device_ptrs);
+
+/* Exchange step of Algorithm 1 for given local controls: run every local
+ * model at w_all, record the local trajectories as the neighbour data of the
+ * next evaluations and assemble the boundary trajectory as their
+ * partition-of-unity sum (Eq. rest). */
+dd4dv_status dd4dv_exchange(dd4dv_ctx* ctx, const double* w_all, int device_ptrs);
+
+/* Return the exchange state to l = 0 (background everywhere). */
+dd4dv_status dd4dv_reset_exchange(dd4dv_ctx* ctx);
+
+/* The current assembled (boundary) trajectory [nsteps+1][3][nlat][nlon]. */
+dd4dv_status dd4dv_boundary_trajectory(dd4dv_ctx* ctx, double* traj, int device_ptrs);
+
+/* Global model run (Sec. 7 model, whole sphere) from x0 [3][nlat][nlon];
+ * traj [nsteps+1][3][nlat][nlon], FP64 on the device. */
+dd4dv_status dd4dv_forward(dd4dv_ctx* ctx, const double* x0, double* traj, int device_ptrs);
+
+/* Observation operator H (bilinear, as in dd4dv_set_observations) applied to
+ * a global trajectory traj [nsteps+1][3][nlat][nlon]: out[k] = H_k traj. */
+dd4dv_status dd4dv_observe(dd4dv_ctx* ctx, const double* traj, long long n, const int* level,
+                           const int* var, const double* fi, const double* fj, double* out,
+                           int device_ptrs);
+
+/* One outer iteration of Algorithm 1: batched local L-BFGS on every
+ * subdomain from its current control, then the Exchange.  stats may be NULL;
+ * otherwise its counters are incremented (zero it before the first call). */
+dd4dv_status dd4dv_outer_step(dd4dv_ctx* ctx, const dd4dv_solver* solver, dd4dv_stats* stats);
+
+/* Algorithm 1: outer iterations until max_s ||w^l - w^(l-1)||_inf < eps_outer
+ * or max_outer, then the Gather: xa0 [3][nlat][nlon] (host, may be NULL) is
+ * the analysis at t0 = the partition-of-unity sum of the first window's
+ * local states.  Starts from the context's current controls and exchange
+ * state.  Returns DD4DV_NOTCONV if max_outer was reached. */
+dd4dv_status dd4dv_run(dd4dv_ctx* ctx, const dd4dv_solver* solver, double* xa0,
+                       dd4dv_stats* stats);
+
+/* Current analysis at t0 (boundary trajectory level 0), [3][nlat][nlon]. */
+dd4dv_status dd4dv_analysis(dd4dv_ctx* ctx, double* xa0, int device_ptrs);
+
+/* Current packed controls (copy out) / replace them (copy in). */
+dd4dv_status dd4dv_get_controls(dd4dv_ctx* ctx, double* w_all, int device_ptrs);
+dd4dv_status dd4dv_set_controls(dd4dv_ctx* ctx, const double* w_all, int device_ptrs);
+
+/* Subdomain pt-steps of one evaluation: sum_s nx_s ny_s (b_s - a_s). */
+dd4dv_status dd4dv_pt_steps(const dd4dv_ctx* ctx, long long* n);
+
+/* Number of this library's kernel launches on the context since it was
+ * created (cumulative; take differences around a region to count it). */
+dd4dv_status dd4dv_launch_count(const dd4dv_ctx* ctx, long long* n);
+
+/* The cluster size (CTAs per subdomain) the sweeps use. */
+dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* ctx, int* n);
+
+/* Message of the last error on this context (library-owned, valid until the
+ * next call on the context); ctx == NULL gives the last create() error. */
+const char* dd4dv_last_error(const dd4dv_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD4DVAR_H */

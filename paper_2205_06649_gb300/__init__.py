@@ -1,0 +1,314 @@
+"""GB300-native space-time domain-decomposed 4D-Var (DD-4DVar) hot path.
+
+Python binding of the C ABI in include/dd4dvar.h: one ``Context`` object
+wraps one ``dd4dv_ctx``; its methods carry the C names without the
+``dd4dv_`` prefix and only marshal arguments (numpy arrays -> host pointers,
+CUDA torch tensors -> device pointers).  Every step of the computation runs in
+the library's CUDA kernels; there is no CPU fallback.
+
+Method: D'Amore, Constantinescu & Carracciuolo, arXiv 2205.06649 (Alg. 1,
+local functional Eq. eq:cost:parallel1, shallow-water model of Sec. 7).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _abi
+
+__all__ = ["Context", "DD4DVError", "lib", "solver_defaults"]
+
+lib = _abi.load()
+
+
+class DD4DVError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_abi.STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+def _ptr(x, dtype, device: bool):
+    """Data pointer of a contiguous array of the given dtype (numpy for host,
+    torch CUDA tensor for device)."""
+    if x is None:
+        return None
+    if device:
+        if not _is_torch_cuda(x):
+            raise TypeError("device call needs CUDA torch tensors")
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        want = {np.float64: "torch.float64", np.int32: "torch.int32"}[dtype]
+        if str(x.dtype) != want:
+            raise TypeError(f"expected {want}, got {x.dtype}")
+        return C.c_void_p(x.data_ptr())
+    if not isinstance(x, np.ndarray) or x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"expected a C-contiguous numpy array of {np.dtype(dtype)}")
+    return C.c_void_p(x.ctypes.data)
+
+
+def solver_defaults(**kw) -> _abi.dd4dv_solver:
+    s = _abi.dd4dv_solver(lbfgs_m=5, max_local_iters=20, max_trials=20, max_outer=10,
+                          eps_outer=1e-6, gtol_rel=1e-6, c1=1e-4)
+    for k, v in kw.items():
+        setattr(s, k, v)
+    return s
+
+
+class Context:
+    """One DD-4DVar problem on the current CUDA device (dd4dv_ctx)."""
+
+    def __init__(self, nlon: int, nlat: int, dt: float, nsteps: int, precision: int = 0,
+                 lat_min_deg: float = -80.0, lat_max_deg: float = 80.0, radius: float = 6.371e6,
+                 gravity: float = 9.81, omega: float = 7.292e-5, h_ref: float = 4000.0,
+                 stream: Optional[int] = None):
+        self.model = _abi.dd4dv_model(nlon, nlat, lat_min_deg, lat_max_deg, radius, gravity, omega,
+                                      dt, nsteps, precision, h_ref)
+        h = C.c_void_p()
+        st = lib.dd4dv_create(C.byref(self.model), C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != 0:
+            raise DD4DVError(st, lib.dd4dv_last_error(None).decode())
+        self._h = h
+        self.nlon, self.nlat, self.nsteps = nlon, nlat, nsteps
+        self.n_sub = 0
+
+    # ---- lifetime ----
+    def destroy(self):
+        if getattr(self, "_h", None):
+            lib.dd4dv_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+    def _check(self, st: int, allow_notconv: bool = False) -> int:
+        if st < 0 or (st > 0 and not allow_notconv):
+            raise DD4DVError(st, lib.dd4dv_last_error(self._h).decode())
+        return st
+
+    def last_error(self) -> str:
+        return lib.dd4dv_last_error(self._h).decode()
+
+    # ---- setup (Alg. 1 inputs) ----
+    def set_background(self, xb0: np.ndarray):
+        xb0 = np.ascontiguousarray(xb0, dtype=np.float64)
+        self._check(lib.dd4dv_set_background(self._h, _ptr(xb0, np.float64, False)))
+
+    def set_background_error(self, sigma_b: Sequence[float], corr_len: float = 0.0, rf_passes: int = 4):
+        sb = np.ascontiguousarray(sigma_b, dtype=np.float64)
+        self._check(lib.dd4dv_set_background_error(self._h, _ptr(sb, np.float64, False), corr_len, rf_passes))
+
+    def set_observations(self, level, var, fi, fj, value, sigma_o):
+        lv = np.ascontiguousarray(level, dtype=np.int32)
+        vr = np.ascontiguousarray(var, dtype=np.int32)
+        a = [np.ascontiguousarray(x, dtype=np.float64) for x in (fi, fj, value, sigma_o)]
+        self._check(lib.dd4dv_set_observations(self._h, len(lv), _ptr(lv, np.int32, False),
+                                               _ptr(vr, np.int32, False),
+                                               *[_ptr(x, np.float64, False) for x in a]))
+
+    def set_decomposition(self, P1, P2, Q, o_lon, o_lat, o_t, lon_cuts=None, lat_cuts=None,
+                          t_cuts=None, mu=1.0, lam=1.0, weight_obs=1, cluster=0, ckpt_k=0):
+        keep = []
+
+        def cuts(c):
+            if c is None:
+                return None
+            arr = np.ascontiguousarray(c, dtype=np.int32)
+            keep.append(arr)
+            return arr.ctypes.data_as(_abi.c_int_p)
+        d = _abi.dd4dv_decomp(P1, P2, Q, cuts(lon_cuts), cuts(lat_cuts), cuts(t_cuts), o_lon, o_lat,
+                              o_t, mu, lam, weight_obs, cluster, ckpt_k)
+        self._check(lib.dd4dv_set_decomposition(self._h, C.byref(d)))
+        n = C.c_int()
+        self._check(lib.dd4dv_num_subdomains(self._h, C.byref(n)))
+        self.n_sub = n.value
+        self.offsets = np.zeros(self.n_sub + 1, dtype=np.int64)
+        self.boxes = np.zeros((self.n_sub, 6), dtype=np.int32)
+        self._check(lib.dd4dv_control_layout(self._h, C.c_void_p(self.offsets.ctypes.data),
+                                             C.c_void_p(self.boxes.ctypes.data)))
+        self.traj_offsets = np.zeros(self.n_sub + 1, dtype=np.int64)
+        self._check(lib.dd4dv_traj_layout(self._h, C.c_void_p(self.traj_offsets.ctypes.data)))
+        self.ctrl_total = int(self.offsets[-1])
+        self.traj_total = int(self.traj_offsets[-1])
+
+    # ---- queries ----
+    def cluster_size(self) -> int:
+        n = C.c_int()
+        self._check(lib.dd4dv_cluster_size(self._h, C.byref(n)))
+        return n.value
+
+    def pt_steps(self) -> int:
+        n = C.c_longlong()
+        self._check(lib.dd4dv_pt_steps(self._h, C.byref(n)))
+        return n.value
+
+    def launch_count(self) -> int:
+        n = C.c_longlong()
+        self._check(lib.dd4dv_launch_count(self._h, C.byref(n)))
+        return n.value
+
+    # ---- evaluation (host numpy or device torch) ----
+    def eval(self, w, grad: bool = True, parts: bool = False):
+        dev = _is_torch_cuda(w)
+        if dev:
+            import torch
+            J = torch.empty(self.n_sub, dtype=torch.float64, device=w.device)
+            g = torch.empty_like(w) if grad else None
+            P = torch.empty(3 * self.n_sub, dtype=torch.float64, device=w.device) if parts else None
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            J = np.zeros(self.n_sub)
+            g = np.zeros(self.ctrl_total) if grad else None
+            P = np.zeros(3 * self.n_sub) if parts else None
+        self._check(lib.dd4dv_eval(self._h, _ptr(w, np.float64, dev), _ptr(J, np.float64, dev),
+                                   _ptr(g, np.float64, dev), _ptr(P, np.float64, dev), int(dev)))
+        out = [J]
+        if grad:
+            out.append(g)
+        if parts:
+            out.append(P.reshape(self.n_sub, 3))
+        return tuple(out) if len(out) > 1 else J
+
+    def eval_forward(self, w):
+        dev = _is_torch_cuda(w)
+        if dev:
+            import torch
+            J = torch.empty(self.n_sub, dtype=torch.float64, device=w.device)
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            J = np.zeros(self.n_sub)
+        self._check(lib.dd4dv_eval_forward(self._h, _ptr(w, np.float64, dev), _ptr(J, np.float64, dev),
+                                           None, int(dev)))
+        return J
+
+    def eval_backward(self, scale=None, like=None):
+        dev = _is_torch_cuda(like) if like is not None else _is_torch_cuda(scale)
+        if dev:
+            import torch
+            g = torch.empty(self.ctrl_total, dtype=torch.float64, device=(like if like is not None else scale).device)
+        else:
+            g = np.zeros(self.ctrl_total)
+            if scale is not None:
+                scale = np.ascontiguousarray(scale, dtype=np.float64)
+        self._check(lib.dd4dv_eval_backward(self._h, _ptr(scale, np.float64, dev), _ptr(g, np.float64, dev),
+                                            int(dev)))
+        return g
+
+    def tlm(self, w, dw):
+        dev = _is_torch_cuda(w)
+        if dev:
+            import torch
+            out = torch.empty(self.traj_total, dtype=torch.float64, device=w.device)
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            dw = np.ascontiguousarray(dw, dtype=np.float64)
+            out = np.zeros(self.traj_total)
+        self._check(lib.dd4dv_tlm(self._h, _ptr(w, np.float64, dev), _ptr(dw, np.float64, dev),
+                                  _ptr(out, np.float64, dev), int(dev)))
+        return out
+
+    def adjoint(self, w, y):
+        dev = _is_torch_cuda(w)
+        if dev:
+            import torch
+            out = torch.empty(self.ctrl_total, dtype=torch.float64, device=w.device)
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            y = np.ascontiguousarray(y, dtype=np.float64)
+            out = np.zeros(self.ctrl_total)
+        self._check(lib.dd4dv_adjoint(self._h, _ptr(w, np.float64, dev), _ptr(y, np.float64, dev),
+                                      _ptr(out, np.float64, dev), int(dev)))
+        return out
+
+    def trajectories(self, w):
+        dev = _is_torch_cuda(w)
+        if dev:
+            import torch
+            out = torch.empty(self.traj_total, dtype=torch.float64, device=w.device)
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            out = np.zeros(self.traj_total)
+        self._check(lib.dd4dv_trajectories(self._h, _ptr(w, np.float64, dev), _ptr(out, np.float64, dev),
+                                           int(dev)))
+        return out
+
+    def exchange(self, w):
+        dev = _is_torch_cuda(w)
+        if not dev:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+        self._check(lib.dd4dv_exchange(self._h, _ptr(w, np.float64, dev), int(dev)))
+
+    def reset_exchange(self):
+        self._check(lib.dd4dv_reset_exchange(self._h))
+
+    def boundary_trajectory(self) -> np.ndarray:
+        out = np.zeros((self.nsteps + 1, 3, self.nlat, self.nlon))
+        self._check(lib.dd4dv_boundary_trajectory(self._h, C.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def analysis(self) -> np.ndarray:
+        out = np.zeros((3, self.nlat, self.nlon))
+        self._check(lib.dd4dv_analysis(self._h, C.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def forward(self, x0) -> np.ndarray:
+        x0 = np.ascontiguousarray(x0, dtype=np.float64)
+        out = np.zeros((self.nsteps + 1, 3, self.nlat, self.nlon))
+        self._check(lib.dd4dv_forward(self._h, C.c_void_p(x0.ctypes.data), C.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def observe(self, traj, level, var, fi, fj) -> np.ndarray:
+        traj = np.ascontiguousarray(traj, dtype=np.float64)
+        lv = np.ascontiguousarray(level, dtype=np.int32)
+        vr = np.ascontiguousarray(var, dtype=np.int32)
+        fi = np.ascontiguousarray(fi, dtype=np.float64)
+        fj = np.ascontiguousarray(fj, dtype=np.float64)
+        out = np.zeros(len(lv))
+        self._check(lib.dd4dv_observe(self._h, C.c_void_p(traj.ctypes.data), len(lv),
+                                      C.c_void_p(lv.ctypes.data), C.c_void_p(vr.ctypes.data),
+                                      C.c_void_p(fi.ctypes.data), C.c_void_p(fj.ctypes.data),
+                                      C.c_void_p(out.ctypes.data), 0))
+        return out
+
+    # ---- outer loop (Alg. 1) ----
+    def outer_step(self, solver=None, stats=None):
+        solver = solver or solver_defaults()
+        stats = stats if stats is not None else _abi.dd4dv_stats()
+        self._check(lib.dd4dv_outer_step(self._h, C.byref(solver), C.byref(stats)))
+        return stats
+
+    def run(self, solver=None):
+        solver = solver or solver_defaults()
+        stats = _abi.dd4dv_stats()
+        xa = np.zeros((3, self.nlat, self.nlon))
+        st = self._check(lib.dd4dv_run(self._h, C.byref(solver), C.c_void_p(xa.ctypes.data), C.byref(stats)),
+                         allow_notconv=True)
+        return xa, stats, st
+
+    def get_controls(self) -> np.ndarray:
+        w = np.zeros(self.ctrl_total)
+        self._check(lib.dd4dv_get_controls(self._h, C.c_void_p(w.ctypes.data), 0))
+        return w
+
+    def set_controls(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        self._check(lib.dd4dv_set_controls(self._h, C.c_void_p(w.ctypes.data), 0))
+
+    # ---- packed-layout helpers ----
+    def split_controls(self, w) -> list:
+        return [w[self.offsets[s]:self.offsets[s + 1]] for s in range(self.n_sub)]
+
+    def split_traj(self, x) -> list:
+        out = []
+        for s in range(self.n_sub):
+            i0, nx, j0, ny, a, b = self.boxes[s]
+            out.append(x[self.traj_offsets[s]:self.traj_offsets[s + 1]].reshape(b - a + 1, 3, ny, nx))
+        return out

@@ -1,0 +1,1455 @@
+// C ABI of the DD-4DVar GB300 library (include/dd4dvar.h): context, argument
+// checks, decomposition tables, observation preprocessing and the host-side
+// orchestration of the device kernels (sweep.cu, aux.cu).  Every numerical
+// step runs in this library's CUDA kernels; the host only validates inputs,
+// builds index tables and enqueues work.
+#include "dd4dvar.h"
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+using namespace dd4dv;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Fail {
+  dd4dv_status st;
+};
+
+}  // namespace
+
+struct dd4dv_ctx {
+  dd4dv_model m{};
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  std::string err;
+  long long launches = 0;
+
+  // grid
+  std::vector<RowConst> rows_h;
+  RowConst* rows_d = nullptr;
+  double Bth = 0, gBth = 0;
+  size_t gstate = 0;          // 3*nlat*nlon
+  size_t gtraj = 0;           // (nsteps+1)*gstate
+
+  bool has_bg = false, has_berr = false, has_obs = false, has_dec = false;
+  double* xb_traj = nullptr;  // global background trajectory (FP64)
+  double* gscratch = nullptr; // 3 global states for the global model
+  double* gtraj_io = nullptr; // global trajectory staging (FP64)
+
+  double sigma_b[3] = {1, 1, 1};
+  double corr_len = 0;
+  int rf_passes = 4;
+  double rf_alpha = 0, rf_c = 1;
+  double* sigma_d = nullptr;
+
+  std::vector<int> ob_level, ob_var;
+  std::vector<double> ob_fi, ob_fj, ob_val, ob_so;
+
+  // decomposition
+  dd4dv_decomp dec{};
+  std::vector<int> lon_cuts, lat_cuts, t_cuts;
+  int n_sub = 0;
+  std::vector<SubDesc> subs_h;
+  SubDesc* subs_d = nullptr;
+  int* order_d = nullptr;
+  long long ctrl_total = 0, traj_elems = 0, ptraj_total = 0, pt_steps = 0;
+  int max_nx = 0, max_ny = 0, min_ny = 0, max_levels = 0, max_pts = 0;
+  int cl = 1, R = 1, W = 3;
+  size_t tsize = 8;
+
+  void* traj = nullptr;
+  void* tgt = nullptr;
+  void* bnd = nullptr;
+  double *xb_a = nullptr, *w = nullptr, *w_prev = nullptr, *g = nullptr, *wt = nullptr,
+         *gt = nullptr, *p = nullptr, *S = nullptr, *Y = nullptr, *rho = nullptr;
+  double *vw = nullptr, *vw2 = nullptr, *lam_a = nullptr, *J = nullptr, *Jt = nullptr,
+         *parts = nullptr, *part = nullptr, *vconst = nullptr, *vpart = nullptr;
+  double *io_a = nullptr, *io_b = nullptr, *io_c = nullptr, *io_p = nullptr;
+  double* ptraj_io = nullptr;
+  ObsRec* obs_d = nullptr;
+  int* lvl_obs_d = nullptr;
+  double* obs_force_d = nullptr;
+  int *sc_tgt_d = nullptr, *sc_off_d = nullptr, *sc_obs_d = nullptr, *lvl_sc_d = nullptr;
+  double* sc_w_d = nullptr;
+  int *lon_cov_d = nullptr, *lat_cov_d = nullptr, *t_cov_d = nullptr;
+  LbState* lbst = nullptr;
+  int* phase_d = nullptr;
+  int* counter_d = nullptr;
+  int* counter_h = nullptr;   // pinned
+  int* phase_h = nullptr;     // pinned
+  double* scal_d = nullptr;
+  double* scal_h = nullptr;   // pinned
+  int* err_d = nullptr;
+  int vblocks = 8;
+  bool fwd_pending = false;
+  std::vector<void*> dec_allocs;
+
+  ~dd4dv_ctx();
+  void free_dec();
+};
+
+namespace {
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) fail(ctx, DD4DV_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define KL(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    ++ctx->launches;                                                                  \
+    if (e_ != cudaSuccess) fail(ctx, DD4DV_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+[[noreturn]] void fail(dd4dv_ctx* ctx, dd4dv_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  else g_create_error = buf;
+  throw Fail{st};
+}
+
+template <typename F>
+dd4dv_status guard(dd4dv_ctx* ctx, F&& f) {
+  if (!ctx) return DD4DV_EINVAL;
+  ctx->err.clear();
+  try {
+    return f();
+  } catch (const Fail& e) {
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    ctx->err = "host allocation failed";
+    return DD4DV_ENOMEM;
+  } catch (...) {
+    ctx->err = "internal error";
+    return DD4DV_EINVAL;
+  }
+}
+
+template <typename T>
+T* dalloc(dd4dv_ctx* ctx, size_t n, std::vector<void*>* list = nullptr) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(ctx, DD4DV_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(T), cudaGetErrorString(e));
+  }
+  if (list) list->push_back(p);
+  return static_cast<T*>(p);
+}
+
+void sync(dd4dv_ctx* ctx) {
+  CK(cudaStreamSynchronize(ctx->st));
+  int h = 0;
+  CK(cudaMemcpy(&h, ctx->err_d, sizeof(int), cudaMemcpyDeviceToHost));
+  if (h) {
+    CK(cudaMemset(ctx->err_d, 0, sizeof(int)));
+    fail(ctx, DD4DV_EINVAL, "device kernel rejected its launch configuration (code %d)", h);
+  }
+}
+
+void h2d(dd4dv_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ctx->st));
+}
+void d2h(dd4dv_ctx* ctx, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->st));
+}
+
+bool all_finite(const double* x, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+
+// Recursive-filter coefficient and amplitude (see dd4dv_set_background_error):
+// alpha from matching the variance 4 N alpha/(1-alpha)^2 of L L^T to ell^2;
+// c^-2 = centre value of (F^T F)^(2N) applied to a unit impulse on a line long
+// enough for the kernel to have decayed to below double precision.
+void rf_coeffs(double ell, int npass, double* alpha, double* c) {
+  const double E = 2.0 * npass / (ell * ell);
+  const double a = 1.0 + E - std::sqrt(E * (E + 2.0));
+  const int half = (int)(40 * ell) + 60;
+  const int n = 2 * half + 1;
+  std::vector<double> x(n, 0.0);
+  x[half] = 1.0;
+  for (int p = 0; p < 2 * npass; ++p) {
+    double q = 0.0;
+    for (int i = 0; i < n; ++i) { q = a * q + (1.0 - a) * x[i]; x[i] = q; }
+    q = 0.0;
+    for (int i = n - 1; i >= 0; --i) { q = a * q + (1.0 - a) * x[i]; x[i] = q; }
+  }
+  *alpha = a;
+  *c = 1.0 / std::sqrt(x[half]);
+}
+
+void require_dec(dd4dv_ctx* ctx) {
+  if (!ctx->has_dec) fail(ctx, DD4DV_ESTATE, "set_decomposition has not been called (or was invalidated)");
+}
+
+template <typename T>
+SweepArgs<T> sweep_args(dd4dv_ctx* ctx) {
+  SweepArgs<T> a{};
+  a.subs = ctx->subs_d;
+  a.order = ctx->order_d;
+  a.n_sub = ctx->n_sub;
+  a.traj = static_cast<T*>(ctx->traj);
+  a.tgt = static_cast<const T*>(ctx->tgt);
+  a.bnd = static_cast<const T*>(ctx->bnd);
+  a.rows = ctx->rows_d;
+  a.Bth = ctx->Bth;
+  a.gBth = ctx->gBth;
+  a.dt = ctx->m.dt;
+  a.h_ref = (sizeof(T) == 4) ? ctx->m.h_ref : 0.0;
+  a.nlon = ctx->m.nlon;
+  a.nlat = ctx->m.nlat;
+  a.nsteps = ctx->m.nsteps;
+  for (int v = 0; v < 3; ++v) a.isb2[v] = 1.0 / (ctx->sigma_b[v] * ctx->sigma_b[v]);
+  a.lam = ctx->dec.lambda;
+  a.mu = ctx->dec.mu;
+  a.obs = ctx->obs_d;
+  a.lvl_obs = ctx->lvl_obs_d;
+  a.obs_force = ctx->obs_force_d;
+  a.sc_tgt = ctx->sc_tgt_d;
+  a.sc_off = ctx->sc_off_d;
+  a.sc_obs = ctx->sc_obs_d;
+  a.sc_w = ctx->sc_w_d;
+  a.lvl_sc = ctx->lvl_sc_d;
+  a.part = ctx->part;
+  a.cl_max = ctx->cl;
+  a.active = nullptr;
+  a.active_value = 0;
+  a.lam_a = ctx->lam_a;
+  a.yforce = nullptr;
+  a.dx_out = nullptr;
+  a.dx0 = nullptr;
+  a.R = ctx->R;
+  a.W = ctx->W;
+  a.err = ctx->err_d;
+  return a;
+}
+
+double h_ref_of(dd4dv_ctx* ctx) { return ctx->m.precision == 1 ? ctx->m.h_ref : 0.0; }
+
+// V w -> initial states (level 0 of every trajectory).  vw_buf receives L w.
+template <typename T>
+void init_states(dd4dv_ctx* ctx, const double* w, double* vw_buf, const int* active, int av) {
+  const double* src = w;
+  if (ctx->corr_len > 0.0) {
+    KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, w, nullptr, vw_buf, active, av, ctx->max_pts, ctx->st));
+    RFArgs ra{ctx->subs_d, ctx->n_sub, ctx->rf_alpha, ctx->rf_c, ctx->rf_passes, active, av};
+    KL(launch_rf_rows(vw_buf, ra, ctx->max_ny, ctx->st));
+    KL(launch_rf_cols(vw_buf, ra, ctx->max_nx, ctx->st));
+    src = vw_buf;
+  }
+  KL(launch_init_state<T>(ctx->subs_d, ctx->n_sub, ctx->xb_a, src, ctx->sigma_d, 1, h_ref_of(ctx),
+                          static_cast<T*>(ctx->traj), active, av, ctx->max_pts, ctx->st));
+}
+
+// out = V^T y  (+ w, times scale) for the subdomains in the mask.
+void apply_VT(dd4dv_ctx* ctx, const double* y, const double* w, const double* scale, double* out,
+              const int* active, int av) {
+  KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, y, ctx->sigma_d, ctx->vw2, active, av, ctx->max_pts, ctx->st));
+  if (ctx->corr_len > 0.0) {
+    RFArgs ra{ctx->subs_d, ctx->n_sub, ctx->rf_alpha, ctx->rf_c, ctx->rf_passes, active, av};
+    KL(launch_rf_cols(ctx->vw2, ra, ctx->max_nx, ctx->st));
+    KL(launch_rf_rows(ctx->vw2, ra, ctx->max_ny, ctx->st));
+  }
+  KL(launch_grad_finish(ctx->subs_d, ctx->n_sub, w, ctx->vw2, scale, out, active, av, ctx->max_pts, ctx->st));
+}
+
+template <typename T>
+void forward_sweep(dd4dv_ctx* ctx, const int* active, int av) {
+  SweepArgs<T> a = sweep_args<T>(ctx);
+  a.active = active;
+  a.active_value = av;
+  KL(launch_forward<T>(a, ctx->cl, 256, ctx->st));
+}
+
+template <typename T>
+void eval_T(dd4dv_ctx* ctx, const double* w, double* J, double* grad, double* parts, const int* active,
+            int av, const double* scale) {
+  init_states<T>(ctx, w, ctx->vw, active, av);
+  forward_sweep<T>(ctx, active, av);
+  KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, w, ctx->part, ctx->cl, ctx->vconst, ctx->dec.lambda,
+                       ctx->dec.mu, J, parts, active, av, ctx->st));
+  if (grad) {
+    SweepArgs<T> a = sweep_args<T>(ctx);
+    a.active = active;
+    a.active_value = av;
+    KL(launch_adjoint<T>(a, ctx->cl, 256, ctx->st));
+    apply_VT(ctx, ctx->lam_a, w, scale, grad, active, av);
+  }
+}
+
+template <typename T>
+void exchange_T(dd4dv_ctx* ctx, const double* w) {
+  init_states<T>(ctx, w, ctx->vw, nullptr, 0);
+  forward_sweep<T>(ctx, nullptr, 0);
+  ExchArgs<T> x{};
+  x.subs = ctx->subs_d;
+  x.n_sub = ctx->n_sub;
+  x.P1 = ctx->dec.P1;
+  x.P2 = ctx->dec.P2;
+  x.Q = ctx->dec.Q;
+  x.nlon = ctx->m.nlon;
+  x.nlat = ctx->m.nlat;
+  x.nsteps = ctx->m.nsteps;
+  x.traj = static_cast<const T*>(ctx->traj);
+  x.tgt = static_cast<T*>(ctx->tgt);
+  x.bnd = static_cast<T*>(ctx->bnd);
+  for (int v = 0; v < 3; ++v) x.isb2[v] = 1.0 / (ctx->sigma_b[v] * ctx->sigma_b[v]);
+  x.vpart = ctx->vpart;
+  x.vblocks = ctx->vblocks;
+  x.lon_cov = ctx->lon_cov_d;
+  x.lat_cov = ctx->lat_cov_d;
+  x.t_cov = ctx->t_cov_d;
+  KL(launch_targets<T>(x, ctx->st));
+  KL(launch_sum_vconst(ctx->vpart, ctx->n_sub, ctx->vblocks, ctx->vconst, ctx->st));
+  KL(launch_assemble<T>(x, ctx->st));
+  ctx->fwd_pending = false;
+}
+
+template <typename T>
+void reset_exchange_T(dd4dv_ctx* ctx) {
+  const long long n = (long long)ctx->gtraj;
+  KL(launch_bnd_from_global<T>(ctx->xb_traj, n, h_ref_of(ctx), ctx->m.nlon, ctx->m.nlat,
+                               static_cast<T*>(ctx->bnd), ctx->st));
+  KL(launch_restrict<T>(ctx->subs_d, ctx->n_sub, ctx->m.nlon, ctx->m.nlat, ctx->xb_traj, h_ref_of(ctx),
+                        static_cast<T*>(ctx->tgt), ctx->max_pts, ctx->max_levels, ctx->st));
+  CK(cudaMemsetAsync(ctx->vconst, 0, ctx->n_sub * sizeof(double), ctx->st));
+  ctx->fwd_pending = false;
+}
+
+// Global model run x0 (device) -> out trajectory (device, FP64).
+void global_run(dd4dv_ctx* ctx, const double* x0, double* out) {
+  const size_t G = ctx->gstate;
+  CK(cudaMemcpyAsync(out, x0, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  double* s1 = ctx->gscratch;
+  double* s2 = ctx->gscratch + G;
+  for (int n = 0; n < ctx->m.nsteps; ++n) {
+    const double* x = out + (size_t)n * G;
+    double* nx = out + (size_t)(n + 1) * G;
+    KL(launch_global_stage(x, x, s1, 0.0, 1.0, ctx->rows_d, ctx->Bth, ctx->gBth, ctx->m.dt,
+                           ctx->m.nlon, ctx->m.nlat, ctx->st));
+    KL(launch_global_stage(x, s1, s2, 0.75, 0.25, ctx->rows_d, ctx->Bth, ctx->gBth, ctx->m.dt,
+                           ctx->m.nlon, ctx->m.nlat, ctx->st));
+    KL(launch_global_stage(x, s2, nx, 1.0 / 3.0, 2.0 / 3.0, ctx->rows_d, ctx->Bth, ctx->gBth,
+                           ctx->m.dt, ctx->m.nlon, ctx->m.nlat, ctx->st));
+  }
+}
+
+// Copies a host input into a device buffer when device_ptrs == 0.
+const double* stage_in(dd4dv_ctx* ctx, const double* src, double* buf, size_t n, int device_ptrs) {
+  if (device_ptrs) return src;
+  h2d(ctx, buf, src, n * sizeof(double));
+  return buf;
+}
+
+template <typename F>
+auto by_precision(dd4dv_ctx* ctx, F&& f) {
+  if (ctx->m.precision == 1) return f(float{});
+  return f(double{});
+}
+
+// ---------------------------------------------------------------------------
+// Decomposition tables.
+std::vector<int> make_cuts(dd4dv_ctx* ctx, const int* cuts, int n, int parts, const char* name) {
+  std::vector<int> c(parts + 1);
+  if (cuts) {
+    for (int k = 0; k <= parts; ++k) c[k] = cuts[k];
+    if (c[0] != 0 || c[parts] != n) fail(ctx, DD4DV_EINVAL, "%s cuts must run from 0 to %d", name, n);
+    for (int k = 0; k < parts; ++k)
+      if (c[k + 1] <= c[k]) fail(ctx, DD4DV_EINVAL, "%s cuts must increase", name);
+  } else {
+    for (int k = 0; k <= parts; ++k) c[k] = (int)(((long long)k * n) / parts);
+  }
+  return c;
+}
+
+void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
+  const int nlon = ctx->m.nlon, nlat = ctx->m.nlat, nsteps = ctx->m.nsteps;
+  if (d.P1 < 1 || d.P2 < 1 || d.Q < 1) fail(ctx, DD4DV_EINVAL, "P1, P2, Q must be >= 1");
+  if (d.o_lon < 0 || d.o_lat < 0 || d.o_t < 0) fail(ctx, DD4DV_EINVAL, "overlaps must be >= 0");
+  if (!(d.mu >= 0.0) || !(d.lambda >= 0.0)) fail(ctx, DD4DV_EINVAL, "mu, lambda must be >= 0");
+  if (d.Q > 1 && nsteps < 1) fail(ctx, DD4DV_EINVAL, "time split needs nsteps >= 1");
+  ctx->lon_cuts = make_cuts(ctx, d.lon_cuts, nlon, d.P1, "lon");
+  ctx->lat_cuts = make_cuts(ctx, d.lat_cuts, nlat, d.P2, "lat");
+  ctx->t_cuts = make_cuts(ctx, d.t_cuts, nsteps, d.Q, "time");
+  if (d.P1 > 1) {
+    if (d.o_lon < 1) fail(ctx, DD4DV_EINVAL, "o_lon must be >= 1 when longitude is split");
+    for (int k = 0; k < d.P1; ++k) {
+      const int core = ctx->lon_cuts[k + 1] - ctx->lon_cuts[k];
+      if (core < 2 * d.o_lon || core < 2) fail(ctx, DD4DV_EINVAL, "lon core block %d (%d) < 2*o_lon", k, core);
+      if (core + 2 * d.o_lon >= nlon) fail(ctx, DD4DV_EINVAL, "extended lon box wraps onto itself");
+    }
+  }
+  if (d.P2 > 1) {
+    if (d.o_lat < 1) fail(ctx, DD4DV_EINVAL, "o_lat must be >= 1 when latitude is split");
+    for (int k = 0; k < d.P2; ++k) {
+      const int core = ctx->lat_cuts[k + 1] - ctx->lat_cuts[k];
+      if (core < 2 * d.o_lat || core < 2) fail(ctx, DD4DV_EINVAL, "lat core block %d (%d) < 2*o_lat", k, core);
+    }
+  }
+  if (d.Q > 1)
+    for (int k = 0; k < d.Q; ++k) {
+      const int core = ctx->t_cuts[k + 1] - ctx->t_cuts[k];
+      if (core < 2 * d.o_t + 1) fail(ctx, DD4DV_EINVAL, "time core block %d (%d) < 2*o_t+1", k, core);
+    }
+  if (d.ckpt_k != 0) fail(ctx, DD4DV_EINVAL, "trajectory checkpointing (ckpt_k != 0) is not available in this build");
+
+  const int n_sub = d.P1 * d.P2 * d.Q;
+  std::vector<SubDesc> subs(n_sub);
+  long long ctrl = 0, trj = 0, ptrj = 0, pts = 0;
+  int max_nx = 0, max_ny = 0, min_ny = 1 << 30, max_lv = 0, max_pts = 0;
+  for (int q = 0; q < d.Q; ++q)
+    for (int p2 = 0; p2 < d.P2; ++p2)
+      for (int p1 = 0; p1 < d.P1; ++p1) {
+        SubDesc s{};
+        const int idx = (q * d.P2 + p2) * d.P1 + p1;
+        if (d.Q == 1) { s.a = 0; s.b = nsteps; }
+        else {
+          s.a = std::max(0, ctx->t_cuts[q] - d.o_t);
+          s.b = std::min(nsteps, ctx->t_cuts[q + 1] + d.o_t);
+        }
+        if (d.P2 == 1) { s.j0 = 0; s.ny = nlat; }
+        else {
+          s.j0 = std::max(0, ctx->lat_cuts[p2] - d.o_lat);
+          s.ny = std::min(nlat, ctx->lat_cuts[p2 + 1] + d.o_lat) - s.j0;
+        }
+        s.flags = 0;
+        if (d.P1 == 1) { s.i0 = 0; s.nx = nlon; s.flags |= F_PERIODIC; }
+        else {
+          s.i0 = ((ctx->lon_cuts[p1] - d.o_lon) % nlon + nlon) % nlon;
+          s.nx = ctx->lon_cuts[p1 + 1] - ctx->lon_cuts[p1] + 2 * d.o_lon;
+        }
+        if (s.j0 == 0) s.flags |= F_SWALL;
+        if (s.j0 + s.ny == nlat) s.flags |= F_NWALL;
+        s.q = q; s.p2 = p2; s.p1 = p1;
+        s.wL = s.wR = (d.P1 > 1) ? 2 * d.o_lon : 0;
+        s.wS = (p2 > 0) ? 2 * d.o_lat : 0;
+        s.wN = (p2 < d.P2 - 1) ? 2 * d.o_lat : 0;
+        s.tA = (q > 0) ? 2 * d.o_t + 1 : 0;
+        s.tB = (q < d.Q - 1) ? 2 * d.o_t + 1 : 0;
+        if (s.ny < 2 || s.nx < 2) fail(ctx, DD4DV_EINVAL, "subdomain boxes need at least 2x2 points");
+        s.nxp = (s.nx + 3) / 4 * 4;
+        const int L = s.b - s.a;
+        s.ctrl_off = ctrl;
+        s.traj_off = trj;
+        s.ptraj_off = ptrj;
+        ctrl += 3LL * s.ny * s.nx;
+        trj += (long long)(L + 1) * 3 * s.ny * s.nxp;
+        ptrj += (long long)(L + 1) * 3 * s.ny * s.nx;
+        pts += (long long)s.nx * s.ny * L;
+        max_nx = std::max(max_nx, s.nx);
+        max_ny = std::max(max_ny, s.ny);
+        min_ny = std::min(min_ny, s.ny);
+        max_lv = std::max(max_lv, L + 1);
+        max_pts = std::max(max_pts, 3 * s.ny * s.nx);
+        subs[idx] = s;
+      }
+  ctx->n_sub = n_sub;
+  ctx->ctrl_total = ctrl;
+  ctx->traj_elems = trj;
+  ctx->ptraj_total = ptrj;
+  ctx->pt_steps = pts;
+  ctx->max_nx = max_nx;
+  ctx->max_ny = max_ny;
+  ctx->min_ny = min_ny;
+  ctx->max_levels = max_lv;
+  ctx->max_pts = max_pts;
+
+  // observations -> per-subdomain records, per-level ranges, adjoint scatter plan
+  const double href = h_ref_of(ctx);
+  std::vector<std::vector<std::pair<int, ObsRec>>> per_sub(n_sub);   // (level, rec)
+  const size_t nob = ctx->ob_level.size();
+  std::vector<int> lon_in, lat_in, win_in;
+  for (size_t k = 0; k < nob; ++k) {
+    const double fi = ctx->ob_fi[k], fj = ctx->ob_fj[k];
+    const int i0 = (int)std::floor(fi), j0 = (int)std::floor(fj);
+    const double di = fi - i0, dj = fj - j0;
+    const int i1 = (i0 + 1) % nlon;
+    const int lev = ctx->ob_level[k];
+    lon_in.clear(); lat_in.clear(); win_in.clear();
+    for (int p1 = 0; p1 < d.P1; ++p1) {
+      const SubDesc& s = subs[p1];
+      const int k0 = ((i0 - s.i0) % nlon + nlon) % nlon;
+      const int k1 = ((i1 - s.i0) % nlon + nlon) % nlon;
+      if (k0 < s.nx && (di == 0.0 || k1 < s.nx)) lon_in.push_back(p1);
+    }
+    for (int p2 = 0; p2 < d.P2; ++p2) {
+      const SubDesc& s = subs[p2 * d.P1];
+      if (j0 >= s.j0 && j0 < s.j0 + s.ny && (dj == 0.0 || j0 + 1 < s.j0 + s.ny)) lat_in.push_back(p2);
+    }
+    for (int q = 0; q < d.Q; ++q) {
+      const SubDesc& s = subs[q * d.P2 * d.P1];
+      if (lev >= s.a && lev <= s.b) win_in.push_back(q);
+    }
+    const size_t cnt = lon_in.size() * lat_in.size() * win_in.size();
+    if (cnt == 0) continue;
+    const double omega = d.weight_obs ? 1.0 / (double)cnt : 1.0;
+    for (int q : win_in)
+      for (int p2 : lat_in)
+        for (int p1 : lon_in) {
+          const int sidx = (q * d.P2 + p2) * d.P1 + p1;
+          const SubDesc& s = subs[sidx];
+          ObsRec r{};
+          r.var = ctx->ob_var[k];
+          r.r0 = j0 - s.j0;
+          r.k0 = ((i0 - s.i0) % nlon + nlon) % nlon;
+          r.k1 = (di != 0.0) ? ((i1 - s.i0) % nlon + nlon) % nlon : r.k0;
+          r.di = di;
+          r.dj = dj;
+          r.y = ctx->ob_val[k] - (r.var == 0 ? href : 0.0);
+          r.w = omega / (ctx->ob_so[k] * ctx->ob_so[k]);
+          per_sub[sidx].push_back({lev - s.a, r});
+        }
+  }
+  std::vector<ObsRec> recs;
+  std::vector<int> lvl_obs, lvl_sc, sc_tgt, sc_off, sc_obs;
+  std::vector<double> sc_w;
+  for (int sidx = 0; sidx < n_sub; ++sidx) {
+    SubDesc& s = subs[sidx];
+    const int L = s.b - s.a;
+    auto& v = per_sub[sidx];
+    std::stable_sort(v.begin(), v.end(), [](const auto& x, const auto& y) { return x.first < y.first; });
+    s.obs_lvl = (int)lvl_obs.size();
+    s.sc_lvl = (int)lvl_sc.size();
+    size_t pos = 0;
+    for (int l = 0; l <= L; ++l) {
+      lvl_obs.push_back((int)recs.size());
+      lvl_sc.push_back((int)sc_tgt.size());
+      std::map<int, std::vector<std::pair<int, double>>> tg;   // target -> (record, weight)
+      while (pos < v.size() && v[pos].first == l) {
+        const int ridx = (int)recs.size();
+        const ObsRec& r = v[pos].second;
+        recs.push_back(r);
+        const int plane = s.ny * s.nx;
+        auto add = [&](int rr, int kk, double wgt) {
+          tg[r.var * plane + rr * s.nx + kk].push_back({ridx, wgt});
+        };
+        add(r.r0, r.k0, (1.0 - r.dj) * (1.0 - r.di));
+        if (r.di != 0.0) add(r.r0, r.k1, (1.0 - r.dj) * r.di);
+        if (r.dj != 0.0) {
+          add(r.r0 + 1, r.k0, r.dj * (1.0 - r.di));
+          if (r.di != 0.0) add(r.r0 + 1, r.k1, r.dj * r.di);
+        }
+        ++pos;
+      }
+      for (auto& kv : tg) {
+        sc_tgt.push_back(kv.first);
+        sc_off.push_back((int)sc_obs.size());
+        for (auto& c : kv.second) {
+          sc_obs.push_back(c.first);
+          sc_w.push_back(c.second);
+        }
+      }
+    }
+    lvl_obs.push_back((int)recs.size());
+    lvl_sc.push_back((int)sc_tgt.size());
+  }
+  sc_off.push_back((int)sc_obs.size());
+
+  // cover tables for the assembly
+  std::vector<int> lon_cov(nlon * 4, -1), lat_cov(nlat * 4, -1), t_cov((nsteps + 1) * 4, -1);
+  for (int i = 0; i < nlon; ++i) {
+    int c = 0;
+    for (int p1 = 0; p1 < d.P1 && c < 2; ++p1) {
+      const SubDesc& s = subs[p1];
+      const int kk = ((i - s.i0) % nlon + nlon) % nlon;
+      if (kk < s.nx) { lon_cov[i * 4 + 2 * c] = p1; lon_cov[i * 4 + 2 * c + 1] = kk; ++c; }
+    }
+  }
+  for (int j = 0; j < nlat; ++j) {
+    int c = 0;
+    for (int p2 = 0; p2 < d.P2 && c < 2; ++p2) {
+      const SubDesc& s = subs[p2 * d.P1];
+      if (j >= s.j0 && j < s.j0 + s.ny) { lat_cov[j * 4 + 2 * c] = p2; lat_cov[j * 4 + 2 * c + 1] = j - s.j0; ++c; }
+    }
+  }
+  for (int n = 0; n <= nsteps; ++n) {
+    int c = 0;
+    for (int q = 0; q < d.Q && c < 2; ++q) {
+      const SubDesc& s = subs[q * d.P2 * d.P1];
+      if (n >= s.a && n <= s.b) { t_cov[n * 4 + 2 * c] = q; t_cov[n * 4 + 2 * c + 1] = n - s.a; ++c; }
+    }
+  }
+
+  // cluster size: CTAs per subdomain
+  const size_t smem_cap = 232448;
+  const bool f32 = ctx->m.precision == 1;
+  ctx->W = max_nx + 2;
+  auto smem_need = [&](int R) {
+    return f32 ? smem_adjoint<float>(R, ctx->W) : smem_adjoint<double>(R, ctx->W);
+  };
+  int cl = d.cluster;
+  if (cl > 0) {
+    if (cl > 16 || cl > min_ny) fail(ctx, DD4DV_EINVAL, "cluster size %d must be <= 16 and <= smallest box height %d", cl, min_ny);
+    ctx->R = (max_ny + cl - 1) / cl;
+    if (smem_need(ctx->R) > smem_cap) fail(ctx, DD4DV_EINVAL, "cluster size %d needs too much shared memory", cl);
+  } else {
+    // Estimated time ~ waves of CTAs x rows per CTA: pick the smallest
+    // cluster that minimises it (fewer CTAs per subdomain = fewer barriers).
+    int nsm = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    double best = 1e300;
+    int best_cl = -1;
+    for (int c : {1, 2, 4, 8, 16}) {
+      if (c > min_ny) break;
+      const int R = (max_ny + c - 1) / c;
+      const size_t sm = smem_need(R);
+      if (sm > smem_cap) continue;
+      int per_sm = f32 ? occupancy_adjoint<float>(R, ctx->W, 256) : occupancy_adjoint<double>(R, ctx->W, 256);
+      if (per_sm < 1) continue;
+      const long long ctas = (long long)n_sub * c;
+      const double waves = std::ceil((double)ctas / ((double)nsm * per_sm));
+      const double cost = waves * R * (double)per_sm;
+      if (cost < best * 0.97) { best = cost; best_cl = c; }
+    }
+    if (best_cl < 0) fail(ctx, DD4DV_EINVAL, "subdomain boxes too large for the shared-memory sweep (max %dx%d)", max_nx, max_ny);
+    cl = best_cl;
+    ctx->R = (max_ny + cl - 1) / cl;
+  }
+  ctx->cl = cl;
+
+  // device tables and buffers
+  ctx->free_dec();
+  auto& L = ctx->dec_allocs;
+  ctx->tsize = f32 ? sizeof(float) : sizeof(double);
+  ctx->subs_d = dalloc<SubDesc>(ctx, n_sub, &L);
+  ctx->order_d = dalloc<int>(ctx, n_sub, &L);
+  std::vector<int> order(n_sub);
+  for (int s = 0; s < n_sub; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    const long long wx = (long long)subs[x].nx * subs[x].ny * (subs[x].b - subs[x].a + 1);
+    const long long wy = (long long)subs[y].nx * subs[y].ny * (subs[y].b - subs[y].a + 1);
+    return wx > wy;
+  });
+  ctx->traj = dalloc<unsigned char>(ctx, ctx->traj_elems * ctx->tsize, &L);
+  ctx->tgt = dalloc<unsigned char>(ctx, ctx->traj_elems * ctx->tsize, &L);
+  ctx->bnd = dalloc<unsigned char>(ctx, ctx->gtraj * ctx->tsize, &L);
+  const size_t C = (size_t)ctrl;
+  ctx->xb_a = dalloc<double>(ctx, C, &L);
+  ctx->w = dalloc<double>(ctx, C, &L);
+  ctx->w_prev = dalloc<double>(ctx, C, &L);
+  ctx->g = dalloc<double>(ctx, C, &L);
+  ctx->wt = dalloc<double>(ctx, C, &L);
+  ctx->gt = dalloc<double>(ctx, C, &L);
+  ctx->p = dalloc<double>(ctx, C, &L);
+  ctx->vw = dalloc<double>(ctx, C, &L);
+  ctx->vw2 = dalloc<double>(ctx, C, &L);
+  ctx->lam_a = dalloc<double>(ctx, C, &L);
+  ctx->io_a = dalloc<double>(ctx, C, &L);
+  ctx->io_b = dalloc<double>(ctx, C, &L);
+  ctx->io_c = dalloc<double>(ctx, C, &L);
+  ctx->J = dalloc<double>(ctx, n_sub, &L);
+  ctx->Jt = dalloc<double>(ctx, n_sub, &L);
+  ctx->io_p = dalloc<double>(ctx, 5 * n_sub, &L);
+  ctx->parts = dalloc<double>(ctx, 3 * n_sub, &L);
+  ctx->part = dalloc<double>(ctx, 2 * (size_t)n_sub * cl, &L);
+  ctx->vconst = dalloc<double>(ctx, n_sub, &L);
+  ctx->vpart = dalloc<double>(ctx, (size_t)n_sub * ctx->vblocks, &L);
+  ctx->ptraj_io = nullptr;
+  const int m = 8;   // history slots allocated (solver lbfgs_m <= 8)
+  ctx->S = dalloc<double>(ctx, m * C, &L);
+  ctx->Y = dalloc<double>(ctx, m * C, &L);
+  ctx->rho = dalloc<double>(ctx, (size_t)m * n_sub, &L);
+  ctx->lbst = dalloc<LbState>(ctx, n_sub, &L);
+  ctx->phase_d = dalloc<int>(ctx, n_sub, &L);
+  ctx->obs_d = dalloc<ObsRec>(ctx, recs.size(), &L);
+  ctx->obs_force_d = dalloc<double>(ctx, recs.size(), &L);
+  ctx->lvl_obs_d = dalloc<int>(ctx, lvl_obs.size(), &L);
+  ctx->lvl_sc_d = dalloc<int>(ctx, lvl_sc.size(), &L);
+  ctx->sc_tgt_d = dalloc<int>(ctx, sc_tgt.size(), &L);
+  ctx->sc_off_d = dalloc<int>(ctx, sc_off.size(), &L);
+  ctx->sc_obs_d = dalloc<int>(ctx, sc_obs.size(), &L);
+  ctx->sc_w_d = dalloc<double>(ctx, sc_w.size(), &L);
+  ctx->lon_cov_d = dalloc<int>(ctx, lon_cov.size(), &L);
+  ctx->lat_cov_d = dalloc<int>(ctx, lat_cov.size(), &L);
+  ctx->t_cov_d = dalloc<int>(ctx, t_cov.size(), &L);
+  h2d(ctx, ctx->subs_d, subs.data(), subs.size() * sizeof(SubDesc));
+  h2d(ctx, ctx->order_d, order.data(), order.size() * sizeof(int));
+  if (!recs.empty()) h2d(ctx, ctx->obs_d, recs.data(), recs.size() * sizeof(ObsRec));
+  h2d(ctx, ctx->lvl_obs_d, lvl_obs.data(), lvl_obs.size() * sizeof(int));
+  h2d(ctx, ctx->lvl_sc_d, lvl_sc.data(), lvl_sc.size() * sizeof(int));
+  if (!sc_tgt.empty()) h2d(ctx, ctx->sc_tgt_d, sc_tgt.data(), sc_tgt.size() * sizeof(int));
+  h2d(ctx, ctx->sc_off_d, sc_off.data(), sc_off.size() * sizeof(int));
+  if (!sc_obs.empty()) {
+    h2d(ctx, ctx->sc_obs_d, sc_obs.data(), sc_obs.size() * sizeof(int));
+    h2d(ctx, ctx->sc_w_d, sc_w.data(), sc_w.size() * sizeof(double));
+  }
+  h2d(ctx, ctx->lon_cov_d, lon_cov.data(), lon_cov.size() * sizeof(int));
+  h2d(ctx, ctx->lat_cov_d, lat_cov.data(), lat_cov.size() * sizeof(int));
+  h2d(ctx, ctx->t_cov_d, t_cov.data(), t_cov.size() * sizeof(int));
+  CK(cudaMemsetAsync(ctx->w, 0, C * sizeof(double), ctx->st));
+  CK(cudaMemsetAsync(ctx->w_prev, 0, C * sizeof(double), ctx->st));
+  CK(cudaMemsetAsync(ctx->traj, 0, ctx->traj_elems * ctx->tsize, ctx->st));
+  CK(cudaMemsetAsync(ctx->obs_force_d, 0, std::max<size_t>(1, recs.size()) * sizeof(double), ctx->st));
+  ctx->subs_h = subs;
+  ctx->dec = d;
+  ctx->dec.lon_cuts = ctx->dec.lat_cuts = ctx->dec.t_cuts = nullptr;
+  ctx->dec.cluster = cl;
+  KL(launch_restrict_level(ctx->subs_d, n_sub, nlon, nlat, ctx->xb_traj, ctx->xb_a, max_pts, ctx->st));
+  by_precision(ctx, [&](auto t) {
+    using T = decltype(t);
+    reset_exchange_T<T>(ctx);
+    return 0;
+  });
+  sync(ctx);
+  ctx->has_dec = true;
+}
+
+}  // namespace
+
+dd4dv_ctx::~dd4dv_ctx() {
+  free_dec();
+  cudaFree(rows_d);
+  cudaFree(xb_traj);
+  cudaFree(gscratch);
+  cudaFree(gtraj_io);
+  cudaFree(sigma_d);
+  cudaFree(counter_d);
+  cudaFree(scal_d);
+  cudaFree(err_d);
+  cudaFreeHost(counter_h);
+  cudaFreeHost(phase_h);
+  cudaFreeHost(scal_h);
+  cudaFree(ptraj_io);
+  if (own_stream && st) cudaStreamDestroy(st);
+}
+
+void dd4dv_ctx::free_dec() {
+  if (st) cudaStreamSynchronize(st);
+  for (void* p : dec_allocs) cudaFree(p);
+  dec_allocs.clear();
+  cudaFreeHost(phase_h);
+  phase_h = nullptr;
+  cudaFree(ptraj_io);
+  ptraj_io = nullptr;
+  has_dec = false;
+}
+
+extern "C" {
+
+dd4dv_status dd4dv_create(const dd4dv_model* model, void* cuda_stream, dd4dv_ctx** out) {
+  g_create_error.clear();
+  if (!model || !out) {
+    g_create_error = "NULL argument";
+    return DD4DV_EINVAL;
+  }
+  *out = nullptr;
+  dd4dv_ctx* ctx = nullptr;
+  try {
+    const dd4dv_model& m = *model;
+    if (m.nlon < 3 || m.nlat < 2 || !(m.dt > 0.0) || m.nsteps < 0 || !(m.radius > 0.0) ||
+        !(m.gravity > 0.0) || !(m.lat_max_deg > m.lat_min_deg) || m.lat_min_deg <= -90.0 ||
+        m.lat_max_deg >= 90.0 || (m.precision != 0 && m.precision != 1) || !std::isfinite(m.omega) ||
+        !std::isfinite(m.h_ref)) {
+      g_create_error = "invalid model parameters";
+      return DD4DV_EINVAL;
+    }
+    ctx = new dd4dv_ctx();
+    ctx->m = m;
+    if (cuda_stream) {
+      ctx->st = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+      cudaError_t e = cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        g_create_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+        delete ctx;
+        return DD4DV_ECUDA;
+      }
+      ctx->own_stream = true;
+    }
+    // row constants (Sec. 7): theta_j at cell centres between the walls
+    const double pi = 3.14159265358979323846;
+    const double dlam = 2.0 * pi / m.nlon;
+    const double dth = (m.lat_max_deg - m.lat_min_deg) * pi / 180.0 / m.nlat;
+    const double th0 = m.lat_min_deg * pi / 180.0;
+    ctx->Bth = 1.0 / (2.0 * m.radius * dth);
+    ctx->gBth = m.gravity * ctx->Bth;
+    ctx->rows_h.resize(m.nlat);
+    for (int j = 0; j < m.nlat; ++j) {
+      const double th = th0 + (j + 0.5) * dth;
+      RowConst r;
+      r.c = std::cos(th);
+      r.A = 1.0 / (2.0 * m.radius * r.c * dlam);
+      r.f = 2.0 * m.omega * std::sin(th);
+      r.tau = std::tan(th) / m.radius;
+      r.BinvC = ctx->Bth / r.c;
+      r.gA = m.gravity * r.A;
+      ctx->rows_h[j] = r;
+    }
+    ctx->gstate = 3ULL * m.nlat * m.nlon;
+    ctx->gtraj = (size_t)(m.nsteps + 1) * ctx->gstate;
+    ctx->rows_d = dalloc<RowConst>(ctx, m.nlat);
+    ctx->xb_traj = dalloc<double>(ctx, ctx->gtraj);
+    ctx->gscratch = dalloc<double>(ctx, 3 * ctx->gstate);
+    ctx->gtraj_io = dalloc<double>(ctx, ctx->gtraj);
+    ctx->sigma_d = dalloc<double>(ctx, 3);
+    ctx->counter_d = dalloc<int>(ctx, 4);
+    ctx->scal_d = dalloc<double>(ctx, 8);
+    ctx->err_d = dalloc<int>(ctx, 1);
+    if (cudaMallocHost(&ctx->counter_h, 4 * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->scal_h, 8 * sizeof(double)) != cudaSuccess)
+      fail(ctx, DD4DV_ENOMEM, "pinned host allocation failed");
+    CK(cudaMemcpyAsync(ctx->rows_d, ctx->rows_h.data(), m.nlat * sizeof(RowConst),
+                       cudaMemcpyHostToDevice, ctx->st));
+    CK(cudaMemsetAsync(ctx->err_d, 0, sizeof(int), ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    *out = ctx;
+    return DD4DV_OK;
+  } catch (const Fail& f) {
+    if (ctx) {
+      g_create_error = ctx->err;
+      delete ctx;
+    }
+    return f.st;
+  } catch (...) {
+    delete ctx;
+    g_create_error = "allocation failed";
+    return DD4DV_ENOMEM;
+  }
+}
+
+dd4dv_status dd4dv_destroy(dd4dv_ctx* ctx) {
+  delete ctx;
+  return DD4DV_OK;
+}
+
+const char* dd4dv_last_error(const dd4dv_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+dd4dv_status dd4dv_set_background(dd4dv_ctx* ctx, const double* xb0) {
+  return guard(ctx, [&] {
+    if (!xb0) fail(ctx, DD4DV_EINVAL, "xb0 is NULL");
+    if (!all_finite(xb0, ctx->gstate)) fail(ctx, DD4DV_ENONFINITE, "background contains NaN or Inf");
+    ctx->free_dec();
+    h2d(ctx, ctx->gscratch + 2 * ctx->gstate, xb0, ctx->gstate * sizeof(double));
+    // the global run needs the initial state outside its scratch: stage it in the io trajectory
+    CK(cudaMemcpyAsync(ctx->gtraj_io, ctx->gscratch + 2 * ctx->gstate, ctx->gstate * sizeof(double),
+                       cudaMemcpyDeviceToDevice, ctx->st));
+    global_run(ctx, ctx->gtraj_io, ctx->xb_traj);
+    sync(ctx);
+    ctx->has_bg = true;
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_set_background_error(dd4dv_ctx* ctx, const double sigma_b[3], double corr_len,
+                                        int rf_passes) {
+  return guard(ctx, [&] {
+    if (!sigma_b) fail(ctx, DD4DV_EINVAL, "sigma_b is NULL");
+    for (int v = 0; v < 3; ++v)
+      if (!(sigma_b[v] > 0.0) || !std::isfinite(sigma_b[v])) fail(ctx, DD4DV_EINVAL, "sigma_b must be > 0");
+    if (!(corr_len >= 0.0) || !std::isfinite(corr_len)) fail(ctx, DD4DV_EINVAL, "corr_len must be >= 0");
+    if (corr_len > 0.0 && (rf_passes < 1 || rf_passes > 8)) fail(ctx, DD4DV_EINVAL, "rf_passes must be 1..8");
+    ctx->free_dec();
+    for (int v = 0; v < 3; ++v) ctx->sigma_b[v] = sigma_b[v];
+    ctx->corr_len = corr_len;
+    ctx->rf_passes = rf_passes;
+    if (corr_len > 0.0) rf_coeffs(corr_len, rf_passes, &ctx->rf_alpha, &ctx->rf_c);
+    h2d(ctx, ctx->sigma_d, ctx->sigma_b, 3 * sizeof(double));
+    sync(ctx);
+    ctx->has_berr = true;
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_set_observations(dd4dv_ctx* ctx, long long n, const int* level, const int* var,
+                                    const double* fi, const double* fj, const double* value,
+                                    const double* sigma_o) {
+  return guard(ctx, [&] {
+    if (n < 0) fail(ctx, DD4DV_EINVAL, "n < 0");
+    if (n > 0 && (!level || !var || !fi || !fj || !value || !sigma_o)) fail(ctx, DD4DV_EINVAL, "NULL array");
+    const int nlon = ctx->m.nlon, nlat = ctx->m.nlat;
+    for (long long k = 0; k < n; ++k) {
+      if (level[k] < 0 || level[k] > ctx->m.nsteps) fail(ctx, DD4DV_EINVAL, "obs %lld: level out of range", k);
+      if (var[k] < 0 || var[k] > 2) fail(ctx, DD4DV_EINVAL, "obs %lld: var out of range", k);
+      if (!std::isfinite(fi[k]) || !std::isfinite(fj[k]) || !std::isfinite(value[k]) || !std::isfinite(sigma_o[k]))
+        fail(ctx, DD4DV_ENONFINITE, "obs %lld: NaN or Inf", k);
+      if (!(fi[k] >= 0.0 && fi[k] < nlon)) fail(ctx, DD4DV_EINVAL, "obs %lld: fi out of [0, nlon)", k);
+      if (!(fj[k] >= 0.0 && fj[k] <= nlat - 1)) fail(ctx, DD4DV_EINVAL, "obs %lld: fj out of [0, nlat-1]", k);
+      if (!(sigma_o[k] > 0.0)) fail(ctx, DD4DV_EINVAL, "obs %lld: sigma_o must be > 0", k);
+    }
+    ctx->free_dec();
+    ctx->ob_level.assign(level, level + n);
+    ctx->ob_var.assign(var, var + n);
+    ctx->ob_fi.assign(fi, fi + n);
+    ctx->ob_fj.assign(fj, fj + n);
+    ctx->ob_val.assign(value, value + n);
+    ctx->ob_so.assign(sigma_o, sigma_o + n);
+    ctx->has_obs = true;
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_set_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp* dec) {
+  return guard(ctx, [&] {
+    if (!dec) fail(ctx, DD4DV_EINVAL, "dec is NULL");
+    if (!ctx->has_bg || !ctx->has_berr || !ctx->has_obs)
+      fail(ctx, DD4DV_ESTATE, "set_background, set_background_error and set_observations must come first");
+    build_decomposition(ctx, *dec);
+    if (cudaMallocHost(&ctx->phase_h, ctx->n_sub * sizeof(int)) != cudaSuccess)
+      fail(ctx, DD4DV_ENOMEM, "pinned host allocation failed");
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_num_subdomains(const dd4dv_ctx* cctx, int* n) {
+  auto* ctx = const_cast<dd4dv_ctx*>(cctx);
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!n) fail(ctx, DD4DV_EINVAL, "n is NULL");
+    *n = ctx->n_sub;
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_control_layout(const dd4dv_ctx* cctx, long long* offsets, int* boxes) {
+  auto* ctx = const_cast<dd4dv_ctx*>(cctx);
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!offsets) fail(ctx, DD4DV_EINVAL, "offsets is NULL");
+    for (int s = 0; s < ctx->n_sub; ++s) {
+      const SubDesc& d = ctx->subs_h[s];
+      offsets[s] = d.ctrl_off;
+      if (boxes) {
+        boxes[6 * s + 0] = d.i0; boxes[6 * s + 1] = d.nx; boxes[6 * s + 2] = d.j0;
+        boxes[6 * s + 3] = d.ny; boxes[6 * s + 4] = d.a; boxes[6 * s + 5] = d.b;
+      }
+    }
+    offsets[ctx->n_sub] = ctx->ctrl_total;
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_traj_layout(const dd4dv_ctx* cctx, long long* offsets) {
+  auto* ctx = const_cast<dd4dv_ctx*>(cctx);
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!offsets) fail(ctx, DD4DV_EINVAL, "offsets is NULL");
+    for (int s = 0; s < ctx->n_sub; ++s) offsets[s] = ctx->subs_h[s].ptraj_off;
+    offsets[ctx->n_sub] = ctx->ptraj_total;
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_eval(dd4dv_ctx* ctx, const double* w_all, double* J_all, double* grad_all,
+                        double* parts, int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all || !J_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    const size_t C = ctx->ctrl_total;
+    const double* w = stage_in(ctx, w_all, ctx->io_a, C, device_ptrs);
+    double* J = device_ptrs ? J_all : ctx->io_p;
+    double* pa = device_ptrs ? parts : (parts ? ctx->io_p + ctx->n_sub : nullptr);
+    double* gr = grad_all ? (device_ptrs ? grad_all : ctx->io_b) : nullptr;
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      eval_T<T>(ctx, w, J, gr, pa, nullptr, 0, nullptr);
+      return 0;
+    });
+    ctx->fwd_pending = false;
+    if (!device_ptrs) {
+      d2h(ctx, J_all, J, ctx->n_sub * sizeof(double));
+      if (parts) d2h(ctx, parts, pa, 3 * ctx->n_sub * sizeof(double));
+      if (grad_all) d2h(ctx, grad_all, gr, C * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_eval_forward(dd4dv_ctx* ctx, const double* w_all, double* J_all, double* parts,
+                                int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all || !J_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    const size_t C = ctx->ctrl_total;
+    // keep w for the backward pass in io_c
+    if (device_ptrs) CK(cudaMemcpyAsync(ctx->io_c, w_all, C * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    else h2d(ctx, ctx->io_c, w_all, C * sizeof(double));
+    double* J = device_ptrs ? J_all : ctx->io_p;
+    double* pa = device_ptrs ? parts : (parts ? ctx->io_p + ctx->n_sub : nullptr);
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      init_states<T>(ctx, ctx->io_c, ctx->vw, nullptr, 0);
+      forward_sweep<T>(ctx, nullptr, 0);
+      KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, ctx->io_c, ctx->part, ctx->cl, ctx->vconst,
+                           ctx->dec.lambda, ctx->dec.mu, J, pa, nullptr, 0, ctx->st));
+      return 0;
+    });
+    ctx->fwd_pending = true;
+    if (!device_ptrs) {
+      d2h(ctx, J_all, J, ctx->n_sub * sizeof(double));
+      if (parts) d2h(ctx, parts, pa, 3 * ctx->n_sub * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_eval_backward(dd4dv_ctx* ctx, const double* scale, double* grad_all, int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!ctx->fwd_pending) fail(ctx, DD4DV_ESTATE, "no pending dd4dv_eval_forward");
+    if (!grad_all) fail(ctx, DD4DV_EINVAL, "grad_all is NULL");
+    const double* sc = nullptr;
+    if (scale) sc = stage_in(ctx, scale, ctx->io_p + 4 * ctx->n_sub, ctx->n_sub, device_ptrs);
+    double* gr = device_ptrs ? grad_all : ctx->io_b;
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      SweepArgs<T> a = sweep_args<T>(ctx);
+      KL(launch_adjoint<T>(a, ctx->cl, 256, ctx->st));
+      apply_VT(ctx, ctx->lam_a, ctx->io_c, sc, gr, nullptr, 0);
+      return 0;
+    });
+    ctx->fwd_pending = false;
+    if (!device_ptrs) {
+      d2h(ctx, grad_all, gr, ctx->ctrl_total * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+static double* ptraj_buf(dd4dv_ctx* ctx) {
+  if (!ctx->ptraj_io) ctx->ptraj_io = dalloc<double>(ctx, ctx->ptraj_total);
+  return ctx->ptraj_io;
+}
+
+dd4dv_status dd4dv_tlm(dd4dv_ctx* ctx, const double* w_all, const double* dw_all, double* dx_all,
+                       int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all || !dw_all || !dx_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    const size_t need = ctx->m.precision == 1 ? smem_tlm<float>(ctx->R, ctx->W) : smem_tlm<double>(ctx->R, ctx->W);
+    if (need > 232448) fail(ctx, DD4DV_EINVAL, "tangent-linear sweep needs %zu bytes of shared memory at cluster size %d; use a larger cluster", need, ctx->cl);
+    const size_t C = ctx->ctrl_total;
+    const double* w = stage_in(ctx, w_all, ctx->io_a, C, device_ptrs);
+    const double* dw = stage_in(ctx, dw_all, ctx->io_b, C, device_ptrs);
+    double* out = device_ptrs ? dx_all : ptraj_buf(ctx);
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      init_states<T>(ctx, w, ctx->vw, nullptr, 0);
+      // dx(a) = V dw into vw2
+      const double* src = dw;
+      if (ctx->corr_len > 0.0) {
+        KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, dw, nullptr, ctx->vw2, nullptr, 0, ctx->max_pts, ctx->st));
+        RFArgs ra{ctx->subs_d, ctx->n_sub, ctx->rf_alpha, ctx->rf_c, ctx->rf_passes, nullptr, 0};
+        KL(launch_rf_rows(ctx->vw2, ra, ctx->max_ny, ctx->st));
+        KL(launch_rf_cols(ctx->vw2, ra, ctx->max_nx, ctx->st));
+        src = ctx->vw2;
+      }
+      KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, src, ctx->sigma_d, ctx->io_c, nullptr, 0, ctx->max_pts, ctx->st));
+      SweepArgs<T> a = sweep_args<T>(ctx);
+      a.dx0 = ctx->io_c;
+      a.dx_out = out;
+      KL(launch_tlm<T>(a, ctx->cl, 256, ctx->st));
+      return 0;
+    });
+    ctx->fwd_pending = false;
+    if (!device_ptrs) {
+      d2h(ctx, dx_all, out, ctx->ptraj_total * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_adjoint(dd4dv_ctx* ctx, const double* w_all, const double* y_all, double* dw_all,
+                           int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all || !y_all || !dw_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    const size_t C = ctx->ctrl_total;
+    const double* w = stage_in(ctx, w_all, ctx->io_a, C, device_ptrs);
+    const double* y = device_ptrs ? y_all : nullptr;
+    if (!device_ptrs) {
+      double* b = ptraj_buf(ctx);
+      h2d(ctx, b, y_all, ctx->ptraj_total * sizeof(double));
+      y = b;
+    }
+    double* out = device_ptrs ? dw_all : ctx->io_b;
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      init_states<T>(ctx, w, ctx->vw, nullptr, 0);
+      forward_sweep<T>(ctx, nullptr, 0);
+      SweepArgs<T> a = sweep_args<T>(ctx);
+      a.yforce = y;
+      KL(launch_adjoint<T>(a, ctx->cl, 256, ctx->st));
+      apply_VT(ctx, ctx->lam_a, nullptr, nullptr, out, nullptr, 0);
+      return 0;
+    });
+    ctx->fwd_pending = false;
+    if (!device_ptrs) {
+      d2h(ctx, dw_all, out, C * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_trajectories(dd4dv_ctx* ctx, const double* w_all, double* traj_all, int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all || !traj_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    const double* w = stage_in(ctx, w_all, ctx->io_a, ctx->ctrl_total, device_ptrs);
+    double* out = device_ptrs ? traj_all : ptraj_buf(ctx);
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      init_states<T>(ctx, w, ctx->vw, nullptr, 0);
+      forward_sweep<T>(ctx, nullptr, 0);
+      KL(launch_export_traj<T>(ctx->subs_d, ctx->n_sub, static_cast<const T*>(ctx->traj), h_ref_of(ctx),
+                               out, ctx->max_pts, ctx->max_levels, ctx->st));
+      return 0;
+    });
+    ctx->fwd_pending = false;
+    if (!device_ptrs) {
+      d2h(ctx, traj_all, out, ctx->ptraj_total * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_exchange(dd4dv_ctx* ctx, const double* w_all, int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    const double* w = stage_in(ctx, w_all, ctx->io_a, ctx->ctrl_total, device_ptrs);
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      exchange_T<T>(ctx, w);
+      return 0;
+    });
+    if (!device_ptrs) sync(ctx);
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_reset_exchange(dd4dv_ctx* ctx) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      reset_exchange_T<T>(ctx);
+      return 0;
+    });
+    sync(ctx);
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_boundary_trajectory(dd4dv_ctx* ctx, double* traj, int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!traj) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    double* out = device_ptrs ? traj : ctx->gtraj_io;
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      KL(launch_bnd_to_global<T>(static_cast<const T*>(ctx->bnd), (long long)ctx->gtraj, h_ref_of(ctx),
+                                 ctx->m.nlon, ctx->m.nlat, out, ctx->st));
+      return 0;
+    });
+    if (!device_ptrs) {
+      d2h(ctx, traj, out, ctx->gtraj * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_analysis(dd4dv_ctx* ctx, double* xa0, int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!xa0) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    double* out = device_ptrs ? xa0 : ctx->gtraj_io;
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      KL(launch_bnd_to_global<T>(static_cast<const T*>(ctx->bnd), (long long)ctx->gstate, h_ref_of(ctx),
+                                 ctx->m.nlon, ctx->m.nlat, out, ctx->st));
+      return 0;
+    });
+    if (!device_ptrs) {
+      d2h(ctx, xa0, out, ctx->gstate * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_forward(dd4dv_ctx* ctx, const double* x0, double* traj, int device_ptrs) {
+  return guard(ctx, [&] {
+    if (!x0 || !traj) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    double* out = device_ptrs ? traj : ctx->gtraj_io;
+    const double* in = x0;
+    if (!device_ptrs) {
+      if (!all_finite(x0, ctx->gstate)) fail(ctx, DD4DV_ENONFINITE, "x0 contains NaN or Inf");
+      h2d(ctx, ctx->gtraj_io, x0, ctx->gstate * sizeof(double));
+      in = ctx->gtraj_io;
+    }
+    global_run(ctx, in, out);
+    if (!device_ptrs) {
+      d2h(ctx, traj, out, ctx->gtraj * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_observe(dd4dv_ctx* ctx, const double* traj, long long n, const int* level,
+                           const int* var, const double* fi, const double* fj, double* out,
+                           int device_ptrs) {
+  return guard(ctx, [&] {
+    if (n < 0) fail(ctx, DD4DV_EINVAL, "n < 0");
+    if (n == 0) return DD4DV_OK;
+    if (!traj || !level || !var || !fi || !fj || !out) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    if (device_ptrs) {
+      KL(launch_observe(traj, n, level, var, fi, fj, ctx->m.nlon, ctx->m.nlat, out, ctx->st));
+      return DD4DV_OK;
+    }
+    for (long long k = 0; k < n; ++k) {
+      if (level[k] < 0 || level[k] > ctx->m.nsteps || var[k] < 0 || var[k] > 2 || !(fi[k] >= 0.0) ||
+          !(fi[k] < ctx->m.nlon) || !(fj[k] >= 0.0) || !(fj[k] <= ctx->m.nlat - 1))
+        fail(ctx, DD4DV_EINVAL, "observation site %lld out of range", k);
+    }
+    std::vector<void*> tmp;
+    try {
+      double* dt = dalloc<double>(ctx, ctx->gtraj, &tmp);
+      int* dl = dalloc<int>(ctx, n, &tmp);
+      int* dv = dalloc<int>(ctx, n, &tmp);
+      double* dfi = dalloc<double>(ctx, n, &tmp);
+      double* dfj = dalloc<double>(ctx, n, &tmp);
+      double* dout = dalloc<double>(ctx, n, &tmp);
+      h2d(ctx, dt, traj, ctx->gtraj * sizeof(double));
+      h2d(ctx, dl, level, n * sizeof(int));
+      h2d(ctx, dv, var, n * sizeof(int));
+      h2d(ctx, dfi, fi, n * sizeof(double));
+      h2d(ctx, dfj, fj, n * sizeof(double));
+      KL(launch_observe(dt, n, dl, dv, dfi, dfj, ctx->m.nlon, ctx->m.nlat, dout, ctx->st));
+      d2h(ctx, out, dout, n * sizeof(double));
+      sync(ctx);
+    } catch (...) {
+      for (void* p : tmp) cudaFree(p);
+      throw;
+    }
+    for (void* p : tmp) cudaFree(p);
+    return DD4DV_OK;
+  });
+}
+
+static void check_solver(dd4dv_ctx* ctx, const dd4dv_solver* s) {
+  if (!s) fail(ctx, DD4DV_EINVAL, "solver is NULL");
+  if (s->lbfgs_m < 1 || s->lbfgs_m > 8) fail(ctx, DD4DV_EINVAL, "lbfgs_m must be 1..8");
+  if (s->max_local_iters < 0 || s->max_trials < 1 || s->max_outer < 0) fail(ctx, DD4DV_EINVAL, "bad iteration limits");
+  if (!(s->c1 > 0.0 && s->c1 < 1.0)) fail(ctx, DD4DV_EINVAL, "c1 must be in (0,1)");
+  if (!(s->gtol_rel >= 0.0) || !(s->eps_outer >= 0.0)) fail(ctx, DD4DV_EINVAL, "tolerances must be >= 0");
+}
+
+}  // extern "C"
+
+template <typename T>
+static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* stats) {
+  LbArgs la{};
+  la.subs = ctx->subs_d;
+  la.n_sub = ctx->n_sub;
+  la.w = ctx->w;
+  la.g = ctx->g;
+  la.wt = ctx->wt;
+  la.gt = ctx->gt;
+  la.p = ctx->p;
+  la.S = ctx->S;
+  la.Y = ctx->Y;
+  la.rho = ctx->rho;
+  la.total = ctx->ctrl_total;
+  la.st = ctx->lbst;
+  la.m = sv.lbfgs_m;
+  la.max_iter = sv.max_local_iters;
+  la.max_trials = sv.max_trials;
+  la.gtol = sv.gtol_rel;
+  la.c1 = sv.c1;
+  la.counter = ctx->counter_d;
+  la.phase = ctx->phase_d;
+  long long evals = 0, sub_evals = 0, pts = 0;
+  // evaluation at the starting point of every local problem
+  eval_T<T>(ctx, ctx->w, ctx->J, ctx->g, nullptr, nullptr, 0, nullptr);
+  ++evals;
+  sub_evals += ctx->n_sub;
+  pts += ctx->pt_steps;
+  la.J_eval = ctx->J;
+  KL(launch_lb_start(la, ctx->st));
+  la.J_eval = ctx->Jt;
+  std::vector<long long> sub_pts(ctx->n_sub);
+  for (int s = 0; s < ctx->n_sub; ++s) {
+    const SubDesc& d = ctx->subs_h[s];
+    sub_pts[s] = (long long)d.nx * d.ny * (d.b - d.a);
+  }
+  const int guard_iters = sv.max_local_iters + 2;
+  for (int it = 0; it < guard_iters; ++it) {
+    CK(cudaMemsetAsync(ctx->counter_d, 0, 2 * sizeof(int), ctx->st));
+    KL(launch_lb_direction(la, ctx->st));
+    d2h(ctx, ctx->counter_h, ctx->counter_d, 2 * sizeof(int));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (ctx->counter_h[0] == 0) break;
+    for (int tr = 0; tr < sv.max_trials; ++tr) {
+      d2h(ctx, ctx->phase_h, ctx->phase_d, ctx->n_sub * sizeof(int));
+      eval_T<T>(ctx, ctx->wt, ctx->Jt, ctx->gt, nullptr, ctx->phase_d, 1, nullptr);
+      CK(cudaMemsetAsync(ctx->counter_d, 0, 2 * sizeof(int), ctx->st));
+      KL(launch_lb_linesearch(la, ctx->st));
+      d2h(ctx, ctx->counter_h, ctx->counter_d, 2 * sizeof(int));
+      CK(cudaStreamSynchronize(ctx->st));
+      ++evals;
+      for (int s = 0; s < ctx->n_sub; ++s)
+        if (ctx->phase_h[s] == 1) {
+          ++sub_evals;
+          pts += sub_pts[s];
+        }
+      if (ctx->counter_h[0] == 0) break;
+    }
+  }
+  // Exchange at the new local solutions, outer increment, next start point
+  exchange_T<T>(ctx, ctx->w);
+  KL(launch_max_abs_diff(ctx->w, ctx->w_prev, ctx->ctrl_total, ctx->scal_d, ctx->st));
+  CK(cudaMemcpyAsync(ctx->w_prev, ctx->w, ctx->ctrl_total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  d2h(ctx, ctx->scal_h, ctx->scal_d, sizeof(double));
+  std::vector<LbState> lst(ctx->n_sub);
+  std::vector<double> Jh(ctx->n_sub);
+  d2h(ctx, lst.data(), ctx->lbst, ctx->n_sub * sizeof(LbState));
+  sync(ctx);
+  if (stats) {
+    stats->outer_iters += 1;
+    stats->evals += evals;
+    stats->sub_evals += sub_evals;
+    stats->pt_steps += pts;
+    stats->dw_inf = ctx->scal_h[0];
+    double Js = 0.0, gmax = 0.0;
+    int fails = 0;
+    for (const LbState& s : lst) {
+      Js += s.J;
+      if (s.g0n > 0.0) gmax = std::max(gmax, s.gn / s.g0n);
+      if (s.status == 3) ++fails;
+    }
+    stats->J_sum = Js;
+    stats->gnorm_rel_max = gmax;
+    stats->n_linesearch_fail += fails;
+  }
+}
+
+extern "C" {
+
+dd4dv_status dd4dv_outer_step(dd4dv_ctx* ctx, const dd4dv_solver* solver, dd4dv_stats* stats) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    check_solver(ctx, solver);
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      outer_step_T<T>(ctx, *solver, stats);
+      return 0;
+    });
+    ctx->fwd_pending = false;
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_run(dd4dv_ctx* ctx, const dd4dv_solver* solver, double* xa0, dd4dv_stats* stats) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    check_solver(ctx, solver);
+    dd4dv_stats local{};
+    dd4dv_stats* stp = stats ? stats : &local;
+    std::memset(stp, 0, sizeof(*stp));
+    bool conv = false;
+    for (int l = 0; l < solver->max_outer; ++l) {
+      by_precision(ctx, [&](auto t) {
+        using T = decltype(t);
+        outer_step_T<T>(ctx, *solver, stp);
+        return 0;
+      });
+      if (stp->dw_inf < solver->eps_outer) {
+        conv = true;
+        break;
+      }
+    }
+    ctx->fwd_pending = false;
+    if (xa0) {
+      by_precision(ctx, [&](auto t) {
+        using T = decltype(t);
+        KL(launch_bnd_to_global<T>(static_cast<const T*>(ctx->bnd), (long long)ctx->gstate, h_ref_of(ctx),
+                                   ctx->m.nlon, ctx->m.nlat, ctx->gtraj_io, ctx->st));
+        return 0;
+      });
+      d2h(ctx, xa0, ctx->gtraj_io, ctx->gstate * sizeof(double));
+      sync(ctx);
+    }
+    return conv ? DD4DV_OK : DD4DV_NOTCONV;
+  });
+}
+
+dd4dv_status dd4dv_get_controls(dd4dv_ctx* ctx, double* w_all, int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    CK(cudaMemcpyAsync(w_all, ctx->w, ctx->ctrl_total * sizeof(double),
+                       device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, ctx->st));
+    if (!device_ptrs) sync(ctx);
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_set_controls(dd4dv_ctx* ctx, const double* w_all, int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    if (!device_ptrs && !all_finite(w_all, ctx->ctrl_total)) fail(ctx, DD4DV_ENONFINITE, "controls contain NaN or Inf");
+    const auto kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->w, w_all, ctx->ctrl_total * sizeof(double), kind, ctx->st));
+    CK(cudaMemcpyAsync(ctx->w_prev, w_all, ctx->ctrl_total * sizeof(double), kind, ctx->st));
+    sync(ctx);
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_pt_steps(const dd4dv_ctx* cctx, long long* n) {
+  auto* ctx = const_cast<dd4dv_ctx*>(cctx);
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!n) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    *n = ctx->pt_steps;
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_launch_count(const dd4dv_ctx* ctx, long long* n) {
+  if (!ctx || !n) return DD4DV_EINVAL;
+  *n = ctx->launches;
+  return DD4DV_OK;
+}
+
+dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* cctx, int* n) {
+  auto* ctx = const_cast<dd4dv_ctx*>(cctx);
+  if (!ctx || !n) return DD4DV_EINVAL;
+  if (!ctx->has_dec) return DD4DV_ESTATE;
+  *n = ctx->cl;
+  return DD4DV_OK;
+}
+
+}  // extern "C"

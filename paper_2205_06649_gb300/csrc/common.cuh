@@ -1,0 +1,186 @@
+// Internal declarations of the DD-4DVar GB300 library (not part of the C ABI).
+//
+// Device data layout (HBM):
+//   * per-subdomain trajectories: traj[s] = [L+1 levels][3 vars][ny rows][nxp],
+//     state type T (double, or float with h stored as h - h_ref), row pitch
+//     nxp = nx rounded up to a multiple of 4 so every row starts on a 32-byte
+//     boundary; subdomains are packed one after another (SubDesc::traj_off);
+//   * overlap targets tgt[s]: same shape, the mean of the neighbours' values
+//     at every point the subdomain shares with others (zero elsewhere);
+//   * boundary trajectory bnd = [nsteps+1][3][nlat][nlon] (type T), the
+//     partition-of-unity sum of the local trajectories (Eq. rest);
+//   * controls, gradients, L-BFGS vectors: packed FP64 [3][ny][nx] per
+//     subdomain (SubDesc::ctrl_off).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace dd4dv {
+
+enum { F_PERIODIC = 1, F_SWALL = 2, F_NWALL = 4 };
+
+struct SubDesc {
+  int i0, nx, j0, ny, a, b;   // box [i0, i0+nx) (lon, mod nlon) x [j0, j0+ny), levels [a, b]
+  int nxp;                    // trajectory row pitch (elements)
+  int flags;                  // F_PERIODIC | F_SWALL | F_NWALL
+  int q, p2, p1;              // block coordinates
+  int wL, wR, wS, wN;         // overlap band widths: lon west/east, lat south/north
+  int tA, tB;                 // overlap level counts at window start / end
+  int obs_lvl;                // first entry of this subdomain in lvl_obs (L+2 entries)
+  int sc_lvl;                 // first entry in lvl_sc (L+2 entries)
+  long long ctrl_off;         // packed control offset (doubles)
+  long long traj_off;         // trajectory offset (elements of T)
+  long long ptraj_off;        // packed public trajectory offset (doubles, pitch nx)
+};
+
+struct ObsRec {               // one observation as seen by one subdomain
+  int var, r0, k0, k1;        // local lower corner row/col, east corner col (wrapped)
+  double di, dj;              // fractional offsets (0 = corner not used)
+  double y;                   // observed value (h: minus h_ref on the FP32 path)
+  double w;                   // omega / sigma_o^2
+};
+
+struct RowConst {             // per global latitude row j
+  double A;                   // 1 / (2 a cos(theta_j) dlambda)
+  double f;                   // 2 Omega sin(theta_j)
+  double tau;                 // tan(theta_j) / a
+  double c;                   // cos(theta_j)
+  double BinvC;               // Bth / cos(theta_j)
+  double gA;                  // g A
+};
+
+// Arguments shared by the sweep kernels (forward, adjoint, tangent-linear).
+template <typename T>
+struct SweepArgs {
+  const SubDesc* subs;
+  const int* order;           // cluster -> subdomain (longest first)
+  int n_sub;
+  T* traj;
+  const T* tgt;
+  const T* bnd;
+  const RowConst* rows;       // [nlat]
+  double Bth, gBth, dt, h_ref;
+  int nlon, nlat, nsteps;
+  double isb2[3];             // 1 / sigma_b^2 per variable
+  double lam, mu;
+  const ObsRec* obs;          // per-subdomain, per-level sorted
+  const int* lvl_obs;         // obs ranges per (subdomain, level)
+  double* obs_force;          // lambda * omega * d / sigma_o^2 per obs record
+  const int* sc_tgt;          // adjoint scatter targets: var*ny*nx + r*nx + k
+  const int* sc_off;          // contributions of each target
+  const int* sc_obs;
+  const double* sc_w;
+  const int* lvl_sc;          // target ranges per (subdomain, level)
+  double* part;               // [n_sub][cl_max][2] partial J_o, J_mu
+  int cl_max;
+  const int* active;          // per-subdomain mask (phase == active_value), or nullptr
+  int active_value;
+  double* lam_a;              // adjoint state at level a, packed control layout
+  const double* yforce;       // external adjoint forcing (packed FP64 trajectories) or nullptr
+  double* dx_out;             // tangent-linear output (packed FP64 trajectories)
+  const double* dx0;          // tangent-linear initial perturbation (packed control layout)
+  int R;                      // max rows per CTA
+  int W;                      // shared-memory row pitch (>= max nx + 2)
+  int* err;                   // device error word (0 = ok)
+};
+
+// ---- launchers (sweep.cu) ----
+template <typename T> cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);
+template <typename T> cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);
+template <typename T> cudaError_t launch_tlm(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);
+template <typename T> size_t smem_forward(int R, int W);
+template <typename T> size_t smem_adjoint(int R, int W);
+template <typename T> size_t smem_tlm(int R, int W);
+// resident CTAs per SM of the adjoint sweep (the largest of the three)
+template <typename T> int occupancy_adjoint(int R, int W, int nthreads);
+
+// ---- auxiliary kernels (aux.cu) ----
+struct RFArgs {
+  const SubDesc* subs; int n_sub;
+  double alpha, c; int npass;
+  const int* active; int active_value;
+};
+// in place: lines along lon (rows) or lat (columns) of each [3][ny][nx] block
+cudaError_t launch_rf_rows(double* x, const RFArgs& a, int max_ny, cudaStream_t st);
+cudaError_t launch_rf_cols(double* x, const RFArgs& a, int max_nx, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_init_state(const SubDesc* subs, int n_sub, const double* xb_a, const double* vw,
+                              const double* sigma, int scale_sigma, double h_ref, T* traj,
+                              const int* active, int active_value, int max_pts, cudaStream_t st);
+cudaError_t launch_scale_copy(const SubDesc* subs, int n_sub, const double* in, const double* sigma,
+                              double* out, const int* active, int active_value, int max_pts,
+                              cudaStream_t st);
+cudaError_t launch_grad_finish(const SubDesc* subs, int n_sub, const double* w, const double* vty,
+                               const double* scale, double* grad, const int* active,
+                               int active_value, int max_pts, cudaStream_t st);
+cudaError_t launch_finalize_J(const SubDesc* subs, int n_sub, const double* w, const double* part,
+                              int cl_max, const double* vconst, double lam, double mu, double* J,
+                              double* parts, const int* active, int active_value, cudaStream_t st);
+
+template <typename T>
+struct ExchArgs {
+  const SubDesc* subs; int n_sub;
+  int P1, P2, Q;
+  int nlon, nlat, nsteps;
+  const T* traj; T* tgt; T* bnd;
+  double isb2[3];
+  double* vpart;              // [n_sub][blocks] partial sums of the overlap constant
+  int vblocks;
+  const int* lon_cov;         // [nlon][2][2] (p1, local col) or -1
+  const int* lat_cov;         // [nlat][2][2]
+  const int* t_cov;           // [nsteps+1][2][2]
+};
+template <typename T> cudaError_t launch_targets(const ExchArgs<T>& a, cudaStream_t st);
+template <typename T> cudaError_t launch_assemble(const ExchArgs<T>& a, cudaStream_t st);
+cudaError_t launch_sum_vconst(const double* vpart, int n_sub, int vblocks, double* vconst, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_restrict(const SubDesc* subs, int n_sub, int nlon, int nlat, const double* glob,
+                            double h_ref, T* traj, int max_pts, int max_levels, cudaStream_t st);
+template <typename T>
+cudaError_t launch_export_traj(const SubDesc* subs, int n_sub, const T* traj, double h_ref,
+                               double* out, int max_pts, int max_levels, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bnd_from_global(const double* glob, long long n, double h_ref, int nlon, int nlat,
+                                   T* bnd, cudaStream_t st);
+template <typename T>
+cudaError_t launch_bnd_to_global(const T* bnd, long long n, double h_ref, int nlon, int nlat,
+                                 double* glob, cudaStream_t st);
+cudaError_t launch_restrict_level(const SubDesc* subs, int n_sub, int nlon, int nlat,
+                                  const double* glob_traj, double* xb_a, int max_pts, cudaStream_t st);
+
+// global model (whole sphere), FP64
+cudaError_t launch_global_stage(const double* x, const double* y, double* out, double ca, double cb,
+                                const RowConst* rows, double Bth, double gBth, double dt, int nlon,
+                                int nlat, cudaStream_t st);
+cudaError_t launch_observe(const double* traj, long long n, const int* level, const int* var,
+                           const double* fi, const double* fj, int nlon, int nlat, double* out,
+                           cudaStream_t st);
+
+// L-BFGS (batched, one block per subdomain)
+struct LbState {
+  double J, Jt, gp, alpha, g0n, gn;
+  int head, count, iter, trial, phase, status;
+};
+struct LbArgs {
+  const SubDesc* subs; int n_sub;
+  double* w; double* g; double* wt; double* gt; double* p;
+  double* S; double* Y; double* rho;   // [m][total], [m][total], [n_sub][m]
+  long long total;
+  LbState* st;
+  const double* J_eval;                // J of the last evaluation
+  int m, max_iter, max_trials;
+  double gtol, c1;
+  int* counter;                        // [2]: # in line search, # needing a direction
+  int* phase;                          // [n_sub] mirror of LbState::phase (sweep masks)
+};
+cudaError_t launch_lb_start(const LbArgs& a, cudaStream_t st);
+cudaError_t launch_lb_direction(const LbArgs& a, cudaStream_t st);
+cudaError_t launch_lb_linesearch(const LbArgs& a, cudaStream_t st);
+cudaError_t launch_max_abs_diff(const double* a, const double* b, long long n, double* out,
+                                cudaStream_t st);
+cudaError_t launch_finite_check(const double* a, long long n, int* flag, cudaStream_t st);
+
+}  // namespace dd4dv

@@ -1,0 +1,829 @@
+// Forward, adjoint and tangent-linear sweeps of the local shallow-water model
+// over every subdomain's time window, batched in one launch each.
+//
+// Design (GB300, sm_103a): one thread-block cluster per subdomain.  The
+// cluster's CTAs split the subdomain's box into horizontal stripes of rows;
+// each CTA keeps its stripe of the state (plus one halo row on each side and
+// a ghost column on each side) resident in shared memory for the whole time
+// window.  After every RK3 stage the CTAs barrier on the cluster and read
+// their neighbours' edge rows through distributed shared memory
+// (ld.shared::cluster via cooperative_groups::cluster_group::map_shared_rank),
+// so the only HBM traffic of a step is the trajectory store (forward), the
+// trajectory load (adjoint), ghost values of the frozen boundary trajectory
+// and the sparse observation / overlap data.  Clusters are ordered longest
+// subdomain first (uneven sizes in one launch).
+//
+// Mathematics (paper arXiv 2205.06649):
+//   model      Sec. 7 Eqs. EquU-EquH, centred differences, flux-form
+//              continuity; SSP-RK3 time stepping
+//   J terms    Sec. 3.3 Eq. eq:cost:parallel1 (observation misfit and overlap
+//              penalty per level; the background term is in aux.cu)
+//   adjoint    Alg. 6 (ADJ), the reversed product of step adjoints Eq. adjProd,
+//              derived by hand from the discrete forward step
+//   TLM        Alg. 6 (TLM), the linearised forward step.
+#include "common.cuh"
+
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
+namespace dd4dv {
+
+namespace {
+
+template <typename T>
+struct Geo {
+  int s, rank, CL, R0, Rn, nx, ny, L, a, R2, W, P, flags;
+  int Rprev, Rnext;   // own-row counts of the south / north neighbour CTA
+  SubDesc d;
+};
+
+__device__ __forceinline__ void split_rows(int ny, int CL, int rank, int& R0, int& Rn) {
+  const int base = ny / CL, rem = ny % CL;
+  R0 = rank * base + min(rank, rem);
+  Rn = base + (rank < rem ? 1 : 0);
+}
+
+template <typename T>
+__device__ __forceinline__ int off(const Geo<T>& g, int v, int rr, int k) {
+  return (v * g.R2 + rr + 1) * g.W + k + 1;
+}
+
+// Per-row constants staged in shared memory for rows rr = -1 .. Rn (index rr+1).
+template <typename T>
+struct RowSmem {
+  T *A, *f, *tau, *BinvC, *gA, *c, *ic, *BcC;
+};
+
+template <typename T>
+__device__ void load_rows(const SweepArgs<T>& a, const Geo<T>& g, RowSmem<T>& rs) {
+  for (int i = threadIdx.x; i < g.Rn + 2; i += blockDim.x) {
+    const int j = g.d.j0 + g.R0 + i - 1;
+    const int jc = min(max(j, 0), a.nlat - 1);       // wall ghost rows mirror cos
+    const RowConst rc = a.rows[jc];
+    rs.A[i] = (T)rc.A;
+    rs.f[i] = (T)rc.f;
+    rs.tau[i] = (T)rc.tau;
+    rs.BinvC[i] = (T)rc.BinvC;
+    rs.gA[i] = (T)rc.gA;
+    rs.c[i] = (T)rc.c;
+    rs.ic[i] = (T)(1.0 / rc.c);
+    rs.BcC[i] = (T)(a.Bth * rc.c);
+  }
+}
+
+// Buffer kinds for halo / ghost completion.
+enum { K_STATE = 0, K_ADJ = 1, K_DELTA = 2 };
+
+// Boundary-trajectory value for variable v at global (j, i) blended between
+// levels nA and nB with weights wA, wB.
+template <typename T>
+__device__ __forceinline__ T bnd_val(const SweepArgs<T>& a, int nA, int nB, T wA, T wB, int v, int j,
+                                     int i) {
+  const size_t plane = (size_t)a.nlat * a.nlon;
+  const size_t o = ((size_t)v * a.nlat + j) * a.nlon + i;
+  const T xa = a.bnd[(size_t)nA * 3 * plane + o];
+  if (wB == (T)0) return xa;
+  const T xb = a.bnd[(size_t)nB * 3 * plane + o];
+  return wA * xa + wB * xb;
+}
+
+// Complete a buffer whose own rows were just written by this CTA: cluster
+// barrier, halo rows from the neighbour CTAs (DSMEM) or from the box-edge rule
+// (wall mirror, frozen boundary trajectory, or zero), ghost columns of the own
+// rows (periodic wrap, boundary trajectory, or zero), CTA barrier.
+template <typename T>
+__device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const Geo<T>& g, T* X,
+                             int kind, int nA, int nB, T wA, T wB) {
+  cl.sync();
+  const int nx = g.nx;
+  const bool periodic = g.flags & F_PERIODIC;
+  // halo rows
+  const T* south_nb = (g.rank > 0) ? cl.map_shared_rank(X, g.rank - 1) : nullptr;
+  const T* north_nb = (g.rank < g.CL - 1) ? cl.map_shared_rank(X, g.rank + 1) : nullptr;
+  for (int idx = threadIdx.x; idx < 2 * 3 * nx; idx += blockDim.x) {
+    const int side = idx / (3 * nx);
+    const int rem = idx - side * 3 * nx;
+    const int v = rem / nx;
+    const int k = rem - v * nx;
+    T val;
+    if (side == 0) {   // south halo rr = -1
+      if (south_nb) {
+        val = south_nb[off(g, v, g.Rprev - 1, k)];
+      } else if (g.flags & F_SWALL) {
+        val = (kind == K_ADJ) ? (T)0 : ((v == 2) ? -X[off(g, v, 0, k)] : X[off(g, v, 0, k)]);
+      } else {
+        val = (kind == K_STATE)
+                  ? bnd_val(a, nA, nB, wA, wB, v, g.d.j0 - 1, (g.d.i0 + k) % a.nlon)
+                  : (T)0;
+      }
+      X[off(g, v, -1, k)] = val;
+    } else {           // north halo rr = Rn
+      if (north_nb) {
+        val = north_nb[off(g, v, 0, k)];
+      } else if (g.flags & F_NWALL) {
+        val = (kind == K_ADJ) ? (T)0
+                              : ((v == 2) ? -X[off(g, v, g.Rn - 1, k)] : X[off(g, v, g.Rn - 1, k)]);
+      } else {
+        val = (kind == K_STATE)
+                  ? bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.ny, (g.d.i0 + k) % a.nlon)
+                  : (T)0;
+      }
+      X[off(g, v, g.Rn, k)] = val;
+    }
+  }
+  // ghost columns of own rows
+  for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
+    const int side = idx / (3 * g.Rn);
+    const int rem = idx - side * 3 * g.Rn;
+    const int v = rem / g.Rn;
+    const int rr = rem - v * g.Rn;
+    T val;
+    if (periodic) {
+      val = side == 0 ? X[off(g, v, rr, nx - 1)] : X[off(g, v, rr, 0)];
+    } else if (kind == K_STATE) {
+      const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + nx) % a.nlon;
+      val = bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.R0 + rr, i);
+    } else {
+      val = (T)0;
+    }
+    X[off(g, v, rr, side == 0 ? -1 : nx)] = val;
+  }
+  __syncthreads();
+}
+
+// Load level l of this subdomain's stored trajectory into X (own rows and
+// interior halo rows straight from HBM, box-edge halos by rule), ghosts at
+// boundary level n.  Ends with a CTA barrier.
+template <typename T>
+__device__ void load_level(const SweepArgs<T>& a, const Geo<T>& g, T* X, int l, int n) {
+  const int nx = g.nx;
+  const T* src = a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp;
+  const int r_lo = (g.rank > 0) ? -1 : 0;
+  const int r_hi = (g.rank < g.CL - 1) ? g.Rn + 1 : g.Rn;
+  const int nr = r_hi - r_lo;
+  for (int idx = threadIdx.x; idx < 3 * nr * nx; idx += blockDim.x) {
+    const int v = idx / (nr * nx);
+    const int rem = idx - v * nr * nx;
+    const int rr = rem / nx + r_lo;
+    const int k = rem - (rr - r_lo) * nx;
+    X[off(g, v, rr, k)] = src[((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k];
+  }
+  __syncthreads();
+  const bool periodic = g.flags & F_PERIODIC;
+  if (g.rank == 0) {
+    for (int idx = threadIdx.x; idx < 3 * nx; idx += blockDim.x) {
+      const int v = idx / nx, k = idx - v * nx;
+      X[off(g, v, -1, k)] = (g.flags & F_SWALL)
+                                ? ((v == 2) ? -X[off(g, v, 0, k)] : X[off(g, v, 0, k)])
+                                : bnd_val(a, n, n, (T)1, (T)0, v, g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
+    }
+  }
+  if (g.rank == g.CL - 1) {
+    for (int idx = threadIdx.x; idx < 3 * nx; idx += blockDim.x) {
+      const int v = idx / nx, k = idx - v * nx;
+      X[off(g, v, g.Rn, k)] =
+          (g.flags & F_NWALL)
+              ? ((v == 2) ? -X[off(g, v, g.Rn - 1, k)] : X[off(g, v, g.Rn - 1, k)])
+              : bnd_val(a, n, n, (T)1, (T)0, v, g.d.j0 + g.ny, (g.d.i0 + k) % a.nlon);
+    }
+  }
+  for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
+    const int side = idx / (3 * g.Rn);
+    const int rem = idx - side * 3 * g.Rn;
+    const int v = rem / g.Rn;
+    const int rr = rem - v * g.Rn;
+    T val;
+    if (periodic) {
+      val = side == 0 ? X[off(g, v, rr, nx - 1)] : X[off(g, v, rr, 0)];
+    } else {
+      const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + nx) % a.nlon;
+      val = bnd_val(a, n, n, (T)1, (T)0, v, g.d.j0 + g.R0 + rr, i);
+    }
+    X[off(g, v, rr, side == 0 ? -1 : nx)] = val;
+  }
+  __syncthreads();
+}
+
+// Tendencies F(Z) at one point (Sec. 7, centred differences):
+//   F_u = -A u (uE-uW) - Bth v (uN-uS) + (f + tau u) v - gA (hE-hW)
+//   F_v = -A u (vE-vW) - Bth v (vN-vS) - (f + tau u) u - gBth (hN-hS)
+//   F_h = -A ((hu)_E - (hu)_W) - (Bth/c) ((h v c)_N - (h v c)_S)
+// On the FP32 path h = h_ref + h' and the h_ref parts of the fluxes are
+// formed from velocity differences.
+template <typename T, bool DEV>
+__device__ __forceinline__ void rhs_pt(const T* Z, int o, int P, int W, T A, T f, T tau, T BinvC,
+                                       T gA, T cN, T cS, T Bth, T gBth, T href, T& Fh, T& Fu,
+                                       T& Fv) {
+  const T* H = Z;
+  const T* U = Z + P;
+  const T* V = Z + 2 * P;
+  const T u = U[o], v = V[o];
+  const T uE = U[o + 1], uW = U[o - 1], uN = U[o + W], uS = U[o - W];
+  const T vE = V[o + 1], vW = V[o - 1], vN = V[o + W], vS = V[o - W];
+  const T hE = H[o + 1], hW = H[o - 1], hN = H[o + W], hS = H[o - W];
+  const T fu = f + tau * u;
+  Fu = -A * u * (uE - uW) - Bth * v * (uN - uS) + fu * v - gA * (hE - hW);
+  Fv = -A * u * (vE - vW) - Bth * v * (vN - vS) - fu * u - gBth * (hN - hS);
+  T flx = hE * uE - hW * uW;
+  T fly = hN * vN * cN - hS * vS * cS;
+  if (DEV) {
+    flx += href * (uE - uW);
+    fly += href * (vN * cN - vS * cS);
+  }
+  Fh = -A * flx - BinvC * fly;
+}
+
+// Adjoint of the tendencies: G = F'(Z)^T M at one point (derived by hand from
+// rhs_pt; M holds zero at ghost points that carry no tendency).  Wall rows add
+// the transposed ghost mirror (h, u, -v) of the edge row.
+template <typename T, bool DEV>
+__device__ __forceinline__ void rhs_adj_pt(const T* Z, const T* M, int o, int P, int W, T A, T f,
+                                           T tau, T gA, T BcC, T icN, T icS, T Bth, T gBth, T href,
+                                           int wall, T& Gh, T& Gu, T& Gv) {
+  const T* H = Z;
+  const T* U = Z + P;
+  const T* V = Z + 2 * P;
+  const T* mH = M;
+  const T* mU = M + P;
+  const T* mV = M + 2 * P;
+  T h = H[o];
+  if (DEV) h += href;
+  const T u = U[o], v = V[o];
+  const T uE = U[o + 1], uW = U[o - 1], uN = U[o + W], uS = U[o - W];
+  const T vE = V[o + 1], vW = V[o - 1], vN = V[o + W], vS = V[o - W];
+  const T mu = mU[o], mv = mV[o], mh = mH[o];
+  const T muE = mU[o + 1], muW = mU[o - 1], muN = mU[o + W], muS = mU[o - W];
+  const T mvE = mV[o + 1], mvW = mV[o - 1], mvN = mV[o + W], mvS = mV[o - W];
+  const T mhE = mH[o + 1], mhW = mH[o - 1], mhN = mH[o + W], mhS = mH[o - W];
+  const T dmhEW = mhE - mhW;
+  const T dmhNS = mhN * icN - mhS * icS;
+  Gu = mu * (tau * v - A * (uE - uW)) - mv * (A * (vE - vW) + f + (T)2 * tau * u) +
+       A * (muE * uE - muW * uW) + A * h * dmhEW + Bth * (muN * vN - muS * vS);
+  Gv = mu * (f + tau * u - Bth * (uN - uS)) - mv * (Bth * (vN - vS)) + A * (mvE * uE - mvW * uW) +
+       Bth * (mvN * vN - mvS * vS) + BcC * h * dmhNS;
+  Gh = gA * (muE - muW) + gBth * (mvN - mvS) + A * u * dmhEW + BcC * v * dmhNS;
+  if (wall == 1) {         // south wall: ghost row = (h, u, -v) of this row
+    Gu += Bth * mu * v;
+    Gv -= Bth * (mv * v + h * mh);
+    Gh += gBth * mv - Bth * v * mh;
+  } else if (wall == 2) {  // north wall
+    Gu -= Bth * mu * v;
+    Gv += Bth * (mv * v + h * mh);
+    Gh += Bth * v * mh - gBth * mv;
+  }
+}
+
+// Tangent-linear tendencies dF = F'(Z) dZ at one point.
+template <typename T, bool DEV>
+__device__ __forceinline__ void rhs_tl_pt(const T* Z, const T* D, int o, int P, int W, T A, T f,
+                                          T tau, T BinvC, T gA, T cN, T cS, T Bth, T gBth, T href,
+                                          T& dFh, T& dFu, T& dFv) {
+  const T* H = Z;
+  const T* U = Z + P;
+  const T* V = Z + 2 * P;
+  const T* dH = D;
+  const T* dU = D + P;
+  const T* dV = D + 2 * P;
+  const T u = U[o], v = V[o];
+  const T du = dU[o], dv = dV[o];
+  const T uE = U[o + 1], uW = U[o - 1], uN = U[o + W], uS = U[o - W];
+  const T vE = V[o + 1], vW = V[o - 1], vN = V[o + W], vS = V[o - W];
+  T hE = H[o + 1], hW = H[o - 1], hN = H[o + W], hS = H[o - W];
+  if (DEV) {
+    hE += href; hW += href; hN += href; hS += href;
+  }
+  const T duE = dU[o + 1], duW = dU[o - 1], duN = dU[o + W], duS = dU[o - W];
+  const T dvE = dV[o + 1], dvW = dV[o - 1], dvN = dV[o + W], dvS = dV[o - W];
+  const T dhE = dH[o + 1], dhW = dH[o - 1], dhN = dH[o + W], dhS = dH[o - W];
+  dFu = -A * (du * (uE - uW) + u * (duE - duW)) - Bth * (dv * (uN - uS) + v * (duN - duS)) +
+        (f + tau * u) * dv + tau * du * v - gA * (dhE - dhW);
+  dFv = -A * (du * (vE - vW) + u * (dvE - dvW)) - Bth * (dv * (vN - vS) + v * (dvN - dvS)) -
+        (f + tau * u) * du - tau * du * u - gBth * (dhN - dhS);
+  dFh = -A * ((dhE * uE + hE * duE) - (dhW * uW + hW * duW)) -
+        BinvC * ((dhN * vN + hN * dvN) * cN - (dhS * vS + hS * dvS) * cS);
+}
+
+template <typename T>
+__device__ __forceinline__ void block_reduce2(double& x, double& y, double* scratch) {
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) {
+    scratch[2 * wid] = x;
+    scratch[2 * wid + 1] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sx = 0.0, sy = 0.0;
+    for (int w = 0; w < nw; ++w) {
+      sx += scratch[2 * w];
+      sy += scratch[2 * w + 1];
+    }
+    x = sx;
+    y = sy;
+  }
+}
+
+// Overlap count at a local point: (covering subdomains) - 1.
+template <typename T>
+__device__ __forceinline__ int overlap_count(const Geo<T>& g, int l, int r, int k) {
+  const SubDesc& d = g.d;
+  const int cx = 1 + (k < d.wL) + (k >= d.nx - d.wR);
+  const int cy = 1 + (r < d.wS) + (r >= d.ny - d.wN);
+  const int ct = 1 + (l < d.tA) + (l > g.L - d.tB);
+  return cx * cy * ct - 1;
+}
+
+// Observation misfit of the observations of level l whose lower corner row
+// is one of this CTA's rows: J_o += 1/2 w d^2, obs_force = lambda w d.
+template <typename T>
+__device__ void obs_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int l, double& Jo) {
+  const int o0 = a.lvl_obs[g.d.obs_lvl + l], o1 = a.lvl_obs[g.d.obs_lvl + l + 1];
+  for (int o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
+    const ObsRec ob = a.obs[o];
+    const int rr = ob.r0 - g.R0;
+    if (rr < 0 || rr >= g.Rn) continue;
+    const T* P = X + ob.var * g.P;
+    double acc = 0.0;
+    const double wj0 = 1.0 - ob.dj, wi0 = 1.0 - ob.di;
+    acc += (wj0 * wi0) * (double)P[(rr + 1) * g.W + ob.k0 + 1];
+    if (ob.di != 0.0) acc += (wj0 * ob.di) * (double)P[(rr + 1) * g.W + ob.k1 + 1];
+    if (ob.dj != 0.0) {
+      acc += (ob.dj * wi0) * (double)P[(rr + 2) * g.W + ob.k0 + 1];
+      if (ob.di != 0.0) acc += (ob.dj * ob.di) * (double)P[(rr + 2) * g.W + ob.k1 + 1];
+    }
+    const double d = acc - ob.y;
+    Jo += 0.5 * ob.w * d * d;
+    a.obs_force[o] = a.lam * ob.w * d;
+  }
+}
+
+// Overlap penalty at level l over own points: J_mu += 1/2 c sum_v (x - m)^2 / sb^2.
+template <typename T>
+__device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int l, double& Jm) {
+  const SubDesc& d = g.d;
+  const bool any_t = (l < d.tA) || (l > g.L - d.tB);
+  const bool any_s = d.wL || d.wR || d.wS || d.wN;
+  if (!any_t && !any_s) return;
+  const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
+  for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+    const int rr = idx / g.nx, k = idx - rr * g.nx;
+    const int r = g.R0 + rr;
+    const int c = overlap_count(g, l, r, k);
+    if (c == 0) continue;
+    double acc = 0.0;
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const double e = (double)X[off(g, v, rr, k)] - (double)tg[((size_t)v * g.ny + r) * d.nxp + k];
+      acc += e * e * a.isb2[v];
+    }
+    Jm += 0.5 * c * acc;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ bool setup_geo(const SweepArgs<T>& a, cg::cluster_group& cl, Geo<T>& g) {
+  g.rank = cl.block_rank();
+  g.CL = cl.num_blocks();
+  const int cid = blockIdx.x / g.CL;
+  if (cid >= a.n_sub) return false;
+  g.s = a.order[cid];
+  if (a.active && a.active[g.s] != a.active_value) return false;
+  g.d = a.subs[g.s];
+  g.nx = g.d.nx;
+  g.ny = g.d.ny;
+  g.a = g.d.a;
+  g.L = g.d.b - g.d.a;
+  g.flags = g.d.flags;
+  if (g.ny < g.CL || g.nx + 2 > a.W) {   // uniform over the cluster
+    if (threadIdx.x == 0 && g.rank == 0) atomicExch(a.err, 1);
+    return false;
+  }
+  split_rows(g.ny, g.CL, g.rank, g.R0, g.Rn);
+  int t;
+  if (g.rank > 0) split_rows(g.ny, g.CL, g.rank - 1, t, g.Rprev); else g.Rprev = 0;
+  if (g.rank < g.CL - 1) split_rows(g.ny, g.CL, g.rank + 1, t, g.Rnext); else g.Rnext = 0;
+  g.R2 = a.R + 2;
+  g.W = a.W;
+  g.P = g.R2 * g.W;
+  if (g.rank != 0) g.flags &= ~F_SWALL;           // only the edge CTAs see the walls
+  if (g.rank != g.CL - 1) g.flags &= ~F_NWALL;
+  return true;
+}
+
+// One RK3 stage on own rows: out = cx X + cy (Y + dt F(Y)).
+template <typename T, bool DEV>
+__device__ void stage(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs, T* out,
+                      const T* X, const T* Y, T cx, T cy) {
+  const T dt = (T)a.dt, Bth = (T)a.Bth, gBth = (T)a.gBth, href = (T)a.h_ref;
+  for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+    const int rr = idx / g.nx, k = idx - rr * g.nx;
+    const int o = (rr + 1) * g.W + k + 1;
+    const int ri = rr + 1;
+    T Fh, Fu, Fv;
+    rhs_pt<T, DEV>(Y, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.BinvC[ri], rs.gA[ri],
+                   rs.c[ri + 1], rs.c[ri - 1], Bth, gBth, href, Fh, Fu, Fv);
+    if (cx == (T)0) {
+      out[o] = cy * (Y[o] + dt * Fh);
+      out[o + g.P] = cy * (Y[o + g.P] + dt * Fu);
+      out[o + 2 * g.P] = cy * (Y[o + 2 * g.P] + dt * Fv);
+    } else {
+      out[o] = cx * X[o] + cy * (Y[o] + dt * Fh);
+      out[o + g.P] = cx * X[o + g.P] + cy * (Y[o + g.P] + dt * Fu);
+      out[o + 2 * g.P] = cx * X[o + 2 * g.P] + cy * (Y[o + 2 * g.P] + dt * Fv);
+    }
+  }
+}
+
+template <typename T>
+__device__ void store_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int l) {
+  T* dst = a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp;
+  for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
+    const int v = idx / (g.Rn * g.nx);
+    const int rem = idx - v * g.Rn * g.nx;
+    const int rr = rem / g.nx, k = rem - rr * g.nx;
+    dst[((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k] = X[off(g, v, rr, k)];
+  }
+}
+
+template <typename T>
+__device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs, RowSmem<T>& rs,
+                      double** scratch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* p = reinterpret_cast<T*>(smem_raw);
+  for (int b = 0; b < nbuf; ++b) {
+    bufs[b] = p;
+    p += 3 * g.P;
+  }
+  const int nr = a.R + 2;
+  rs.A = p; p += nr;
+  rs.f = p; p += nr;
+  rs.tau = p; p += nr;
+  rs.BinvC = p; p += nr;
+  rs.gA = p; p += nr;
+  rs.c = p; p += nr;
+  rs.ic = p; p += nr;
+  rs.BcC = p; p += nr;
+  uintptr_t q = reinterpret_cast<uintptr_t>(p);
+  q = (q + 15) & ~uintptr_t(15);
+  *scratch = reinterpret_cast<double*>(q);
+}
+
+template <typename T>
+size_t smem_bytes(int nbuf, int R, int W) {
+  return (size_t)nbuf * 3 * (R + 2) * W * sizeof(T) + 8 * (size_t)(R + 2) * sizeof(T) + 16 +
+         64 * sizeof(double);
+}
+
+// ---------------------------------------------------------------------------
+// Forward sweep: x(a) (stored at level 0 by the init kernel) -> x(a+1..b),
+// trajectory stored at every level, J_o and J_mu partial sums per CTA.
+template <typename T>
+__global__ void __launch_bounds__(256) fwd_kernel(SweepArgs<T> a) {
+  constexpr bool DEV = sizeof(T) == 4;
+  cg::cluster_group cl = cg::this_cluster();
+  Geo<T> g;
+  if (!setup_geo(a, cl, g)) return;
+  T* buf[3];
+  RowSmem<T> rs;
+  double* scratch;
+  carve(a, g, 3, buf, rs, &scratch);
+  T* X = buf[0];
+  T* S1 = buf[1];
+  T* S2 = buf[2];
+  load_rows(a, g, rs);
+  load_level(a, g, X, 0, g.a);   // includes a CTA barrier
+  double Jo = 0.0, Jm = 0.0;
+  obs_level(a, g, X, 0, Jo);
+  overlap_level(a, g, X, 0, Jm);
+  for (int l = 0; l < g.L; ++l) {
+    const int n = g.a + l;
+    stage<T, DEV>(a, g, rs, S1, X, X, (T)0, (T)1);
+    complete_buf(cl, a, g, S1, K_STATE, n + 1, n + 1, (T)1, (T)0);
+    stage<T, DEV>(a, g, rs, S2, X, S1, (T)0.75, (T)0.25);
+    complete_buf(cl, a, g, S2, K_STATE, n, n + 1, (T)0.5, (T)0.5);
+    stage<T, DEV>(a, g, rs, X, X, S2, (T)(1.0 / 3.0), (T)(2.0 / 3.0));
+    complete_buf(cl, a, g, X, K_STATE, n + 1, n + 1, (T)1, (T)0);
+    store_level(a, g, X, l + 1);
+    obs_level(a, g, X, l + 1, Jo);
+    overlap_level(a, g, X, l + 1, Jm);
+  }
+  block_reduce2<T>(Jo, Jm, scratch);
+  if (threadIdx.x == 0) {
+    a.part[((size_t)g.s * a.cl_max + g.rank) * 2 + 0] = Jo;
+    a.part[((size_t)g.s * a.cl_max + g.rank) * 2 + 1] = Jm;
+  }
+  cl.sync();   // keep shared memory alive until every neighbour is done with it
+}
+
+// Forcing of the adjoint at level l on own rows: observation scatter (H^T of
+// lambda w d, fixed order per target) and overlap term mu c (x - m)/sb^2, or an
+// external forcing y.  L holds the adjoint state, X the state at that level.
+template <typename T>
+__device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const T* X, int l) {
+  const SubDesc& d = g.d;
+  if (a.yforce) {
+    const double* y = a.yforce + d.ptraj_off + (size_t)l * 3 * g.ny * g.nx;
+    for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
+      const int v = idx / (g.Rn * g.nx);
+      const int rem = idx - v * g.Rn * g.nx;
+      const int rr = rem / g.nx, k = rem - rr * g.nx;
+      Lb[off(g, v, rr, k)] += (T)y[((size_t)v * g.ny + g.R0 + rr) * g.nx + k];
+    }
+    __syncthreads();
+    return;
+  }
+  const bool any_t = (l < d.tA) || (l > g.L - d.tB);
+  const bool any_s = d.wL || d.wR || d.wS || d.wN;
+  if ((any_t || any_s) && a.mu != 0.0) {
+    const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
+    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+      const int rr = idx / g.nx, k = idx - rr * g.nx;
+      const int r = g.R0 + rr;
+      const int c = overlap_count(g, l, r, k);
+      if (c == 0) continue;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        const double e = (double)X[off(g, v, rr, k)] - (double)tg[((size_t)v * g.ny + r) * d.nxp + k];
+        Lb[off(g, v, rr, k)] += (T)(a.mu * c * e * a.isb2[v]);
+      }
+    }
+  }
+  __syncthreads();
+  const int t0 = a.lvl_sc[d.sc_lvl + l], t1 = a.lvl_sc[d.sc_lvl + l + 1];
+  const int plane = g.ny * g.nx;
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    const int tg = a.sc_tgt[t];
+    const int v = tg / plane;
+    const int rem = tg - v * plane;
+    const int r = rem / g.nx, k = rem - r * g.nx;
+    const int rr = r - g.R0;
+    if (rr < 0 || rr >= g.Rn) continue;
+    double acc = 0.0;
+    for (int c = a.sc_off[t]; c < a.sc_off[t + 1]; ++c) acc += a.sc_w[c] * a.obs_force[a.sc_obs[c]];
+    Lb[off(g, v, rr, k)] += (T)acc;
+  }
+  __syncthreads();
+}
+
+// Adjoint sweep: lambda(b) = forcing(b); lambda(n) = M_n^T lambda(n+1) + forcing(n),
+// the RK3 stages recomputed from the stored x(n).  Writes lambda(a) to lam_a.
+template <typename T>
+__global__ void __launch_bounds__(256) adj_kernel(SweepArgs<T> a) {
+  constexpr bool DEV = sizeof(T) == 4;
+  cg::cluster_group cl = cg::this_cluster();
+  Geo<T> g;
+  if (!setup_geo(a, cl, g)) return;
+  T* buf[5];
+  RowSmem<T> rs;
+  double* scratch;
+  carve(a, g, 5, buf, rs, &scratch);
+  T* X = buf[0];
+  T* X1 = buf[1];
+  T* X2 = buf[2];   // also lambda_x1
+  T* Lp = buf[3];
+  T* L2 = buf[4];
+  load_rows(a, g, rs);
+  for (int i = threadIdx.x; i < 3 * g.P; i += blockDim.x) Lp[i] = (T)0;
+  load_level(a, g, X, g.L, g.a + g.L);
+  add_forcing(a, g, Lp, X, g.L);
+  complete_buf(cl, a, g, Lp, K_ADJ, 0, 0, (T)1, (T)0);
+  const T dt = (T)a.dt, Bth = (T)a.Bth, gBth = (T)a.gBth, href = (T)a.h_ref;
+  const T c23 = (T)(2.0 / 3.0), c13 = (T)(1.0 / 3.0);
+  const int wall_s = (g.flags & F_SWALL) ? 1 : 0;
+  const int wall_n = (g.flags & F_NWALL) ? 2 : 0;
+  for (int l = g.L - 1; l >= 0; --l) {
+    const int n = g.a + l;
+    load_level(a, g, X, l, n);
+    stage<T, DEV>(a, g, rs, X1, X, X, (T)0, (T)1);
+    complete_buf(cl, a, g, X1, K_STATE, n + 1, n + 1, (T)1, (T)0);
+    stage<T, DEV>(a, g, rs, X2, X, X1, (T)0.75, (T)0.25);
+    complete_buf(cl, a, g, X2, K_STATE, n, n + 1, (T)0.5, (T)0.5);
+    // lambda_x2 = 2/3 lambda' + 2/3 dt F'(x2)^T lambda'
+    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+      const int rr = idx / g.nx, k = idx - rr * g.nx;
+      const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
+      const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
+      T Gh, Gu, Gv;
+      rhs_adj_pt<T, DEV>(X2, Lp, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
+                         rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
+      L2[o] = c23 * (Lp[o] + dt * Gh);
+      L2[o + g.P] = c23 * (Lp[o + g.P] + dt * Gu);
+      L2[o + 2 * g.P] = c23 * (Lp[o + 2 * g.P] + dt * Gv);
+    }
+    complete_buf(cl, a, g, L2, K_ADJ, 0, 0, (T)1, (T)0);
+    // lambda_x1 = 1/4 lambda_x2 + 1/4 dt F'(x1)^T lambda_x2   (into X2's buffer)
+    T* L1 = X2;
+    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+      const int rr = idx / g.nx, k = idx - rr * g.nx;
+      const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
+      const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
+      T Gh, Gu, Gv;
+      rhs_adj_pt<T, DEV>(X1, L2, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
+                         rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
+      L1[o] = (T)0.25 * (L2[o] + dt * Gh);
+      L1[o + g.P] = (T)0.25 * (L2[o + g.P] + dt * Gu);
+      L1[o + 2 * g.P] = (T)0.25 * (L2[o + 2 * g.P] + dt * Gv);
+    }
+    complete_buf(cl, a, g, L1, K_ADJ, 0, 0, (T)1, (T)0);
+    // lambda(n) = 1/3 lambda' + 3/4 lambda_x2 + lambda_x1 + dt F'(x)^T lambda_x1
+    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+      const int rr = idx / g.nx, k = idx - rr * g.nx;
+      const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
+      const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
+      T Gh, Gu, Gv;
+      rhs_adj_pt<T, DEV>(X, L1, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
+                         rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
+      Lp[o] = c13 * Lp[o] + (T)0.75 * L2[o] + L1[o] + dt * Gh;
+      Lp[o + g.P] = c13 * Lp[o + g.P] + (T)0.75 * L2[o + g.P] + L1[o + g.P] + dt * Gu;
+      Lp[o + 2 * g.P] = c13 * Lp[o + 2 * g.P] + (T)0.75 * L2[o + 2 * g.P] + L1[o + 2 * g.P] + dt * Gv;
+    }
+    __syncthreads();
+    add_forcing(a, g, Lp, X, l);
+    complete_buf(cl, a, g, Lp, K_ADJ, 0, 0, (T)1, (T)0);
+  }
+  // lambda(a) -> packed control layout (FP64)
+  double* out = a.lam_a + g.d.ctrl_off;
+  for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
+    const int v = idx / (g.Rn * g.nx);
+    const int rem = idx - v * g.Rn * g.nx;
+    const int rr = rem / g.nx, k = rem - rr * g.nx;
+    out[((size_t)v * g.ny + g.R0 + rr) * g.nx + k] = (double)Lp[off(g, v, rr, k)];
+  }
+  cl.sync();
+}
+
+// Tangent-linear sweep: x and dx advanced together; x stored to the
+// trajectory, dx to the packed FP64 output.
+template <typename T>
+__device__ void load_delta0(const SweepArgs<T>& a, const Geo<T>& g, T* D) {
+  const double* src = a.dx0 + g.d.ctrl_off;
+  const int r_lo = (g.rank > 0) ? -1 : 0;
+  const int r_hi = (g.rank < g.CL - 1) ? g.Rn + 1 : g.Rn;
+  const int nr = r_hi - r_lo;
+  for (int i = threadIdx.x; i < 3 * g.P; i += blockDim.x) D[i] = (T)0;
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 3 * nr * g.nx; idx += blockDim.x) {
+    const int v = idx / (nr * g.nx);
+    const int rem = idx - v * nr * g.nx;
+    const int rr = rem / g.nx + r_lo;
+    const int k = rem - (rr - r_lo) * g.nx;
+    D[off(g, v, rr, k)] = (T)src[((size_t)v * g.ny + g.R0 + rr) * g.nx + k];
+  }
+  __syncthreads();
+  if (g.flags & F_SWALL)
+    for (int idx = threadIdx.x; idx < 3 * g.nx; idx += blockDim.x) {
+      const int v = idx / g.nx, k = idx - v * g.nx;
+      D[off(g, v, -1, k)] = (v == 2) ? -D[off(g, v, 0, k)] : D[off(g, v, 0, k)];
+    }
+  if (g.flags & F_NWALL)
+    for (int idx = threadIdx.x; idx < 3 * g.nx; idx += blockDim.x) {
+      const int v = idx / g.nx, k = idx - v * g.nx;
+      D[off(g, v, g.Rn, k)] = (v == 2) ? -D[off(g, v, g.Rn - 1, k)] : D[off(g, v, g.Rn - 1, k)];
+    }
+  if (g.flags & F_PERIODIC)
+    for (int idx = threadIdx.x; idx < 3 * g.Rn; idx += blockDim.x) {
+      const int v = idx / g.Rn, rr = idx - v * g.Rn;
+      D[off(g, v, rr, -1)] = D[off(g, v, rr, g.nx - 1)];
+      D[off(g, v, rr, g.nx)] = D[off(g, v, rr, 0)];
+    }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void store_delta(const SweepArgs<T>& a, const Geo<T>& g, const T* D, int l) {
+  double* dst = a.dx_out + g.d.ptraj_off + (size_t)l * 3 * g.ny * g.nx;
+  for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
+    const int v = idx / (g.Rn * g.nx);
+    const int rem = idx - v * g.Rn * g.nx;
+    const int rr = rem / g.nx, k = rem - rr * g.nx;
+    dst[((size_t)v * g.ny + g.R0 + rr) * g.nx + k] = (double)D[off(g, v, rr, k)];
+  }
+}
+
+template <typename T, bool DEV>
+__device__ void stage_tl(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs, T* dout,
+                         const T* DX, const T* Y, const T* DY, T cx, T cy) {
+  const T dt = (T)a.dt, Bth = (T)a.Bth, gBth = (T)a.gBth, href = (T)a.h_ref;
+  for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+    const int rr = idx / g.nx, k = idx - rr * g.nx;
+    const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
+    T Fh, Fu, Fv;
+    rhs_tl_pt<T, DEV>(Y, DY, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.BinvC[ri], rs.gA[ri],
+                      rs.c[ri + 1], rs.c[ri - 1], Bth, gBth, href, Fh, Fu, Fv);
+    dout[o] = cx * DX[o] + cy * (DY[o] + dt * Fh);
+    dout[o + g.P] = cx * DX[o + g.P] + cy * (DY[o + g.P] + dt * Fu);
+    dout[o + 2 * g.P] = cx * DX[o + 2 * g.P] + cy * (DY[o + 2 * g.P] + dt * Fv);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) tlm_kernel(SweepArgs<T> a) {
+  constexpr bool DEV = sizeof(T) == 4;
+  cg::cluster_group cl = cg::this_cluster();
+  Geo<T> g;
+  if (!setup_geo(a, cl, g)) return;
+  T* buf[6];
+  RowSmem<T> rs;
+  double* scratch;
+  carve(a, g, 6, buf, rs, &scratch);
+  T *X = buf[0], *S1 = buf[1], *S2 = buf[2], *D = buf[3], *D1 = buf[4], *D2 = buf[5];
+  load_rows(a, g, rs);
+  load_level(a, g, X, 0, g.a);
+  load_delta0(a, g, D);
+  store_delta(a, g, D, 0);
+  for (int l = 0; l < g.L; ++l) {
+    const int n = g.a + l;
+    stage_tl<T, DEV>(a, g, rs, D1, D, X, D, (T)0, (T)1);
+    stage<T, DEV>(a, g, rs, S1, X, X, (T)0, (T)1);
+    complete_buf(cl, a, g, S1, K_STATE, n + 1, n + 1, (T)1, (T)0);
+    complete_buf(cl, a, g, D1, K_DELTA, 0, 0, (T)1, (T)0);
+    stage_tl<T, DEV>(a, g, rs, D2, D, S1, D1, (T)0.75, (T)0.25);
+    stage<T, DEV>(a, g, rs, S2, X, S1, (T)0.75, (T)0.25);
+    complete_buf(cl, a, g, S2, K_STATE, n, n + 1, (T)0.5, (T)0.5);
+    complete_buf(cl, a, g, D2, K_DELTA, 0, 0, (T)1, (T)0);
+    stage_tl<T, DEV>(a, g, rs, D, D, S2, D2, (T)(1.0 / 3.0), (T)(2.0 / 3.0));
+    stage<T, DEV>(a, g, rs, X, X, S2, (T)(1.0 / 3.0), (T)(2.0 / 3.0));
+    complete_buf(cl, a, g, X, K_STATE, n + 1, n + 1, (T)1, (T)0);
+    complete_buf(cl, a, g, D, K_DELTA, 0, 0, (T)1, (T)0);
+    store_level(a, g, X, l + 1);
+    store_delta(a, g, D, l + 1);
+  }
+  cl.sync();
+}
+
+template <typename T, typename K>
+cudaError_t launch_cluster(K kernel, const SweepArgs<T>& a, int cl, int nthreads, size_t smem,
+                           cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (cl > 8) {
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n_sub * cl), 1, 1);
+  cfg.blockDim = dim3((unsigned)nthreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
+}  // namespace
+
+template <typename T> size_t smem_forward(int R, int W) { return smem_bytes<T>(3, R, W); }
+template <typename T> size_t smem_adjoint(int R, int W) { return smem_bytes<T>(5, R, W); }
+template <typename T> size_t smem_tlm(int R, int W) { return smem_bytes<T>(6, R, W); }
+
+template <typename T>
+int occupancy_adjoint(int R, int W, int nthreads) {
+  const size_t smem = smem_adjoint<T>(R, W);
+  if (cudaFuncSetAttribute(adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adj_kernel<T>, nthreads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <typename T>
+cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
+  return launch_cluster(fwd_kernel<T>, a, cl, nthreads, smem_forward<T>(a.R, a.W), st);
+}
+template <typename T>
+cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
+  return launch_cluster(adj_kernel<T>, a, cl, nthreads, smem_adjoint<T>(a.R, a.W), st);
+}
+template <typename T>
+cudaError_t launch_tlm(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
+  return launch_cluster(tlm_kernel<T>, a, cl, nthreads, smem_tlm<T>(a.R, a.W), st);
+}
+
+#define DD4DV_INST(T)                                                                        \
+  template size_t smem_forward<T>(int, int);                                                 \
+  template size_t smem_adjoint<T>(int, int);                                                 \
+  template size_t smem_tlm<T>(int, int);                                                     \
+  template int occupancy_adjoint<T>(int, int, int);                                          \
+  template cudaError_t launch_forward<T>(const SweepArgs<T>&, int, int, cudaStream_t);       \
+  template cudaError_t launch_adjoint<T>(const SweepArgs<T>&, int, int, cudaStream_t);       \
+  template cudaError_t launch_tlm<T>(const SweepArgs<T>&, int, int, cudaStream_t);
+DD4DV_INST(double)
+DD4DV_INST(float)
+#undef DD4DV_INST
+
+}  // namespace dd4dv

@@ -33,3 +33,23 @@ def perturbed_state(st, seed=11, scale=0.3):
 def rand_w(n, seed=3, scale=0.5):
     g = torch.Generator().manual_seed(seed)
     return scale * torch.randn(n, generator=g, dtype=F64)
+
+
+def make_context(wl, st, inputs, precision=0, cluster=0, mu=None):
+    """Library context for a workload, fed the same inputs as the oracle Setup."""
+    import paper_2205_06649_gb300 as dd
+    ctx = dd.Context(wl.nlon, wl.nlat, inputs["dt"], wl.nsteps, precision=precision)
+    ctx.set_background(inputs["x_b0"])
+    ctx.set_background_error(wl.sigma_b, wl.corr_len, wl.rf_passes)
+    ob = st.obs
+    ctx.set_observations(ob.level, ob.var, ob.fi, ob.fj, ob.value, ob.sigma_o)
+    ctx.set_decomposition(wl.P1, wl.P2, wl.Q, wl.o_lon, wl.o_lat, wl.o_t, inputs["lon_cuts"],
+                          inputs["lat_cuts"], inputs["t_cuts"], mu=wl.mu if mu is None else mu,
+                          lam=wl.lam, cluster=cluster)
+    return ctx
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
