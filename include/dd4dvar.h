@@ -263,6 +263,14 @@ dd4dv_status dd4dv_pt_steps(const dd4dv_ctx* ctx, long long* n);
  * created (cumulative; take differences around a region to count it). */
 dd4dv_status dd4dv_launch_count(const dd4dv_ctx* ctx, long long* n);
 
+/* Kernel timing (diagnostics): evaluates J and grad J at w_all (host,
+ * packed) reps times after one warm-up and returns in ms[4] the mean
+ * duration of one forward-sweep launch, one adjoint-sweep launch, one whole
+ * evaluation (all kernels of dd4dv_eval) and the number of kernels in one
+ * evaluation; durations come from CUDA events recorded on the context's
+ * stream around each launch. */
+dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps, double* ms);
+
 /* The cluster size (CTAs per subdomain) the sweeps use. */
 dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* ctx, int* n);
 

@@ -155,6 +155,13 @@ class Context:
         self._check(lib.dd4dv_launch_count(self._h, C.byref(n)))
         return n.value
 
+    def profile_sweeps(self, w, reps: int = 5) -> dict:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        ms = np.zeros(4)
+        self._check(lib.dd4dv_profile_sweeps(self._h, C.c_void_p(w.ctypes.data), reps,
+                                             C.c_void_p(ms.ctypes.data)))
+        return dict(forward_ms=ms[0], adjoint_ms=ms[1], eval_ms=ms[2], kernels_per_eval=int(ms[3]))
+
     # ---- evaluation (host numpy or device torch) ----
     def eval(self, w, grad: bool = True, parts: bool = False):
         dev = _is_torch_cuda(w)
@@ -293,14 +300,17 @@ class Context:
                          allow_notconv=True)
         return xa, stats, st
 
-    def get_controls(self) -> np.ndarray:
-        w = np.zeros(self.ctrl_total)
-        self._check(lib.dd4dv_get_controls(self._h, C.c_void_p(w.ctypes.data), 0))
+    def get_controls(self, out=None):
+        dev = out is not None and _is_torch_cuda(out)
+        w = out if out is not None else np.zeros(self.ctrl_total)
+        self._check(lib.dd4dv_get_controls(self._h, _ptr(w, np.float64, dev), int(dev)))
         return w
 
     def set_controls(self, w):
-        w = np.ascontiguousarray(w, dtype=np.float64)
-        self._check(lib.dd4dv_set_controls(self._h, C.c_void_p(w.ctypes.data), 0))
+        dev = _is_torch_cuda(w)
+        if not dev:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+        self._check(lib.dd4dv_set_controls(self._h, _ptr(w, np.float64, dev), int(dev)))
 
     # ---- packed-layout helpers ----
     def split_controls(self, w) -> list:

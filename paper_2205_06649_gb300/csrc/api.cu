@@ -1444,6 +1444,53 @@ dd4dv_status dd4dv_launch_count(const dd4dv_ctx* ctx, long long* n) {
   return DD4DV_OK;
 }
 
+dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps, double* ms) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all || !ms || reps < 1) fail(ctx, DD4DV_EINVAL, "bad argument");
+    h2d(ctx, ctx->io_a, w_all, ctx->ctrl_total * sizeof(double));
+    cudaEvent_t ev[6];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    double tf = 0, ta = 0, te = 0;
+    long long kernels = 0;
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      for (int r = 0; r <= reps; ++r) {
+        const long long k0 = ctx->launches;
+        CK(cudaEventRecord(ev[4], ctx->st));
+        init_states<T>(ctx, ctx->io_a, ctx->vw, nullptr, 0);
+        CK(cudaEventRecord(ev[0], ctx->st));
+        forward_sweep<T>(ctx, nullptr, 0);
+        CK(cudaEventRecord(ev[1], ctx->st));
+        KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, ctx->io_a, ctx->part, ctx->cl, ctx->vconst,
+                             ctx->dec.lambda, ctx->dec.mu, ctx->io_p, nullptr, nullptr, 0, ctx->st));
+        SweepArgs<T> a = sweep_args<T>(ctx);
+        CK(cudaEventRecord(ev[2], ctx->st));
+        KL(launch_adjoint<T>(a, ctx->cl, 256, ctx->st));
+        CK(cudaEventRecord(ev[3], ctx->st));
+        apply_VT(ctx, ctx->lam_a, ctx->io_a, nullptr, ctx->io_b, nullptr, 0);
+        CK(cudaEventRecord(ev[5], ctx->st));
+        CK(cudaEventSynchronize(ev[5]));
+        float f = 0, ad = 0, e = 0;
+        CK(cudaEventElapsedTime(&f, ev[0], ev[1]));
+        CK(cudaEventElapsedTime(&ad, ev[2], ev[3]));
+        CK(cudaEventElapsedTime(&e, ev[4], ev[5]));
+        if (r > 0) { tf += f; ta += ad; te += e; }
+        kernels = ctx->launches - k0;
+      }
+      return 0;
+    });
+    for (auto& e : ev) cudaEventDestroy(e);
+    sync(ctx);
+    ms[0] = tf / reps;
+    ms[1] = ta / reps;
+    ms[2] = te / reps;
+    ms[3] = (double)kernels;
+    ctx->fwd_pending = false;
+    return DD4DV_OK;
+  });
+}
+
 dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* cctx, int* n) {
   auto* ctx = const_cast<dd4dv_ctx*>(cctx);
   if (!ctx || !n) return DD4DV_EINVAL;

@@ -159,3 +159,25 @@ def test_device_pointer_eval_equals_host_eval():
     Jd, gd = ctx.eval(torch.as_tensor(w, device="cuda"))
     torch.cuda.synchronize()
     assert np.array_equal(J, Jd.cpu().numpy()) and np.array_equal(g, gd.cpu().numpy())
+
+
+def test_outer_loop_matches_oracle_dd4dvar():
+    """Algorithm 1 end to end (batched device L-BFGS, Exchange, Gather) against
+    the oracle's outer loop on the small workload: same local minimiser
+    settings, two outer iterations."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("small")
+    st, inp, truth = _setup(wl)
+    ref = oracle.dd4dvar(st, max_outer=2, local_iters=6, m=5, gtol=1e-6)
+    ctx = make_context(wl, st, inp)
+    solver = dd.solver_defaults(lbfgs_m=5, max_local_iters=6, max_outer=2, eps_outer=0.0)
+    xa, stats, status = ctx.run(solver)
+    assert stats.outer_iters == 2
+    xb = inp["x_b0"]
+    inc_ref = ref.xa0.numpy() - xb
+    assert rel(xa - xb, inc_ref) <= 1e-6
+    w = ctx.get_controls()
+    for s, ws in enumerate(ctx.split_controls(w)):
+        assert rel(ws, ref.w[s].numpy()) <= 1e-6, s
+    assert abs(stats.J_sum - sum(ref.J_hist[-1])) <= 1e-8 * abs(sum(ref.J_hist[-1]))
+    assert abs(stats.dw_inf - ref.dw_inf[-1]) <= 1e-6 * ref.dw_inf[-1]
