@@ -274,8 +274,37 @@ dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps,
 /* The cluster size (CTAs per subdomain) the sweeps use. */
 dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* ctx, int* n);
 
+/* Global model run for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this is an interface variant of dd4dv_forward.
+ * Some callers cannot call cudaMalloc: a framework whose caching allocator
+ * already holds the free device memory, code that may not allocate after
+ * start-up, or a thread that must not trigger the device-wide
+ * synchronisation cudaMalloc/cudaFree can cause.  dd4dv_create allocates, so
+ * those callers cannot use dd4dv_forward; this call needs no context and
+ * makes no cudaMalloc, cudaFree or other allocating call.
+ *   model: as for dd4dv_create (precision and h_ref are ignored: FP64).
+ *   x0: device pointer, [3][nlat][nlon] initial state.
+ *   traj: device pointer, [nsteps+1][3][nlat][nlon] output (caller-owned).
+ *   cuda_stream: cudaStream_t to order the work on (NULL = legacy stream).
+ *     The call waits once for the work already queued on that stream (it
+ *     copies the grid constants from the host), then enqueues the model run
+ *     and returns without waiting for it.
+ * Limit: 3*nlat*nlon <= 393216 doubles (e.g. 512 x 256 points) and
+ * nlat <= 1024; larger grids return DD4DV_EINVAL.  Errors: EINVAL, ECUDA;
+ * the message is dd4dv_last_error(NULL).
+ * Scratch: the two RK3 stage states live in a fixed 6.3 MB __device__
+ * array of the library that every GPU which loads the library keeps until
+ * the process exits.  The first call on a device (with that device current)
+ * looks up the array's device address; make that first call before any
+ * stream capture.  All calls on a device share the array, so calls whose
+ * work overlaps on the GPU (other streams, other threads) race and must be
+ * ordered by the caller. */
+dd4dv_status dd4dv_forward_noalloc(const dd4dv_model* model, const double* x0, double* traj,
+                                   void* cuda_stream);
+
 /* Message of the last error on this context (library-owned, valid until the
- * next call on the context); ctx == NULL gives the last create() error. */
+ * next call on the context); ctx == NULL gives the message of the calling
+ * thread's last dd4dv_create or dd4dv_forward_noalloc call. */
 const char* dd4dv_last_error(const dd4dv_ctx* ctx);
 
 #ifdef __cplusplus

@@ -27,6 +27,10 @@ struct Fail {
 
 }  // namespace
 
+namespace dd4dv {
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace dd4dv
+
 struct dd4dv_ctx {
   dd4dv_model m{};
   cudaStream_t st = nullptr;
