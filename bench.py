@@ -130,7 +130,7 @@ def build_problem(wl, precision, stream, inputs=None):
     ctx.set_background_error(wl.sigma_b, wl.corr_len, wl.rf_passes)
     ctx.set_observations(inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)
     ctx.set_decomposition(wl.P1, wl.P2, wl.Q, wl.o_lon, wl.o_lat, wl.o_t, inp["lon_cuts"],
-                          inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam)
+                          inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam, cluster=-1)
     return ctx, inp, truth, (inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)
 
 
@@ -184,18 +184,18 @@ def time_to_analysis(ctx, solver, truth0, max_outer, torch, stream, zeros_dev):
     return out
 
 
-def profile_summary_traffic(kernel: str, src_hash: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (otherwise None)."""
-    p = os.path.join(ROOT, "profiles", f"{kernel}_medium_fp64.md")
-    if not os.path.exists(p):
-        return None
-    text = open(p).read()
-    m = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
-    h = re.search(r"sweep_source_sha256:\s*([0-9a-f]+)", text)
-    if not m or not h or h.group(1) != src_hash:
-        return None
-    return float(m.group(1))
+def profile_summary_traffic(kernel: str, src_hash: str, precision: str):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
+    from a committed ncu summary of the medium workload, if it was taken on the
+    current kernel source; otherwise None."""
+    import glob
+    for p in sorted(glob.glob(os.path.join(ROOT, "profiles", f"sweeps_medium_{precision}*.md"))):
+        text = open(p).read()
+        h = re.search(r"sweep_source_sha256:\s*([0-9a-f]+)", text)
+        m = re.search(rf"{kernel}_dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+        if h and m and h.group(1) == src_hash:
+            return float(m.group(1))
+    return None
 
 
 def source_hash():
@@ -363,7 +363,7 @@ def main():
             alu_peak = N_SM * FP32_FLOP_PER_CLK_SM * sm_mhz * 1e6
         alu_frac = flops / alu_peak
         hbm_frac = bytes_ / hbm_peak
-        traffic = profile_summary_traffic(f"{kern}_sweep", source_hash()) if prec == 0 else None
+        traffic = profile_summary_traffic(kern, source_hash(), "fp64" if prec == 0 else "fp32")
         if alu_frac >= hbm_frac:
             roof = {"bound": "alu", "achieved": flops / 1e12, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
                     "frac": alu_frac, "traffic": traffic, "kernel": f"{kern} sweep",
@@ -412,6 +412,7 @@ def main():
             prof32 = ctx32.profile_sweeps(np.zeros(ctx32.ctrl_total), reps=5)
             extras["fp32_state"] = {"value": st32.pt_steps / (ms32 / 1e3), "unit": UNIT,
                                     "ms_per_step": ms32 / args.steps, "dtype": "f32 state, f64 reductions",
+                                    "sweep_launch": ctx32.sweep_config(),
                                     "sweeps_ms": {"forward": prof32["forward_ms"],
                                                   "adjoint": prof32["adjoint_ms"],
                                                   "eval": prof32["eval_ms"]}}
@@ -440,7 +441,7 @@ def main():
             "config": {"workload": wl_desc(wl), "precision": "fp64" if prec == 0 else "fp32-state",
                        "step": "one DD-4DVar outer iteration from the start point (20 batched L-BFGS "
                                "iterations over all 64 subdomains + Exchange)",
-                       "cluster_ctas_per_subdomain": ctx.cluster_size(),
+                       "sweep_launch": ctx.sweep_config(),
                        "pt_steps_per_eval": pts_eval, "evals_per_step": stats.evals / args.steps,
                        "l2": "inputs larger than L2: FP64 trajectories + overlap targets "
                              f"{2 * 8 * ctx.traj_total / 1e6:.0f} MB",

@@ -89,9 +89,20 @@ typedef struct {
  * eq:cost:parallel1).  weight_obs = 1 weights each observation by
  * 1/(number of subdomains containing it), the restriction weights of
  * Definition "Restriction of a function"; 0 gives weight 1.
- * cluster: CTAs per subdomain in the sweep kernels (0 = choose automatically).
- * ckpt_k: store the trajectory every ckpt_k steps and recompute segments in
- * the adjoint (0 = store every level).
+ * cluster: CTAs per subdomain in the sweep kernels (thread-block cluster
+ * size, 1..16); 0 = chosen from a model of the launch; -1 = autotune: every
+ * feasible (cluster size, threads per CTA, stored or recomputed stage states
+ * when ckpt_k = 0) combination is timed on one evaluation and the fastest is
+ * kept (see dd4dv_sweep_config); if recomputation wins, the stage buffer is
+ * freed.
+ * ckpt_k: trajectory storage for the adjoint.  0 = the forward sweep stores
+ * every level and the two RK3 stage states of every step, and the adjoint
+ * loads them (three times the memory of the states alone; on GB300 this
+ * trades FP64 arithmetic for otherwise idle HBM bandwidth); -1 = store every
+ * level, the adjoint recomputes the stage states; k > 0 = checkpointing:
+ * evaluations store only the levels 0, k, 2k, ... and the adjoint
+ * recomputes each k-step segment from its checkpoint before running back
+ * through it (the exchange and dd4dv_trajectories still store every level).
  */
 typedef struct {
   int P1, P2, Q;
@@ -270,6 +281,13 @@ dd4dv_status dd4dv_launch_count(const dd4dv_ctx* ctx, long long* n);
  * evaluation; durations come from CUDA events recorded on the context's
  * stream around each launch. */
 dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps, double* ms);
+
+/* Launch shape of the sweeps: cluster size (CTAs per subdomain), threads
+ * per CTA, whether the adjoint loads stored stage states (1) or recomputes
+ * them (0), and (after autotuning, else 0) the measured evaluation time in
+ * ms of that shape.  Any pointer may be NULL. */
+dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* ctx, int* cluster, int* threads, int* stored_stages,
+                                double* eval_ms);
 
 /* The cluster size (CTAs per subdomain) the sweeps use. */
 dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* ctx, int* n);

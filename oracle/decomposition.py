@@ -147,17 +147,26 @@ def obs_membership(dec: Decomposition, level: Sequence[int], fi: Sequence[float]
                    fj: Sequence[float]):
     """For each observation, the subdomains that contain it: its level in
     the window and every non-zero-weight bilinear corner in the box.
-    Returns (list of lists of subdomain indices, weights 1/count)."""
-    members = []
-    for n, x, y in zip(level, fi, fj):
-        sup = bilinear_support(float(x), float(y), dec.nlon)
-        m = []
-        for s in dec.subs:
-            if not s.has_level(int(n)):
-                continue
-            if all(s.local_row(j) >= 0 and s.local_col(i) >= 0 for (j, i, _) in sup):
-                m.append(s.index)
-        members.append(m)
+    Returns a list (one entry per observation) of lists of subdomain indices.
+    (Same test as bilinear_support + Sub.local_row/local_col, evaluated for
+    all observations of one subdomain at a time.)"""
+    level = np.asarray(level)
+    fi = np.asarray(fi, dtype=np.float64)
+    fj = np.asarray(fj, dtype=np.float64)
+    i0 = np.floor(fi).astype(np.int64)
+    j0 = np.floor(fj).astype(np.int64)
+    has_i1 = (fi - i0) != 0.0
+    has_j1 = (fj - j0) != 0.0
+    i1 = (i0 + 1) % dec.nlon
+    members = [[] for _ in range(len(level))]
+    for s in dec.subs:
+        in_t = (level >= s.a) & (level <= s.b)
+        k0 = (i0 - s.i0) % dec.nlon
+        k1 = (i1 - s.i0) % dec.nlon
+        in_x = (k0 < s.nx) & (~has_i1 | (k1 < s.nx))
+        in_y = (j0 >= s.j0) & (j0 < s.j0 + s.ny) & (~has_j1 | (j0 + 1 < s.j0 + s.ny))
+        for k in np.nonzero(in_t & in_x & in_y)[0]:
+            members[k].append(s.index)
     return members
 
 

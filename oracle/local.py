@@ -92,6 +92,10 @@ class Setup:
             self.xb_traj = global_forward(grid, self.xb0, self.dt, nsteps)
         members = obs_membership(dec, obs.level, obs.fi, obs.fj)
         self.obs_members = members
+        self.obs_of_sub = [[] for _ in dec.subs]
+        for k, m in enumerate(members):
+            for s in m:
+                self.obs_of_sub[s].append(k)
         self.obs_weight = np.array([(1.0 / len(m) if (m and weight_obs) else (1.0 if m else 0.0))
                                     for m in members])
         self.locals = [LocalProblem(self, sub) for sub in dec.subs]
@@ -119,9 +123,7 @@ class LocalProblem:
         # observations of this subdomain, grouped by level
         self.obs_by_level = {}
         ob = st.obs
-        for k, m in enumerate(st.obs_members):
-            if sub.index not in m:
-                continue
+        for k in st.obs_of_sub[sub.index]:
             sup = bilinear_support(float(ob.fi[k]), float(ob.fj[k]), g.nlon)
             rows = [sub.local_row(j) for (j, _, _) in sup]
             cols = [sub.local_col(i) for (_, i, _) in sup]

@@ -67,6 +67,19 @@ class Context:
                  lat_min_deg: float = -80.0, lat_max_deg: float = 80.0, radius: float = 6.371e6,
                  gravity: float = 9.81, omega: float = 7.292e-5, h_ref: float = 4000.0,
                  stream: Optional[int] = None):
+        """stream: handle of a CUDA stream for the library's work; by default a
+        new torch stream.  Calls with CUDA tensors are ordered after the work
+        already queued on torch's current stream, and torch's current stream
+        waits for them, so tensors can be passed and used like any torch op's."""
+        self._tstream = None
+        try:
+            import torch
+            if torch.cuda.is_available():
+                self._tstream = (torch.cuda.Stream() if not stream
+                                 else torch.cuda.ExternalStream(stream))
+                stream = self._tstream.cuda_stream
+        except ImportError:
+            pass
         self.model = _abi.dd4dv_model(nlon, nlat, lat_min_deg, lat_max_deg, radius, gravity, omega,
                                       dt, nsteps, precision, h_ref)
         h = C.c_void_p()
@@ -74,8 +87,25 @@ class Context:
         if st != 0:
             raise DD4DVError(st, lib.dd4dv_last_error(None).decode())
         self._h = h
+        # handle of the stream the library orders its work on (None: its own)
+        self.stream = stream if stream else None
         self.nlon, self.nlat, self.nsteps = nlon, nlat, nsteps
         self.n_sub = 0
+        self._fwd_token = 0
+
+    def _device_call(self, fn, *tensors):
+        """Run a device-pointer call in stream order with torch's current stream."""
+        import torch
+        cur = torch.cuda.current_stream()
+        if self._tstream is not None and self._tstream.cuda_stream != cur.cuda_stream:
+            self._tstream.wait_stream(cur)
+            st = fn()
+            for t in tensors:
+                if t is not None:
+                    t.record_stream(self._tstream)
+            cur.wait_stream(self._tstream)
+            return st
+        return fn()
 
     # ---- lifetime ----
     def destroy(self):
@@ -145,6 +175,12 @@ class Context:
         self._check(lib.dd4dv_cluster_size(self._h, C.byref(n)))
         return n.value
 
+    def sweep_config(self) -> dict:
+        c, t, sg, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
+        self._check(lib.dd4dv_sweep_config(self._h, C.byref(c), C.byref(t), C.byref(sg), C.byref(ms)))
+        return {"cluster": c.value, "threads": t.value, "stored_stages": bool(sg.value),
+                "eval_ms": ms.value}
+
     def pt_steps(self) -> int:
         n = C.c_longlong()
         self._check(lib.dd4dv_pt_steps(self._h, C.byref(n)))
@@ -164,6 +200,7 @@ class Context:
 
     # ---- evaluation (host numpy or device torch) ----
     def eval(self, w, grad: bool = True, parts: bool = False):
+        self._fwd_token += 1
         dev = _is_torch_cuda(w)
         if dev:
             import torch
@@ -175,8 +212,9 @@ class Context:
             J = np.zeros(self.n_sub)
             g = np.zeros(self.ctrl_total) if grad else None
             P = np.zeros(3 * self.n_sub) if parts else None
-        self._check(lib.dd4dv_eval(self._h, _ptr(w, np.float64, dev), _ptr(J, np.float64, dev),
-                                   _ptr(g, np.float64, dev), _ptr(P, np.float64, dev), int(dev)))
+        call = lambda: lib.dd4dv_eval(self._h, _ptr(w, np.float64, dev), _ptr(J, np.float64, dev),
+                                      _ptr(g, np.float64, dev), _ptr(P, np.float64, dev), int(dev))
+        self._check(self._device_call(call, w, J, g, P) if dev else call())
         out = [J]
         if grad:
             out.append(g)
@@ -184,7 +222,12 @@ class Context:
             out.append(P.reshape(self.n_sub, 3))
         return tuple(out) if len(out) > 1 else J
 
+    def forward_token(self) -> int:
+        """Counter of dd4dv_eval_forward calls made through this object."""
+        return self._fwd_token
+
     def eval_forward(self, w):
+        self._fwd_token += 1
         dev = _is_torch_cuda(w)
         if dev:
             import torch
@@ -192,8 +235,9 @@ class Context:
         else:
             w = np.ascontiguousarray(w, dtype=np.float64)
             J = np.zeros(self.n_sub)
-        self._check(lib.dd4dv_eval_forward(self._h, _ptr(w, np.float64, dev), _ptr(J, np.float64, dev),
-                                           None, int(dev)))
+        call = lambda: lib.dd4dv_eval_forward(self._h, _ptr(w, np.float64, dev), _ptr(J, np.float64, dev),
+                                              None, int(dev))
+        self._check(self._device_call(call, w, J) if dev else call())
         return J
 
     def eval_backward(self, scale=None, like=None):
@@ -205,11 +249,13 @@ class Context:
             g = np.zeros(self.ctrl_total)
             if scale is not None:
                 scale = np.ascontiguousarray(scale, dtype=np.float64)
-        self._check(lib.dd4dv_eval_backward(self._h, _ptr(scale, np.float64, dev), _ptr(g, np.float64, dev),
-                                            int(dev)))
+        call = lambda: lib.dd4dv_eval_backward(self._h, _ptr(scale, np.float64, dev), _ptr(g, np.float64, dev),
+                                               int(dev))
+        self._check(self._device_call(call, scale, g) if dev else call())
         return g
 
     def tlm(self, w, dw):
+        self._fwd_token += 1
         dev = _is_torch_cuda(w)
         if dev:
             import torch
@@ -218,11 +264,13 @@ class Context:
             w = np.ascontiguousarray(w, dtype=np.float64)
             dw = np.ascontiguousarray(dw, dtype=np.float64)
             out = np.zeros(self.traj_total)
-        self._check(lib.dd4dv_tlm(self._h, _ptr(w, np.float64, dev), _ptr(dw, np.float64, dev),
-                                  _ptr(out, np.float64, dev), int(dev)))
+        call = lambda: lib.dd4dv_tlm(self._h, _ptr(w, np.float64, dev), _ptr(dw, np.float64, dev),
+                                     _ptr(out, np.float64, dev), int(dev))
+        self._check(self._device_call(call, w, dw, out) if dev else call())
         return out
 
     def adjoint(self, w, y):
+        self._fwd_token += 1
         dev = _is_torch_cuda(w)
         if dev:
             import torch
@@ -231,11 +279,13 @@ class Context:
             w = np.ascontiguousarray(w, dtype=np.float64)
             y = np.ascontiguousarray(y, dtype=np.float64)
             out = np.zeros(self.ctrl_total)
-        self._check(lib.dd4dv_adjoint(self._h, _ptr(w, np.float64, dev), _ptr(y, np.float64, dev),
-                                      _ptr(out, np.float64, dev), int(dev)))
+        call = lambda: lib.dd4dv_adjoint(self._h, _ptr(w, np.float64, dev), _ptr(y, np.float64, dev),
+                                         _ptr(out, np.float64, dev), int(dev))
+        self._check(self._device_call(call, w, y, out) if dev else call())
         return out
 
     def trajectories(self, w):
+        self._fwd_token += 1
         dev = _is_torch_cuda(w)
         if dev:
             import torch
@@ -243,15 +293,18 @@ class Context:
         else:
             w = np.ascontiguousarray(w, dtype=np.float64)
             out = np.zeros(self.traj_total)
-        self._check(lib.dd4dv_trajectories(self._h, _ptr(w, np.float64, dev), _ptr(out, np.float64, dev),
-                                           int(dev)))
+        call = lambda: lib.dd4dv_trajectories(self._h, _ptr(w, np.float64, dev), _ptr(out, np.float64, dev),
+                                              int(dev))
+        self._check(self._device_call(call, w, out) if dev else call())
         return out
 
     def exchange(self, w):
+        self._fwd_token += 1
         dev = _is_torch_cuda(w)
         if not dev:
             w = np.ascontiguousarray(w, dtype=np.float64)
-        self._check(lib.dd4dv_exchange(self._h, _ptr(w, np.float64, dev), int(dev)))
+        call = lambda: lib.dd4dv_exchange(self._h, _ptr(w, np.float64, dev), int(dev))
+        self._check(self._device_call(call, w) if dev else call())
 
     def reset_exchange(self):
         self._check(lib.dd4dv_reset_exchange(self._h))
@@ -287,12 +340,14 @@ class Context:
 
     # ---- outer loop (Alg. 1) ----
     def outer_step(self, solver=None, stats=None):
+        self._fwd_token += 1
         solver = solver or solver_defaults()
         stats = stats if stats is not None else _abi.dd4dv_stats()
         self._check(lib.dd4dv_outer_step(self._h, C.byref(solver), C.byref(stats)))
         return stats
 
     def run(self, solver=None):
+        self._fwd_token += 1
         solver = solver or solver_defaults()
         stats = _abi.dd4dv_stats()
         xa = np.zeros((3, self.nlat, self.nlon))
@@ -303,14 +358,16 @@ class Context:
     def get_controls(self, out=None):
         dev = out is not None and _is_torch_cuda(out)
         w = out if out is not None else np.zeros(self.ctrl_total)
-        self._check(lib.dd4dv_get_controls(self._h, _ptr(w, np.float64, dev), int(dev)))
+        call = lambda: lib.dd4dv_get_controls(self._h, _ptr(w, np.float64, dev), int(dev))
+        self._check(self._device_call(call, w) if dev else call())
         return w
 
     def set_controls(self, w):
         dev = _is_torch_cuda(w)
         if not dev:
             w = np.ascontiguousarray(w, dtype=np.float64)
-        self._check(lib.dd4dv_set_controls(self._h, _ptr(w, np.float64, dev), int(dev)))
+        call = lambda: lib.dd4dv_set_controls(self._h, _ptr(w, np.float64, dev), int(dev))
+        self._check(self._device_call(call, w) if dev else call())
 
     # ---- packed-layout helpers ----
     def split_controls(self, w) -> list:

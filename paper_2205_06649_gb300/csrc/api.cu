@@ -68,10 +68,16 @@ struct dd4dv_ctx {
   int* order_d = nullptr;
   long long ctrl_total = 0, traj_elems = 0, ptraj_total = 0, pt_steps = 0;
   int max_nx = 0, max_ny = 0, min_ny = 0, max_levels = 0, max_pts = 0;
-  int cl = 1, R = 1, W = 3;
+  int cl = 1, R = 1, W = 3, nthreads = 256;
+  double tune_ms = 0.0;
   size_t tsize = 8;
 
   void* traj = nullptr;
+  void* seg = nullptr;        // checkpoint-segment buffers (ckpt_k > 0)
+  int ckpt = 0;
+  void* stg = nullptr;        // RK3 stage states (nullptr: the adjoint recomputes them)
+  long long stg_elems = 0;
+  bool use_stg = false;
   void* tgt = nullptr;
   void* bnd = nullptr;
   double *xb_a = nullptr, *w = nullptr, *w_prev = nullptr, *g = nullptr, *wt = nullptr,
@@ -213,6 +219,9 @@ SweepArgs<T> sweep_args(dd4dv_ctx* ctx) {
   a.order = ctx->order_d;
   a.n_sub = ctx->n_sub;
   a.traj = static_cast<T*>(ctx->traj);
+  a.stg = ctx->use_stg ? static_cast<T*>(ctx->stg) : nullptr;
+  a.ckpt = ctx->ckpt;
+  a.seg = static_cast<T*>(ctx->seg);
   a.tgt = static_cast<const T*>(ctx->tgt);
   a.bnd = static_cast<const T*>(ctx->bnd);
   a.rows = ctx->rows_d;
@@ -277,12 +286,18 @@ void apply_VT(dd4dv_ctx* ctx, const double* y, const double* w, const double* sc
   KL(launch_grad_finish(ctx->subs_d, ctx->n_sub, w, ctx->vw2, scale, out, active, av, ctx->max_pts, ctx->st));
 }
 
+// full = true stores every level (exchange, trajectory export) even when the
+// evaluations checkpoint.
 template <typename T>
-void forward_sweep(dd4dv_ctx* ctx, const int* active, int av) {
+void forward_sweep(dd4dv_ctx* ctx, const int* active, int av, bool full = false) {
   SweepArgs<T> a = sweep_args<T>(ctx);
   a.active = active;
   a.active_value = av;
-  KL(launch_forward<T>(a, ctx->cl, 256, ctx->st));
+  if (full) {
+    a.ckpt = 0;
+    a.stg = nullptr;
+  }
+  KL(launch_forward<T>(a, ctx->cl, ctx->nthreads, ctx->st));
 }
 
 template <typename T>
@@ -296,7 +311,7 @@ void eval_T(dd4dv_ctx* ctx, const double* w, double* J, double* grad, double* pa
     SweepArgs<T> a = sweep_args<T>(ctx);
     a.active = active;
     a.active_value = av;
-    KL(launch_adjoint<T>(a, ctx->cl, 256, ctx->st));
+    KL(launch_adjoint<T>(a, ctx->cl, ctx->nthreads, ctx->st));
     apply_VT(ctx, ctx->lam_a, w, scale, grad, active, av);
   }
 }
@@ -304,7 +319,7 @@ void eval_T(dd4dv_ctx* ctx, const double* w, double* J, double* grad, double* pa
 template <typename T>
 void exchange_T(dd4dv_ctx* ctx, const double* w) {
   init_states<T>(ctx, w, ctx->vw, nullptr, 0);
-  forward_sweep<T>(ctx, nullptr, 0);
+  forward_sweep<T>(ctx, nullptr, 0, true);
   ExchArgs<T> x{};
   x.subs = ctx->subs_d;
   x.n_sub = ctx->n_sub;
@@ -371,6 +386,82 @@ auto by_precision(dd4dv_ctx* ctx, F&& f) {
   return f(double{});
 }
 
+// Times one J / grad J evaluation (at w = 0) for every feasible launch shape
+// (CTAs per subdomain x threads per CTA) and keeps the fastest.  The sweeps'
+// results do not depend on the shape except for the order of the per-CTA
+// partial sums of J.
+void autotune(dd4dv_ctx* ctx) {
+  const bool f32 = ctx->m.precision == 1;
+  const size_t smem_cap = 232448;
+  CK(cudaMemsetAsync(ctx->io_a, 0, ctx->ctrl_total * sizeof(double), ctx->st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int best_cl = ctx->cl, best_nt = ctx->nthreads;
+  bool best_stg = ctx->use_stg;
+  const bool have_stg = ctx->stg != nullptr;
+  for (int use : {1, 0}) {
+  if (use && !have_stg) continue;
+  ctx->use_stg = use;
+  for (int c : {1, 2, 3, 4, 5, 6, 7, 8, 16}) {
+    if (c > ctx->min_ny) break;
+    const int R = (ctx->max_ny + c - 1) / c;
+    const size_t sm = f32 ? smem_adjoint<float>(R, ctx->W) : smem_adjoint<double>(R, ctx->W);
+    if (sm > smem_cap) continue;
+    for (int nt : {256, 512}) {
+      ctx->cl = c;
+      ctx->R = R;
+      ctx->nthreads = nt;
+      double t = 0.0;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {
+        CK(cudaEventRecord(e0, ctx->st));
+        try {
+          by_precision(ctx, [&](auto tt) {
+            using T = decltype(tt);
+            eval_T<T>(ctx, ctx->io_a, ctx->io_p, ctx->io_b, nullptr, nullptr, 0, nullptr);
+            return 0;
+          });
+        } catch (const Fail&) {
+          ok = false;       // shape not launchable (e.g. cluster too large)
+          cudaGetLastError();
+          ctx->err.clear();
+          break;
+        }
+        CK(cudaEventRecord(e1, ctx->st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0) t += ms;
+      }
+      if (ok && t / 2 < best * 0.98) {
+        best = t / 2;
+        best_cl = c;
+        best_nt = nt;
+        best_stg = use;
+      }
+    }
+  }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->cl = best_cl;
+  ctx->R = (ctx->max_ny + best_cl - 1) / best_cl;
+  ctx->nthreads = best_nt;
+  ctx->use_stg = best_stg;
+  ctx->dec.cluster = best_cl;
+  ctx->tune_ms = best;
+  sync(ctx);
+  if (!best_stg && ctx->stg) {   // recomputing the stages won: give the memory back
+    auto it = std::find(ctx->dec_allocs.begin(), ctx->dec_allocs.end(), ctx->stg);
+    if (it != ctx->dec_allocs.end()) ctx->dec_allocs.erase(it);
+    cudaFree(ctx->stg);
+    ctx->stg = nullptr;
+    ctx->stg_elems = 0;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Decomposition tables.
 std::vector<int> make_cuts(dd4dv_ctx* ctx, const int* cuts, int n, int parts, const char* name) {
@@ -415,11 +506,11 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
       const int core = ctx->t_cuts[k + 1] - ctx->t_cuts[k];
       if (core < 2 * d.o_t + 1) fail(ctx, DD4DV_EINVAL, "time core block %d (%d) < 2*o_t+1", k, core);
     }
-  if (d.ckpt_k != 0) fail(ctx, DD4DV_EINVAL, "trajectory checkpointing (ckpt_k != 0) is not available in this build");
+  if (d.ckpt_k < -1) fail(ctx, DD4DV_EINVAL, "ckpt_k must be >= -1");
 
   const int n_sub = d.P1 * d.P2 * d.Q;
   std::vector<SubDesc> subs(n_sub);
-  long long ctrl = 0, trj = 0, ptrj = 0, pts = 0;
+  long long ctrl = 0, trj = 0, ptrj = 0, pts = 0, stgl = 0, segl = 0;
   int max_nx = 0, max_ny = 0, min_ny = 1 << 30, max_lv = 0, max_pts = 0;
   for (int q = 0; q < d.Q; ++q)
     for (int p2 = 0; p2 < d.P2; ++p2)
@@ -456,6 +547,10 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
         s.ctrl_off = ctrl;
         s.traj_off = trj;
         s.ptraj_off = ptrj;
+        s.stg_off = stgl;
+        stgl += (long long)L * 2 * 3 * s.ny * s.nxp;
+        s.seg_off = segl;
+        if (d.ckpt_k > 0) segl += (long long)(std::min(d.ckpt_k, std::max(L, 1)) + 1) * 3 * s.ny * s.nxp;
         ctrl += 3LL * s.ny * s.nx;
         trj += (long long)(L + 1) * 3 * s.ny * s.nxp;
         ptrj += (long long)(L + 1) * 3 * s.ny * s.nx;
@@ -602,6 +697,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
     return f32 ? smem_adjoint<float>(R, ctx->W) : smem_adjoint<double>(R, ctx->W);
   };
   int cl = d.cluster;
+  ctx->nthreads = 256;
   if (cl > 0) {
     if (cl > 16 || cl > min_ny) fail(ctx, DD4DV_EINVAL, "cluster size %d must be <= 16 and <= smallest box height %d", cl, min_ny);
     ctx->R = (max_ny + cl - 1) / cl;
@@ -646,6 +742,17 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
     return wx > wy;
   });
   ctx->traj = dalloc<unsigned char>(ctx, ctx->traj_elems * ctx->tsize, &L);
+  ctx->stg = nullptr;
+  ctx->stg_elems = 0;
+  ctx->use_stg = false;
+  ctx->ckpt = d.ckpt_k > 0 ? d.ckpt_k : 0;
+  ctx->seg = nullptr;
+  if (d.ckpt_k > 0) ctx->seg = dalloc<unsigned char>(ctx, std::max<long long>(1, segl) * ctx->tsize, &L);
+  if (d.ckpt_k == 0) {
+    ctx->stg_elems = stgl;
+    ctx->stg = dalloc<unsigned char>(ctx, std::max<long long>(1, stgl) * ctx->tsize, &L);
+    ctx->use_stg = true;
+  }
   ctx->tgt = dalloc<unsigned char>(ctx, ctx->traj_elems * ctx->tsize, &L);
   ctx->bnd = dalloc<unsigned char>(ctx, ctx->gtraj * ctx->tsize, &L);
   const size_t C = (size_t)ctrl;
@@ -666,7 +773,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   ctx->Jt = dalloc<double>(ctx, n_sub, &L);
   ctx->io_p = dalloc<double>(ctx, 5 * n_sub, &L);
   ctx->parts = dalloc<double>(ctx, 3 * n_sub, &L);
-  ctx->part = dalloc<double>(ctx, 2 * (size_t)n_sub * cl, &L);
+  ctx->part = dalloc<double>(ctx, 2 * (size_t)n_sub * 16, &L);
   ctx->vconst = dalloc<double>(ctx, n_sub, &L);
   ctx->vpart = dalloc<double>(ctx, (size_t)n_sub * ctx->vblocks, &L);
   ctx->ptraj_io = nullptr;
@@ -717,6 +824,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   });
   sync(ctx);
   ctx->has_dec = true;
+  if (d.cluster < 0) autotune(ctx);
 }
 
 }  // namespace
@@ -1022,7 +1130,7 @@ dd4dv_status dd4dv_eval_backward(dd4dv_ctx* ctx, const double* scale, double* gr
     by_precision(ctx, [&](auto t) {
       using T = decltype(t);
       SweepArgs<T> a = sweep_args<T>(ctx);
-      KL(launch_adjoint<T>(a, ctx->cl, 256, ctx->st));
+      KL(launch_adjoint<T>(a, ctx->cl, ctx->nthreads, ctx->st));
       apply_VT(ctx, ctx->lam_a, ctx->io_c, sc, gr, nullptr, 0);
       return 0;
     });
@@ -1045,8 +1153,15 @@ dd4dv_status dd4dv_tlm(dd4dv_ctx* ctx, const double* w_all, const double* dw_all
   return guard(ctx, [&] {
     require_dec(ctx);
     if (!w_all || !dw_all || !dx_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
-    const size_t need = ctx->m.precision == 1 ? smem_tlm<float>(ctx->R, ctx->W) : smem_tlm<double>(ctx->R, ctx->W);
-    if (need > 232448) fail(ctx, DD4DV_EINVAL, "tangent-linear sweep needs %zu bytes of shared memory at cluster size %d; use a larger cluster", need, ctx->cl);
+    // the tangent-linear sweep holds six buffers: use the smallest cluster
+    // (>= the evaluation's) whose stripes fit in shared memory
+    int tl_cl = -1, tl_R = 0;
+    for (int c = ctx->cl; c <= std::min(16, ctx->min_ny); ++c) {
+      const int R = (ctx->max_ny + c - 1) / c;
+      const size_t need = ctx->m.precision == 1 ? smem_tlm<float>(R, ctx->W) : smem_tlm<double>(R, ctx->W);
+      if (need <= 232448 && (c <= 8 || c == 16)) { tl_cl = c; tl_R = R; break; }
+    }
+    if (tl_cl < 0) fail(ctx, DD4DV_EINVAL, "boxes too large for the tangent-linear sweep");
     const size_t C = ctx->ctrl_total;
     const double* w = stage_in(ctx, w_all, ctx->io_a, C, device_ptrs);
     const double* dw = stage_in(ctx, dw_all, ctx->io_b, C, device_ptrs);
@@ -1067,7 +1182,8 @@ dd4dv_status dd4dv_tlm(dd4dv_ctx* ctx, const double* w_all, const double* dw_all
       SweepArgs<T> a = sweep_args<T>(ctx);
       a.dx0 = ctx->io_c;
       a.dx_out = out;
-      KL(launch_tlm<T>(a, ctx->cl, 256, ctx->st));
+      a.R = tl_R;
+      KL(launch_tlm<T>(a, tl_cl, ctx->nthreads, ctx->st));
       return 0;
     });
     ctx->fwd_pending = false;
@@ -1099,7 +1215,7 @@ dd4dv_status dd4dv_adjoint(dd4dv_ctx* ctx, const double* w_all, const double* y_
       forward_sweep<T>(ctx, nullptr, 0);
       SweepArgs<T> a = sweep_args<T>(ctx);
       a.yforce = y;
-      KL(launch_adjoint<T>(a, ctx->cl, 256, ctx->st));
+      KL(launch_adjoint<T>(a, ctx->cl, ctx->nthreads, ctx->st));
       apply_VT(ctx, ctx->lam_a, nullptr, nullptr, out, nullptr, 0);
       return 0;
     });
@@ -1121,7 +1237,7 @@ dd4dv_status dd4dv_trajectories(dd4dv_ctx* ctx, const double* w_all, double* tra
     by_precision(ctx, [&](auto t) {
       using T = decltype(t);
       init_states<T>(ctx, w, ctx->vw, nullptr, 0);
-      forward_sweep<T>(ctx, nullptr, 0);
+      forward_sweep<T>(ctx, nullptr, 0, true);
       KL(launch_export_traj<T>(ctx->subs_d, ctx->n_sub, static_cast<const T*>(ctx->traj), h_ref_of(ctx),
                                out, ctx->max_pts, ctx->max_levels, ctx->st));
       return 0;
@@ -1470,7 +1586,7 @@ dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps,
                              ctx->dec.lambda, ctx->dec.mu, ctx->io_p, nullptr, nullptr, 0, ctx->st));
         SweepArgs<T> a = sweep_args<T>(ctx);
         CK(cudaEventRecord(ev[2], ctx->st));
-        KL(launch_adjoint<T>(a, ctx->cl, 256, ctx->st));
+        KL(launch_adjoint<T>(a, ctx->cl, ctx->nthreads, ctx->st));
         CK(cudaEventRecord(ev[3], ctx->st));
         apply_VT(ctx, ctx->lam_a, ctx->io_a, nullptr, ctx->io_b, nullptr, 0);
         CK(cudaEventRecord(ev[5], ctx->st));
@@ -1493,6 +1609,18 @@ dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps,
     ctx->fwd_pending = false;
     return DD4DV_OK;
   });
+}
+
+dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* cctx, int* cluster, int* threads, int* stored_stages,
+                                double* eval_ms) {
+  auto* ctx = const_cast<dd4dv_ctx*>(cctx);
+  if (!ctx) return DD4DV_EINVAL;
+  if (!ctx->has_dec) return DD4DV_ESTATE;
+  if (cluster) *cluster = ctx->cl;
+  if (threads) *threads = ctx->nthreads;
+  if (stored_stages) *stored_stages = ctx->use_stg ? 1 : 0;
+  if (eval_ms) *eval_ms = ctx->tune_ms;
+  return DD4DV_OK;
 }
 
 dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* cctx, int* n) {

@@ -9,6 +9,9 @@
 //     at every point the subdomain shares with others (zero elsewhere);
 //   * boundary trajectory bnd = [nsteps+1][3][nlat][nlon] (type T), the
 //     partition-of-unity sum of the local trajectories (Eq. rest);
+//   * stage states stg[s] = [L steps][2 stages][3 vars][ny][nxp]: the RK3
+//     intermediate states x1, x2 of every step, stored by the forward sweep so
+//     that the adjoint sweep loads them instead of recomputing them;
 //   * controls, gradients, L-BFGS vectors: packed FP64 [3][ny][nx] per
 //     subdomain (SubDesc::ctrl_off).
 #pragma once
@@ -32,6 +35,8 @@ struct SubDesc {
   long long ctrl_off;         // packed control offset (doubles)
   long long traj_off;         // trajectory offset (elements of T)
   long long ptraj_off;        // packed public trajectory offset (doubles, pitch nx)
+  long long stg_off;          // stage-state offset (elements of T): [L][2][3][ny][nxp]
+  long long seg_off;          // checkpoint-segment buffer offset (elements of T): [k+1][3][ny][nxp]
 };
 
 struct ObsRec {               // one observation as seen by one subdomain
@@ -57,6 +62,10 @@ struct SweepArgs {
   const int* order;           // cluster -> subdomain (longest first)
   int n_sub;
   T* traj;
+  T* stg;                     // RK3 stage states x1, x2 of every step, or nullptr (recompute)
+  int ckpt;                   // 0: every level stored; k > 0: levels 0, k, 2k, ... stored and
+                              // each k-step segment recomputed in the adjoint
+  T* seg;                     // per-subdomain segment buffers for the recomputation
   const T* tgt;
   const T* bnd;
   const RowConst* rows;       // [nlat]

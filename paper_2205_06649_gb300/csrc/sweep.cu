@@ -152,13 +152,14 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
   __syncthreads();
 }
 
-// Load level l of this subdomain's stored trajectory into X (own rows and
-// interior halo rows straight from HBM, box-edge halos by rule), ghosts at
-// boundary level n.  Ends with a CTA barrier.
+// Load one stored state (own rows and interior halo rows straight from HBM,
+// box-edge halos by rule, ghost columns of own rows) whose ghosts come from
+// the boundary trajectory blended between levels nA and nB.  src points at the
+// [3][ny][nxp] block.  Ends with a CTA barrier.
 template <typename T>
-__device__ void load_level(const SweepArgs<T>& a, const Geo<T>& g, T* X, int l, int n) {
+__device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T* src, int nA, int nB,
+                           T wA, T wB) {
   const int nx = g.nx;
-  const T* src = a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp;
   const int r_lo = (g.rank > 0) ? -1 : 0;
   const int r_hi = (g.rank < g.CL - 1) ? g.Rn + 1 : g.Rn;
   const int nr = r_hi - r_lo;
@@ -176,7 +177,7 @@ __device__ void load_level(const SweepArgs<T>& a, const Geo<T>& g, T* X, int l, 
       const int v = idx / nx, k = idx - v * nx;
       X[off(g, v, -1, k)] = (g.flags & F_SWALL)
                                 ? ((v == 2) ? -X[off(g, v, 0, k)] : X[off(g, v, 0, k)])
-                                : bnd_val(a, n, n, (T)1, (T)0, v, g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
+                                : bnd_val(a, nA, nB, wA, wB, v, g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
     }
   }
   if (g.rank == g.CL - 1) {
@@ -185,7 +186,7 @@ __device__ void load_level(const SweepArgs<T>& a, const Geo<T>& g, T* X, int l, 
       X[off(g, v, g.Rn, k)] =
           (g.flags & F_NWALL)
               ? ((v == 2) ? -X[off(g, v, g.Rn - 1, k)] : X[off(g, v, g.Rn - 1, k)])
-              : bnd_val(a, n, n, (T)1, (T)0, v, g.d.j0 + g.ny, (g.d.i0 + k) % a.nlon);
+              : bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.ny, (g.d.i0 + k) % a.nlon);
     }
   }
   for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
@@ -198,11 +199,83 @@ __device__ void load_level(const SweepArgs<T>& a, const Geo<T>& g, T* X, int l, 
       val = side == 0 ? X[off(g, v, rr, nx - 1)] : X[off(g, v, rr, 0)];
     } else {
       const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + nx) % a.nlon;
-      val = bnd_val(a, n, n, (T)1, (T)0, v, g.d.j0 + g.R0 + rr, i);
+      val = bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.R0 + rr, i);
     }
     X[off(g, v, rr, side == 0 ? -1 : nx)] = val;
   }
   __syncthreads();
+}
+
+// Load up to three stored states at once (one pass, one barrier pair) so that
+// their global-load latencies overlap.  Same rules as load_state.
+template <typename T>
+__device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X, const T* const* src,
+                             const int* nA, const int* nB, const T* wA, const T* wB) {
+  const int nx = g.nx;
+  const int r_lo = (g.rank > 0) ? -1 : 0;
+  const int r_hi = (g.rank < g.CL - 1) ? g.Rn + 1 : g.Rn;
+  const int nr = r_hi - r_lo;
+  const int per = 3 * nr * nx;
+  for (int idx = threadIdx.x; idx < 3 * per; idx += blockDim.x) {
+    const int b = idx / per;
+    const int j = idx - b * per;
+    const int v = j / (nr * nx);
+    const int rem = j - v * nr * nx;
+    const int rr = rem / nx + r_lo;
+    const int k = rem - (rr - r_lo) * nx;
+    X[b][off(g, v, rr, k)] = src[b][((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k];
+  }
+  __syncthreads();
+  const bool periodic = g.flags & F_PERIODIC;
+  const int ne = 2 * 3 * nx;      // box-edge halo rows (both sides, all vars)
+  const int nc = 2 * 3 * g.Rn;    // ghost columns of own rows
+  for (int idx = threadIdx.x; idx < 3 * (ne + nc); idx += blockDim.x) {
+    const int b = idx / (ne + nc);
+    int j = idx - b * (ne + nc);
+    T* Y = X[b];
+    if (j < ne) {
+      const int side = j / (3 * nx);
+      const int rem = j - side * 3 * nx;
+      const int v = rem / nx, k = rem - v * nx;
+      if (side == 0 && g.rank == 0) {
+        Y[off(g, v, -1, k)] = (g.flags & F_SWALL)
+                                  ? ((v == 2) ? -Y[off(g, v, 0, k)] : Y[off(g, v, 0, k)])
+                                  : bnd_val(a, nA[b], nB[b], wA[b], wB[b], v, g.d.j0 - 1,
+                                            (g.d.i0 + k) % a.nlon);
+      } else if (side == 1 && g.rank == g.CL - 1) {
+        Y[off(g, v, g.Rn, k)] =
+            (g.flags & F_NWALL)
+                ? ((v == 2) ? -Y[off(g, v, g.Rn - 1, k)] : Y[off(g, v, g.Rn - 1, k)])
+                : bnd_val(a, nA[b], nB[b], wA[b], wB[b], v, g.d.j0 + g.ny, (g.d.i0 + k) % a.nlon);
+      }
+    } else {
+      j -= ne;
+      const int side = j / (3 * g.Rn);
+      const int rem = j - side * 3 * g.Rn;
+      const int v = rem / g.Rn;
+      const int rr = rem - v * g.Rn;
+      T val;
+      if (periodic) {
+        val = side == 0 ? Y[off(g, v, rr, nx - 1)] : Y[off(g, v, rr, 0)];
+      } else {
+        const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + nx) % a.nlon;
+        val = bnd_val(a, nA[b], nB[b], wA[b], wB[b], v, g.d.j0 + g.R0 + rr, i);
+      }
+      Y[off(g, v, rr, side == 0 ? -1 : nx)] = val;
+    }
+  }
+  __syncthreads();
+}
+
+// Level l of the stored trajectory, ghosts at boundary level n.
+template <typename T>
+__device__ __forceinline__ void load_level(const SweepArgs<T>& a, const Geo<T>& g, T* X, int l, int n) {
+  load_state(a, g, X, a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp, n, n, (T)1, (T)0);
+}
+
+template <typename T>
+__device__ __forceinline__ T* stage_ptr(const SweepArgs<T>& a, const Geo<T>& g, int l, int which) {
+  return a.stg + g.d.stg_off + ((size_t)l * 2 + which) * 3 * g.ny * g.d.nxp;
 }
 
 // Tendencies F(Z) at one point (Sec. 7, centred differences):
@@ -415,39 +488,46 @@ __device__ __forceinline__ bool setup_geo(const SweepArgs<T>& a, cg::cluster_gro
   return true;
 }
 
-// One RK3 stage on own rows: out = cx X + cy (Y + dt F(Y)).
+// One RK3 stage on own rows: out = cx X + cy (Y + dt F(Y)).  One point per
+// thread per iteration (pairing points per thread for instruction-level
+// parallelism measured slower on GB300: it doubles register pressure).
 template <typename T, bool DEV>
 __device__ void stage(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs, T* out,
                       const T* X, const T* Y, T cx, T cy) {
   const T dt = (T)a.dt, Bth = (T)a.Bth, gBth = (T)a.gBth, href = (T)a.h_ref;
+  const int P = g.P;
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
     const int rr = idx / g.nx, k = idx - rr * g.nx;
     const int o = (rr + 1) * g.W + k + 1;
     const int ri = rr + 1;
     T Fh, Fu, Fv;
-    rhs_pt<T, DEV>(Y, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.BinvC[ri], rs.gA[ri],
+    rhs_pt<T, DEV>(Y, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.BinvC[ri], rs.gA[ri],
                    rs.c[ri + 1], rs.c[ri - 1], Bth, gBth, href, Fh, Fu, Fv);
     if (cx == (T)0) {
       out[o] = cy * (Y[o] + dt * Fh);
-      out[o + g.P] = cy * (Y[o + g.P] + dt * Fu);
-      out[o + 2 * g.P] = cy * (Y[o + 2 * g.P] + dt * Fv);
+      out[o + P] = cy * (Y[o + P] + dt * Fu);
+      out[o + 2 * P] = cy * (Y[o + 2 * P] + dt * Fv);
     } else {
       out[o] = cx * X[o] + cy * (Y[o] + dt * Fh);
-      out[o + g.P] = cx * X[o + g.P] + cy * (Y[o + g.P] + dt * Fu);
-      out[o + 2 * g.P] = cx * X[o + 2 * g.P] + cy * (Y[o + 2 * g.P] + dt * Fv);
+      out[o + P] = cx * X[o + P] + cy * (Y[o + P] + dt * Fu);
+      out[o + 2 * P] = cx * X[o + 2 * P] + cy * (Y[o + 2 * P] + dt * Fv);
     }
   }
 }
 
 template <typename T>
-__device__ void store_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int l) {
-  T* dst = a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp;
+__device__ void store_block(const Geo<T>& g, const T* X, T* dst) {
   for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
     const int v = idx / (g.Rn * g.nx);
     const int rem = idx - v * g.Rn * g.nx;
     const int rr = rem / g.nx, k = rem - rr * g.nx;
     dst[((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k] = X[off(g, v, rr, k)];
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int l) {
+  store_block(g, X, a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp);
 }
 
 template <typename T>
@@ -483,7 +563,7 @@ size_t smem_bytes(int nbuf, int R, int W) {
 // Forward sweep: x(a) (stored at level 0 by the init kernel) -> x(a+1..b),
 // trajectory stored at every level, J_o and J_mu partial sums per CTA.
 template <typename T>
-__global__ void __launch_bounds__(256) fwd_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(512) fwd_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;
@@ -504,11 +584,14 @@ __global__ void __launch_bounds__(256) fwd_kernel(SweepArgs<T> a) {
     const int n = g.a + l;
     stage<T, DEV>(a, g, rs, S1, X, X, (T)0, (T)1);
     complete_buf(cl, a, g, S1, K_STATE, n + 1, n + 1, (T)1, (T)0);
+    // stores read the buffer with another thread mapping: after the barrier
+    if (a.stg) store_block(g, S1, stage_ptr(a, g, l, 0));
     stage<T, DEV>(a, g, rs, S2, X, S1, (T)0.75, (T)0.25);
     complete_buf(cl, a, g, S2, K_STATE, n, n + 1, (T)0.5, (T)0.5);
+    if (a.stg) store_block(g, S2, stage_ptr(a, g, l, 1));
     stage<T, DEV>(a, g, rs, X, X, S2, (T)(1.0 / 3.0), (T)(2.0 / 3.0));
     complete_buf(cl, a, g, X, K_STATE, n + 1, n + 1, (T)1, (T)0);
-    store_level(a, g, X, l + 1);
+    if (a.ckpt == 0 || (l + 1) % a.ckpt == 0) store_level(a, g, X, l + 1);
     obs_level(a, g, X, l + 1, Jo);
     overlap_level(a, g, X, l + 1, Jm);
   }
@@ -573,7 +656,7 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
 // Adjoint sweep: lambda(b) = forcing(b); lambda(n) = M_n^T lambda(n+1) + forcing(n),
 // the RK3 stages recomputed from the stored x(n).  Writes lambda(a) to lam_a.
 template <typename T>
-__global__ void __launch_bounds__(256) adj_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(512) adj_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;
@@ -589,31 +672,74 @@ __global__ void __launch_bounds__(256) adj_kernel(SweepArgs<T> a) {
   T* L2 = buf[4];
   load_rows(a, g, rs);
   for (int i = threadIdx.x; i < 3 * g.P; i += blockDim.x) Lp[i] = (T)0;
-  load_level(a, g, X, g.L, g.a + g.L);
-  add_forcing(a, g, Lp, X, g.L);
-  complete_buf(cl, a, g, Lp, K_ADJ, 0, 0, (T)1, (T)0);
   const T dt = (T)a.dt, Bth = (T)a.Bth, gBth = (T)a.gBth, href = (T)a.h_ref;
   const T c23 = (T)(2.0 / 3.0), c13 = (T)(1.0 / 3.0);
   const int wall_s = (g.flags & F_SWALL) ? 1 : 0;
   const int wall_n = (g.flags & F_NWALL) ? 2 : 0;
-  for (int l = g.L - 1; l >= 0; --l) {
+  const size_t lvl_sz = (size_t)3 * g.ny * g.d.nxp;
+  const int K = (a.ckpt > 0 && g.L > 0) ? a.ckpt : 0;
+  T* segbuf = K ? a.seg + g.d.seg_off : nullptr;
+  const int nseg = K ? (g.L + K - 1) / K : 1;
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+  // levels [l0, l1] of this segment; without checkpoints one segment [0, L]
+  const int l0 = K ? sgi * K : 0;
+  const int l1 = K ? min(l0 + K, g.L) : g.L;
+  // source of level l: the stored trajectory, or the recomputed segment
+  auto level_src = [&](int l) -> const T* {
+    if (!K || l == l0) return a.traj + g.d.traj_off + (size_t)l * lvl_sz;
+    return segbuf + (size_t)(l - l0) * lvl_sz;
+  };
+  if (K) {
+    // recompute x(l0+1 .. l1) from the checkpoint x(l0) into the segment buffer
+    load_level(a, g, X, l0, g.a + l0);
+    for (int l = l0; l < l1; ++l) {
+      const int n = g.a + l;
+      stage<T, DEV>(a, g, rs, X1, X, X, (T)0, (T)1);
+      complete_buf(cl, a, g, X1, K_STATE, n + 1, n + 1, (T)1, (T)0);
+      stage<T, DEV>(a, g, rs, X2, X, X1, (T)0.75, (T)0.25);
+      complete_buf(cl, a, g, X2, K_STATE, n, n + 1, (T)0.5, (T)0.5);
+      stage<T, DEV>(a, g, rs, X, X, X2, (T)(1.0 / 3.0), (T)(2.0 / 3.0));
+      complete_buf(cl, a, g, X, K_STATE, n + 1, n + 1, (T)1, (T)0);
+      store_block(g, X, segbuf + (size_t)(l + 1 - l0) * lvl_sz);
+    }
+    cl.sync();   // segment rows of every CTA written before any CTA reads its halo rows
+  }
+  if (sgi == nseg - 1) {
+    // lambda(b) = forcing(b)
+    load_state(a, g, X, level_src(g.L), g.a + g.L, g.a + g.L, (T)1, (T)0);
+    add_forcing(a, g, Lp, X, g.L);
+    complete_buf(cl, a, g, Lp, K_ADJ, 0, 0, (T)1, (T)0);
+  }
+  for (int l = l1 - 1; l >= l0; --l) {
     const int n = g.a + l;
-    load_level(a, g, X, l, n);
-    stage<T, DEV>(a, g, rs, X1, X, X, (T)0, (T)1);
-    complete_buf(cl, a, g, X1, K_STATE, n + 1, n + 1, (T)1, (T)0);
-    stage<T, DEV>(a, g, rs, X2, X, X1, (T)0.75, (T)0.25);
-    complete_buf(cl, a, g, X2, K_STATE, n, n + 1, (T)0.5, (T)0.5);
+    if (a.stg && !K) {   // x(n) and the stage states stored by the forward sweep
+      T* bufs[3] = {X, X1, X2};
+      const T* srcs[3] = {a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp,
+                          stage_ptr(a, g, l, 0), stage_ptr(a, g, l, 1)};
+      const int nA[3] = {n, n + 1, n};
+      const int nB[3] = {n, n + 1, n + 1};
+      const T wA[3] = {(T)1, (T)1, (T)0.5};
+      const T wB[3] = {(T)0, (T)0, (T)0.5};
+      load_states3(a, g, bufs, srcs, nA, nB, wA, wB);
+    } else {       // recompute the stage states from x(n)
+      load_state(a, g, X, level_src(l), n, n, (T)1, (T)0);
+      stage<T, DEV>(a, g, rs, X1, X, X, (T)0, (T)1);
+      complete_buf(cl, a, g, X1, K_STATE, n + 1, n + 1, (T)1, (T)0);
+      stage<T, DEV>(a, g, rs, X2, X, X1, (T)0.75, (T)0.25);
+      complete_buf(cl, a, g, X2, K_STATE, n, n + 1, (T)0.5, (T)0.5);
+    }
+    const int P = g.P;
     // lambda_x2 = 2/3 lambda' + 2/3 dt F'(x2)^T lambda'
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
       const int rr = idx / g.nx, k = idx - rr * g.nx;
       const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
-      rhs_adj_pt<T, DEV>(X2, Lp, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
+      rhs_adj_pt<T, DEV>(X2, Lp, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
                          rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
       L2[o] = c23 * (Lp[o] + dt * Gh);
-      L2[o + g.P] = c23 * (Lp[o + g.P] + dt * Gu);
-      L2[o + 2 * g.P] = c23 * (Lp[o + 2 * g.P] + dt * Gv);
+      L2[o + P] = c23 * (Lp[o + P] + dt * Gu);
+      L2[o + 2 * P] = c23 * (Lp[o + 2 * P] + dt * Gv);
     }
     complete_buf(cl, a, g, L2, K_ADJ, 0, 0, (T)1, (T)0);
     // lambda_x1 = 1/4 lambda_x2 + 1/4 dt F'(x1)^T lambda_x2   (into X2's buffer)
@@ -623,11 +749,11 @@ __global__ void __launch_bounds__(256) adj_kernel(SweepArgs<T> a) {
       const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
-      rhs_adj_pt<T, DEV>(X1, L2, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
+      rhs_adj_pt<T, DEV>(X1, L2, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
                          rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
       L1[o] = (T)0.25 * (L2[o] + dt * Gh);
-      L1[o + g.P] = (T)0.25 * (L2[o + g.P] + dt * Gu);
-      L1[o + 2 * g.P] = (T)0.25 * (L2[o + 2 * g.P] + dt * Gv);
+      L1[o + P] = (T)0.25 * (L2[o + P] + dt * Gu);
+      L1[o + 2 * P] = (T)0.25 * (L2[o + 2 * P] + dt * Gv);
     }
     complete_buf(cl, a, g, L1, K_ADJ, 0, 0, (T)1, (T)0);
     // lambda(n) = 1/3 lambda' + 3/4 lambda_x2 + lambda_x1 + dt F'(x)^T lambda_x1
@@ -636,15 +762,16 @@ __global__ void __launch_bounds__(256) adj_kernel(SweepArgs<T> a) {
       const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
-      rhs_adj_pt<T, DEV>(X, L1, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
+      rhs_adj_pt<T, DEV>(X, L1, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
                          rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
       Lp[o] = c13 * Lp[o] + (T)0.75 * L2[o] + L1[o] + dt * Gh;
-      Lp[o + g.P] = c13 * Lp[o + g.P] + (T)0.75 * L2[o + g.P] + L1[o + g.P] + dt * Gu;
-      Lp[o + 2 * g.P] = c13 * Lp[o + 2 * g.P] + (T)0.75 * L2[o + 2 * g.P] + L1[o + 2 * g.P] + dt * Gv;
+      Lp[o + P] = c13 * Lp[o + P] + (T)0.75 * L2[o + P] + L1[o + P] + dt * Gu;
+      Lp[o + 2 * P] = c13 * Lp[o + 2 * P] + (T)0.75 * L2[o + 2 * P] + L1[o + 2 * P] + dt * Gv;
     }
     __syncthreads();
     add_forcing(a, g, Lp, X, l);
     complete_buf(cl, a, g, Lp, K_ADJ, 0, 0, (T)1, (T)0);
+  }
   }
   // lambda(a) -> packed control layout (FP64)
   double* out = a.lam_a + g.d.ctrl_off;
@@ -722,7 +849,7 @@ __device__ void stage_tl(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) tlm_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(512) tlm_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;

@@ -181,3 +181,36 @@ def test_outer_loop_matches_oracle_dd4dvar():
         assert rel(ws, ref.w[s].numpy()) <= 1e-6, s
     assert abs(stats.J_sum - sum(ref.J_hist[-1])) <= 1e-8 * abs(sum(ref.J_hist[-1]))
     assert abs(stats.dw_inf - ref.dw_inf[-1]) <= 1e-6 * ref.dw_inf[-1]
+
+
+def test_autotuned_launch_shape_matches_oracle():
+    """The autotuner (cluster = -1) picks a launch shape by timing; whatever
+    it picks, the evaluation still matches the oracle."""
+    wl = workloads.preset("ragged")
+    st, inp, _ = _setup(wl)
+    ctx = make_context(wl, st, inp, cluster=-1)
+    cfg = ctx.sweep_config()
+    assert cfg["cluster"] >= 1 and cfg["threads"] in (256, 512) and cfg["eval_ms"] > 0
+    w = np.concatenate([rand_w(lp.nctrl, seed=800 + s).numpy() for s, lp in enumerate(st.locals)])
+    _check_eval(ctx, st, w, st.xb_traj, st.background_prev())
+
+
+def test_stored_and_recomputed_stages_agree_with_oracle():
+    """ckpt_k = 0 (stage states stored by the forward sweep) and ckpt_k = -1
+    (stage states recomputed in the adjoint) give the same J and grad J."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("ragged")
+    st, inp, _ = _setup(wl)
+    w = np.concatenate([rand_w(lp.nctrl, seed=900 + s).numpy() for s, lp in enumerate(st.locals)])
+    res = []
+    for ck in (0, -1):
+        ctx = dd.Context(wl.nlon, wl.nlat, inp["dt"], wl.nsteps, precision=0)
+        ctx.set_background(inp["x_b0"])
+        ctx.set_background_error(wl.sigma_b, wl.corr_len, wl.rf_passes)
+        ob = st.obs
+        ctx.set_observations(ob.level, ob.var, ob.fi, ob.fj, ob.value, ob.sigma_o)
+        ctx.set_decomposition(wl.P1, wl.P2, wl.Q, wl.o_lon, wl.o_lat, wl.o_t, inp["lon_cuts"],
+                              inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam, cluster=2, ckpt_k=ck)
+        res.append(_check_eval(ctx, st, w, st.xb_traj, st.background_prev()))
+        ctx.destroy()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
