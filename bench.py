@@ -47,11 +47,29 @@ UNIT = "grid-point-steps/s"
 # (3 values), the adjoint loads it back (3 values).
 FLOPS = {"forward": 141.0, "adjoint": 319.0}
 VALUES_PER_PTSTEP = {"forward": 3.0, "adjoint": 3.0}
+# With stored stage states the forward also stores x1, x2 (6 values) and the
+# adjoint loads them instead of recomputing two stages (2 RHS + 21 = 91 flops).
+FLOPS_STORED = {"forward": 141.0, "adjoint": 228.0}
+VALUES_STORED = {"forward": 9.0, "adjoint": 9.0}
 # FP64 on GB300: 2 FMA / clock / SM (the nominal 1.25 TFLOP/s over 152 SMs at
 # 2070 MHz); FP32: 128 FMA lanes / SM.
 N_SM = 152
 FP64_FLOP_PER_CLK_SM = 4.0
 FP32_FLOP_PER_CLK_SM = 256.0
+
+
+def aggregate_ranks(ms: float, pts: float, device: str):
+    """Max over ranks of the elapsed time and sum over ranks of the work
+    (replicas: the only collectives, none on the data path)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, pts
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    p = torch.tensor([pts], dtype=torch.float64, device=device)
+    dist.all_reduce(p, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(p.item())
 
 
 def log(*a):
@@ -331,16 +349,7 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    pts_local = float(stats.pt_steps)
-    t_max = ms
-    pts_all = pts_local
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        p = torch.tensor([pts_local], device="cuda", dtype=torch.float64)
-        dist.all_reduce(p, op=dist.ReduceOp.SUM)
-        pts_all = float(p.item())
+    t_max, pts_all = aggregate_ranks(ms, float(stats.pt_steps), "cuda")
     value = pts_all / (t_max / 1e3)
     clocks = clk.summary()
 
@@ -354,8 +363,11 @@ def main():
         peaks, peaks_kind = measured_peaks()
         sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
         tsize = 8 if prec == 0 else 4
-        flops = FLOPS[kern] * pts_eval / t_k
-        bytes_ = VALUES_PER_PTSTEP[kern] * tsize * pts_eval / t_k
+        stored = ctx.sweep_config()["stored_stages"]
+        fl = FLOPS_STORED if stored else FLOPS
+        vals = VALUES_STORED if stored else VALUES_PER_PTSTEP
+        flops = fl[kern] * pts_eval / t_k
+        bytes_ = vals[kern] * tsize * pts_eval / t_k
         hbm_peak = float(peaks["hbm_gbs"]) * 1e9
         if prec == 0:
             alu_peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6
@@ -375,6 +387,7 @@ def main():
                     "frac": hbm_frac, "traffic": traffic, "kernel": f"{kern} sweep",
                     "peak_source": f"hbm_gbs of {peaks_kind}", "alu_frac": alu_frac}
         roof["kernel_ms"] = prof[f"{kern}_ms"]
+        roof["algorithmic_per_pt_step"] = {"flops": fl[kern], "bytes": vals[kern] * tsize}
         roof["sweeps_ms"] = {"forward": prof["forward_ms"], "adjoint": prof["adjoint_ms"],
                              "eval": prof["eval_ms"]}
 

@@ -91,6 +91,11 @@ class Context:
         self.stream = stream if stream else None
         self.nlon, self.nlat, self.nsteps = nlon, nlat, nsteps
         self.n_sub = 0
+        self.ctrl_total = 0
+        self.traj_total = 0
+        self.offsets = np.zeros(1, dtype=np.int64)
+        self.traj_offsets = np.zeros(1, dtype=np.int64)
+        self.boxes = np.zeros((0, 6), dtype=np.int32)
         self._fwd_token = 0
 
     def _device_call(self, fn, *tensors):

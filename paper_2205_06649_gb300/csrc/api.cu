@@ -466,6 +466,11 @@ void autotune(dd4dv_ctx* ctx) {
 // Decomposition tables.
 std::vector<int> make_cuts(dd4dv_ctx* ctx, const int* cuts, int n, int parts, const char* name) {
   std::vector<int> c(parts + 1);
+  if (parts == 1) {   // one block: the whole axis, whatever was passed
+    c[0] = 0;
+    c[1] = n;
+    return c;
+  }
   if (cuts) {
     for (int k = 0; k <= parts; ++k) c[k] = cuts[k];
     if (c[0] != 0 || c[parts] != n) fail(ctx, DD4DV_EINVAL, "%s cuts must run from 0 to %d", name, n);

@@ -1,0 +1,39 @@
+"""Multi-GPU runs are replicas: bench.py's only collectives are a max over
+ranks of the elapsed time and a sum of the work.  Checked with world size 2
+on the gloo backend (CPU)."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t, p = bench.aggregate_ranks(10.0 + 5.0 * rank, 100.0 * (rank + 1), "cpu")
+    out[rank] = (t, p)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_aggregation_world_size_2():
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_worker, args=(2, _free_port(), out), nprocs=2, start_method="spawn")
+    assert out[0] == (15.0, 300.0) and out[1] == (15.0, 300.0)
+
+
+def test_single_process_aggregation_is_identity():
+    import bench
+    assert bench.aggregate_ranks(3.0, 7.0, "cpu") == (3.0, 7.0)
