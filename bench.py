@@ -134,7 +134,7 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def build_problem(wl, precision, stream, inputs=None):
+def build_problem(wl, precision, stream, inputs=None, shape=""):
     """Library context with truth run, synthetic observations and decomposition."""
     import paper_2205_06649_gb300 as dd
     inp = inputs if inputs is not None else workloads.generate(wl)
@@ -148,7 +148,11 @@ def build_problem(wl, precision, stream, inputs=None):
     ctx.set_background_error(wl.sigma_b, wl.corr_len, wl.rf_passes)
     ctx.set_observations(inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)
     ctx.set_decomposition(wl.P1, wl.P2, wl.Q, wl.o_lon, wl.o_lat, wl.o_t, inp["lon_cuts"],
-                          inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam, cluster=-1)
+                          inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam,
+                          cluster=-1 if not shape else 1)
+    if shape:
+        c, t, sg = (int(x) for x in shape.split(","))
+        ctx.set_sweep_config(c, t, bool(sg))
     return ctx, inp, truth, (inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)
 
 
@@ -305,6 +309,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip FP32 and time-to-analysis legs")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="only run this many evaluations (for an ncu launch list) and exit")
+    ap.add_argument("--shape", default="",
+                    help="cluster,threads,stored_stages: force the sweep launch shape "
+                         "(e.g. the one an autotuned run reported) instead of autotuning")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -325,7 +332,7 @@ def main():
     wl = workloads.preset(args.workload)
     prec = 0 if args.precision == "f64" else 1
     stream = torch.cuda.Stream()
-    ctx, inp, truth, obs = build_problem(wl, prec, stream.cuda_stream)
+    ctx, inp, truth, obs = build_problem(wl, prec, stream.cuda_stream, shape=args.shape)
     solver = solver_for(wl)
     zeros = torch.zeros(ctx.ctrl_total, dtype=torch.float64, device="cuda")
 

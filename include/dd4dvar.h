@@ -128,6 +128,10 @@ typedef struct {
   double eps_outer;        /* stop when max_s ||w_s^l - w_s^(l-1)||_inf < eps */
   double gtol_rel;         /* local stop when ||g|| / ||g_0|| < gtol       */
   double c1;               /* Armijo constant (1e-4)                       */
+  int use_graphs;          /* 1: each step of the iteration (start evaluation,
+                              L-BFGS direction, line-search trial, exchange) is
+                              captured once as a CUDA graph and replayed;
+                              0: launched eagerly.  Same results.        */
 } dd4dv_solver;
 
 typedef struct {
@@ -288,6 +292,12 @@ dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps,
  * ms of that shape.  Any pointer may be NULL. */
 dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* ctx, int* cluster, int* threads, int* stored_stages,
                                 double* eval_ms);
+
+/* Force a launch shape (e.g. one found by an earlier autotuning run):
+ * cluster 1..16, threads 256 or 512, stored_stages 1 (needs ckpt_k = 0 and the
+ * stage buffer) or 0.  Results are the same for every shape up to the order of
+ * the per-CTA partial sums of J. */
+dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, int cluster, int threads, int stored_stages);
 
 /* The cluster size (CTAs per subdomain) the sweeps use. */
 dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* ctx, int* n);

@@ -54,7 +54,7 @@ def _ptr(x, dtype, device: bool):
 
 def solver_defaults(**kw) -> _abi.dd4dv_solver:
     s = _abi.dd4dv_solver(lbfgs_m=5, max_local_iters=20, max_trials=20, max_outer=10,
-                          eps_outer=1e-6, gtol_rel=1e-6, c1=1e-4)
+                          eps_outer=1e-6, gtol_rel=1e-6, c1=1e-4, use_graphs=1)
     for k, v in kw.items():
         setattr(s, k, v)
     return s
@@ -185,6 +185,9 @@ class Context:
         self._check(lib.dd4dv_sweep_config(self._h, C.byref(c), C.byref(t), C.byref(sg), C.byref(ms)))
         return {"cluster": c.value, "threads": t.value, "stored_stages": bool(sg.value),
                 "eval_ms": ms.value}
+
+    def set_sweep_config(self, cluster: int, threads: int, stored_stages: bool):
+        self._check(lib.dd4dv_set_sweep_config(self._h, cluster, threads, int(stored_stages)))
 
     def pt_steps(self) -> int:
         n = C.c_longlong()

@@ -36,7 +36,7 @@ class dd4dv_decomp(C.Structure):
 class dd4dv_solver(C.Structure):
     _fields_ = [("lbfgs_m", C.c_int), ("max_local_iters", C.c_int), ("max_trials", C.c_int),
                 ("max_outer", C.c_int), ("eps_outer", C.c_double), ("gtol_rel", C.c_double),
-                ("c1", C.c_double)]
+                ("c1", C.c_double), ("use_graphs", C.c_int)]
 
 
 class dd4dv_stats(C.Structure):
@@ -82,6 +82,7 @@ PROTOTYPES = {
     "dd4dv_cluster_size": (C.c_int, [_CTX, c_int_p]),
     "dd4dv_sweep_config": (C.c_int, [_CTX, c_int_p, c_int_p, c_int_p, c_double_p]),
     "dd4dv_profile_sweeps": (C.c_int, [_CTX, _P, C.c_int, _P]),
+    "dd4dv_set_sweep_config": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_int]),
     "dd4dv_forward_noalloc": (C.c_int, [C.POINTER(dd4dv_model), _P, _P, C.c_void_p]),
     "dd4dv_last_error": (C.c_char_p, [_CTX]),
 }

@@ -102,6 +102,16 @@ struct dd4dv_ctx {
   int* err_d = nullptr;
   int vblocks = 8;
   bool fwd_pending = false;
+  LbState* lbst_h = nullptr;  // pinned
+  // captured CUDA graphs of the outer iteration (start evaluation, L-BFGS
+  // direction, one line-search trial, exchange), valid for one solver setting
+  struct Graphs {
+    cudaGraphExec_t start = nullptr, dir = nullptr, trial = nullptr, exch = nullptr;
+    long long k_start = 0, k_dir = 0, k_trial = 0, k_exch = 0;
+    dd4dv_solver key{};
+    bool valid = false;
+  } og;
+  void drop_graphs();
   std::vector<void*> dec_allocs;
 
   ~dd4dv_ctx();
@@ -851,8 +861,20 @@ dd4dv_ctx::~dd4dv_ctx() {
   if (own_stream && st) cudaStreamDestroy(st);
 }
 
+void dd4dv_ctx::drop_graphs() {
+  for (cudaGraphExec_t* g : {&og.start, &og.dir, &og.trial, &og.exch})
+    if (*g) {
+      cudaGraphExecDestroy(*g);
+      *g = nullptr;
+    }
+  og.valid = false;
+}
+
 void dd4dv_ctx::free_dec() {
   if (st) cudaStreamSynchronize(st);
+  drop_graphs();
+  cudaFreeHost(lbst_h);
+  lbst_h = nullptr;
   for (void* p : dec_allocs) cudaFree(p);
   dec_allocs.clear();
   cudaFreeHost(phase_h);
@@ -1024,7 +1046,8 @@ dd4dv_status dd4dv_set_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp* dec) {
     if (!ctx->has_bg || !ctx->has_berr || !ctx->has_obs)
       fail(ctx, DD4DV_ESTATE, "set_background, set_background_error and set_observations must come first");
     build_decomposition(ctx, *dec);
-    if (cudaMallocHost(&ctx->phase_h, ctx->n_sub * sizeof(int)) != cudaSuccess)
+    if (cudaMallocHost(&ctx->phase_h, ctx->n_sub * sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->lbst_h, ctx->n_sub * sizeof(LbState)) != cudaSuccess)
       fail(ctx, DD4DV_ENOMEM, "pinned host allocation failed");
     return DD4DV_OK;
   });
@@ -1385,6 +1408,7 @@ dd4dv_status dd4dv_observe(dd4dv_ctx* ctx, const double* traj, long long n, cons
 static void check_solver(dd4dv_ctx* ctx, const dd4dv_solver* s) {
   if (!s) fail(ctx, DD4DV_EINVAL, "solver is NULL");
   if (s->lbfgs_m < 1 || s->lbfgs_m > 8) fail(ctx, DD4DV_EINVAL, "lbfgs_m must be 1..8");
+  if (s->use_graphs != 0 && s->use_graphs != 1) fail(ctx, DD4DV_EINVAL, "use_graphs must be 0 or 1");
   if (s->max_local_iters < 0 || s->max_trials < 1 || s->max_outer < 0) fail(ctx, DD4DV_EINVAL, "bad iteration limits");
   if (!(s->c1 > 0.0 && s->c1 < 1.0)) fail(ctx, DD4DV_EINVAL, "c1 must be in (0,1)");
   if (!(s->gtol_rel >= 0.0) || !(s->eps_outer >= 0.0)) fail(ctx, DD4DV_EINVAL, "tolerances must be >= 0");
@@ -1392,6 +1416,34 @@ static void check_solver(dd4dv_ctx* ctx, const dd4dv_solver* s) {
 
 }  // extern "C"
 
+// Captures the work enqueued by f on the context stream into an executable
+// graph; *nk receives the number of this library's kernels in it.
+template <typename F>
+static cudaGraphExec_t capture_graph(dd4dv_ctx* ctx, F&& f, long long* nk) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->st, cudaStreamCaptureModeThreadLocal));
+  const long long k0 = ctx->launches;
+  try {
+    f();
+  } catch (...) {
+    cudaStreamEndCapture(ctx->st, &g);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    throw;
+  }
+  CK(cudaStreamEndCapture(ctx->st, &g));
+  *nk = ctx->launches - k0;
+  ctx->launches = k0;
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) fail(ctx, DD4DV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  return ge;
+}
+
+// One outer iteration of Algorithm 1.  The host loop only reads two counters
+// per step (subdomains still in a line search / needing a direction); the
+// device work of each step is one graph launch when sv.use_graphs is set.
 template <typename T>
 static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* stats) {
   LbArgs la{};
@@ -1414,15 +1466,63 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
   la.c1 = sv.c1;
   la.counter = ctx->counter_d;
   la.phase = ctx->phase_d;
+
+  auto q_start = [&] {   // evaluation at every local problem's start point
+    eval_T<T>(ctx, ctx->w, ctx->J, ctx->g, nullptr, nullptr, 0, nullptr);
+    LbArgs l2 = la;
+    l2.J_eval = ctx->J;
+    KL(launch_lb_start(l2, ctx->st));
+  };
+  auto q_dir = [&] {
+    CK(cudaMemsetAsync(ctx->counter_d, 0, 2 * sizeof(int), ctx->st));
+    LbArgs l2 = la;
+    l2.J_eval = ctx->Jt;
+    KL(launch_lb_direction(l2, ctx->st));
+    d2h(ctx, ctx->counter_h, ctx->counter_d, 2 * sizeof(int));
+  };
+  auto q_trial = [&] {   // masked batched evaluation at the trial points + Armijo
+    d2h(ctx, ctx->phase_h, ctx->phase_d, ctx->n_sub * sizeof(int));
+    eval_T<T>(ctx, ctx->wt, ctx->Jt, ctx->gt, nullptr, ctx->phase_d, 1, nullptr);
+    CK(cudaMemsetAsync(ctx->counter_d, 0, 2 * sizeof(int), ctx->st));
+    LbArgs l2 = la;
+    l2.J_eval = ctx->Jt;
+    KL(launch_lb_linesearch(l2, ctx->st));
+    d2h(ctx, ctx->counter_h, ctx->counter_d, 2 * sizeof(int));
+  };
+  auto q_exch = [&] {    // Exchange at the new local solutions, outer increment
+    exchange_T<T>(ctx, ctx->w);
+    KL(launch_max_abs_diff(ctx->w, ctx->w_prev, ctx->ctrl_total, ctx->scal_d, ctx->st));
+    CK(cudaMemcpyAsync(ctx->w_prev, ctx->w, ctx->ctrl_total * sizeof(double), cudaMemcpyDeviceToDevice,
+                       ctx->st));
+    d2h(ctx, ctx->scal_h, ctx->scal_d, sizeof(double));
+    d2h(ctx, ctx->lbst_h, ctx->lbst, ctx->n_sub * sizeof(LbState));
+  };
+
+  auto& og = ctx->og;
+  const bool graphs = sv.use_graphs != 0;
+  if (graphs && (!og.valid || std::memcmp(&og.key, &sv, sizeof(sv)) != 0)) {
+    ctx->drop_graphs();
+    og.start = capture_graph(ctx, q_start, &og.k_start);
+    og.dir = capture_graph(ctx, q_dir, &og.k_dir);
+    og.trial = capture_graph(ctx, q_trial, &og.k_trial);
+    og.exch = capture_graph(ctx, q_exch, &og.k_exch);
+    og.key = sv;
+    og.valid = true;
+  }
+  auto run = [&](auto& q, cudaGraphExec_t ge, long long nk) {
+    if (graphs) {
+      CK(cudaGraphLaunch(ge, ctx->st));
+      ctx->launches += nk;
+    } else {
+      q();
+    }
+  };
+
   long long evals = 0, sub_evals = 0, pts = 0;
-  // evaluation at the starting point of every local problem
-  eval_T<T>(ctx, ctx->w, ctx->J, ctx->g, nullptr, nullptr, 0, nullptr);
+  run(q_start, og.start, og.k_start);
   ++evals;
   sub_evals += ctx->n_sub;
   pts += ctx->pt_steps;
-  la.J_eval = ctx->J;
-  KL(launch_lb_start(la, ctx->st));
-  la.J_eval = ctx->Jt;
   std::vector<long long> sub_pts(ctx->n_sub);
   for (int s = 0; s < ctx->n_sub; ++s) {
     const SubDesc& d = ctx->subs_h[s];
@@ -1430,17 +1530,11 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
   }
   const int guard_iters = sv.max_local_iters + 2;
   for (int it = 0; it < guard_iters; ++it) {
-    CK(cudaMemsetAsync(ctx->counter_d, 0, 2 * sizeof(int), ctx->st));
-    KL(launch_lb_direction(la, ctx->st));
-    d2h(ctx, ctx->counter_h, ctx->counter_d, 2 * sizeof(int));
+    run(q_dir, og.dir, og.k_dir);
     CK(cudaStreamSynchronize(ctx->st));
     if (ctx->counter_h[0] == 0) break;
     for (int tr = 0; tr < sv.max_trials; ++tr) {
-      d2h(ctx, ctx->phase_h, ctx->phase_d, ctx->n_sub * sizeof(int));
-      eval_T<T>(ctx, ctx->wt, ctx->Jt, ctx->gt, nullptr, ctx->phase_d, 1, nullptr);
-      CK(cudaMemsetAsync(ctx->counter_d, 0, 2 * sizeof(int), ctx->st));
-      KL(launch_lb_linesearch(la, ctx->st));
-      d2h(ctx, ctx->counter_h, ctx->counter_d, 2 * sizeof(int));
+      run(q_trial, og.trial, og.k_trial);
       CK(cudaStreamSynchronize(ctx->st));
       ++evals;
       for (int s = 0; s < ctx->n_sub; ++s)
@@ -1451,14 +1545,7 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
       if (ctx->counter_h[0] == 0) break;
     }
   }
-  // Exchange at the new local solutions, outer increment, next start point
-  exchange_T<T>(ctx, ctx->w);
-  KL(launch_max_abs_diff(ctx->w, ctx->w_prev, ctx->ctrl_total, ctx->scal_d, ctx->st));
-  CK(cudaMemcpyAsync(ctx->w_prev, ctx->w, ctx->ctrl_total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-  d2h(ctx, ctx->scal_h, ctx->scal_d, sizeof(double));
-  std::vector<LbState> lst(ctx->n_sub);
-  std::vector<double> Jh(ctx->n_sub);
-  d2h(ctx, lst.data(), ctx->lbst, ctx->n_sub * sizeof(LbState));
+  run(q_exch, og.exch, og.k_exch);
   sync(ctx);
   if (stats) {
     stats->outer_iters += 1;
@@ -1468,10 +1555,11 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
     stats->dw_inf = ctx->scal_h[0];
     double Js = 0.0, gmax = 0.0;
     int fails = 0;
-    for (const LbState& s : lst) {
-      Js += s.J;
-      if (s.g0n > 0.0) gmax = std::max(gmax, s.gn / s.g0n);
-      if (s.status == 3) ++fails;
+    for (int s = 0; s < ctx->n_sub; ++s) {
+      const LbState& l = ctx->lbst_h[s];
+      Js += l.J;
+      if (l.g0n > 0.0) gmax = std::max(gmax, l.gn / l.g0n);
+      if (l.status == 3) ++fails;
     }
     stats->J_sum = Js;
     stats->gnorm_rel_max = gmax;
@@ -1626,6 +1714,26 @@ dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* cctx, int* cluster, int* thread
   if (stored_stages) *stored_stages = ctx->use_stg ? 1 : 0;
   if (eval_ms) *eval_ms = ctx->tune_ms;
   return DD4DV_OK;
+}
+
+dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, int cluster, int threads, int stored_stages) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (cluster < 1 || cluster > 16 || cluster > ctx->min_ny)
+      fail(ctx, DD4DV_EINVAL, "cluster must be 1..16 and <= the smallest box height %d", ctx->min_ny);
+    if (threads != 256 && threads != 512) fail(ctx, DD4DV_EINVAL, "threads must be 256 or 512");
+    if (stored_stages && !ctx->stg) fail(ctx, DD4DV_EINVAL, "no stage buffer (ckpt_k != 0 or freed by the autotuner)");
+    const int R = (ctx->max_ny + cluster - 1) / cluster;
+    const size_t need = ctx->m.precision == 1 ? smem_adjoint<float>(R, ctx->W) : smem_adjoint<double>(R, ctx->W);
+    if (need > 232448) fail(ctx, DD4DV_EINVAL, "cluster size %d needs too much shared memory", cluster);
+    ctx->cl = cluster;
+    ctx->R = R;
+    ctx->nthreads = threads;
+    ctx->use_stg = stored_stages != 0;
+    ctx->dec.cluster = cluster;
+    ctx->drop_graphs();
+    return DD4DV_OK;
+  });
 }
 
 dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* cctx, int* n) {

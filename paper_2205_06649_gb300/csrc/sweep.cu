@@ -25,6 +25,9 @@
 
 #include <cooperative_groups.h>
 
+#include <map>
+#include <mutex>
+
 namespace cg = cooperative_groups;
 
 namespace dd4dv {
@@ -436,6 +439,9 @@ __device__ void obs_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, in
 }
 
 // Overlap penalty at level l over own points: J_mu += 1/2 c sum_v (x - m)^2 / sb^2.
+// The differences and this level's partial sum are formed in the state
+// precision; the partial is added to the FP64 accumulator once per level (on
+// the FP64 path this is all FP64).
 template <typename T>
 __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int l, double& Jm) {
   const SubDesc& d = g.d;
@@ -443,19 +449,21 @@ __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X
   const bool any_s = d.wL || d.wR || d.wS || d.wN;
   if (!any_t && !any_s) return;
   const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
+  const T i0 = (T)a.isb2[0], i1 = (T)a.isb2[1], i2 = (T)a.isb2[2];
+  T part = (T)0;
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
     const int rr = idx / g.nx, k = idx - rr * g.nx;
     const int r = g.R0 + rr;
     const int c = overlap_count(g, l, r, k);
     if (c == 0) continue;
-    double acc = 0.0;
-#pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      const double e = (double)X[off(g, v, rr, k)] - (double)tg[((size_t)v * g.ny + r) * d.nxp + k];
-      acc += e * e * a.isb2[v];
-    }
-    Jm += 0.5 * c * acc;
+    const size_t go = (size_t)r * d.nxp + k;
+    const size_t pl = (size_t)g.ny * d.nxp;
+    const T e0 = X[off(g, 0, rr, k)] - tg[go];
+    const T e1 = X[off(g, 1, rr, k)] - tg[go + pl];
+    const T e2 = X[off(g, 2, rr, k)] - tg[go + 2 * pl];
+    part += (T)c * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
   }
+  Jm += 0.5 * (double)part;
 }
 
 template <typename T>
@@ -624,16 +632,18 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
   const bool any_s = d.wL || d.wR || d.wS || d.wN;
   if ((any_t || any_s) && a.mu != 0.0) {
     const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
+    const T m0 = (T)(a.mu * a.isb2[0]), m1 = (T)(a.mu * a.isb2[1]), m2 = (T)(a.mu * a.isb2[2]);
+    const size_t pl = (size_t)g.ny * d.nxp;
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
       const int rr = idx / g.nx, k = idx - rr * g.nx;
       const int r = g.R0 + rr;
       const int c = overlap_count(g, l, r, k);
       if (c == 0) continue;
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        const double e = (double)X[off(g, v, rr, k)] - (double)tg[((size_t)v * g.ny + r) * d.nxp + k];
-        Lb[off(g, v, rr, k)] += (T)(a.mu * c * e * a.isb2[v]);
-      }
+      const size_t go = (size_t)r * d.nxp + k;
+      const T cc = (T)c;
+      Lb[off(g, 0, rr, k)] += cc * m0 * (X[off(g, 0, rr, k)] - tg[go]);
+      Lb[off(g, 1, rr, k)] += cc * m1 * (X[off(g, 1, rr, k)] - tg[go + pl]);
+      Lb[off(g, 2, rr, k)] += cc * m2 * (X[off(g, 2, rr, k)] - tg[go + 2 * pl]);
     }
   }
   __syncthreads();
@@ -883,15 +893,36 @@ __global__ void __launch_bounds__(512) tlm_kernel(SweepArgs<T> a) {
   cl.sync();
 }
 
+// The dynamic shared-memory attribute is a cap: it is set once per kernel and
+// device to the device's opt-in maximum, together with permission for
+// non-portable (16-CTA) clusters, so that no attribute call is made again
+// (none lands inside a stream capture).
+template <typename K>
+cudaError_t raise_attributes(K kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, bool> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  bool& ok = done[{reinterpret_cast<const void*>(kernel), dev}];
+  if (ok) return cudaSuccess;
+  int cap = 0;
+  e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  ok = true;
+  return cudaSuccess;
+}
+
 template <typename T, typename K>
 cudaError_t launch_cluster(K kernel, const SweepArgs<T>& a, int cl, int nthreads, size_t smem,
                            cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = raise_attributes(kernel);
   if (e != cudaSuccess) return e;
-  if (cl > 8) {
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e != cudaSuccess) return e;
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.n_sub * cl), 1, 1);
   cfg.blockDim = dim3((unsigned)nthreads, 1, 1);
@@ -916,7 +947,7 @@ template <typename T> size_t smem_tlm(int R, int W) { return smem_bytes<T>(6, R,
 template <typename T>
 int occupancy_adjoint(int R, int W, int nthreads) {
   const size_t smem = smem_adjoint<T>(R, W);
-  if (cudaFuncSetAttribute(adj_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+  if (raise_attributes(adj_kernel<T>) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }

@@ -214,3 +214,20 @@ def test_stored_and_recomputed_stages_agree_with_oracle():
         res.append(_check_eval(ctx, st, w, st.xb_traj, st.background_prev()))
         ctx.destroy()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_graph_replay_equals_eager_launches():
+    """The outer iteration captured as CUDA graphs and replayed gives exactly
+    the eagerly launched result (same kernels, same order)."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("ragged")
+    st, inp, _ = _setup(wl)
+    out = []
+    for use in (0, 1):
+        ctx = make_context(wl, st, inp, cluster=2)
+        sv = dd.solver_defaults(max_local_iters=5, max_outer=2, eps_outer=0.0, use_graphs=use)
+        xa, stats, _ = ctx.run(sv)
+        out.append((xa, ctx.get_controls(), stats.pt_steps, stats.evals))
+        ctx.destroy()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2:] == out[1][2:]
