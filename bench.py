@@ -149,10 +149,10 @@ def build_problem(wl, precision, stream, inputs=None, shape=""):
     ctx.set_observations(inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)
     ctx.set_decomposition(wl.P1, wl.P2, wl.Q, wl.o_lon, wl.o_lat, wl.o_t, inp["lon_cuts"],
                           inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam,
-                          cluster=-1 if not shape else 1)
+                          cluster=-1 if not shape else 0)
     if shape:
-        c, t, sg = (int(x) for x in shape.split(","))
-        ctx.set_sweep_config(c, t, bool(sg))
+        cf, tf, ca, ta, sg = (int(x) for x in shape.split(","))
+        ctx.set_sweep_config((cf, tf), (ca, ta), bool(sg))
     return ctx, inp, truth, (inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)
 
 
@@ -310,8 +310,8 @@ def main():
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="only run this many evaluations (for an ncu launch list) and exit")
     ap.add_argument("--shape", default="",
-                    help="cluster,threads,stored_stages: force the sweep launch shape "
-                         "(e.g. the one an autotuned run reported) instead of autotuning")
+                    help="fwd_cluster,fwd_threads,adj_cluster,adj_threads,stored_stages: force the "
+                         "sweep launch shapes (e.g. ones an autotuned run reported) instead of autotuning")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -90,11 +90,11 @@ typedef struct {
  * 1/(number of subdomains containing it), the restriction weights of
  * Definition "Restriction of a function"; 0 gives weight 1.
  * cluster: CTAs per subdomain in the sweep kernels (thread-block cluster
- * size, 1..16); 0 = chosen from a model of the launch; -1 = autotune: every
- * feasible (cluster size, threads per CTA, stored or recomputed stage states
- * when ckpt_k = 0) combination is timed on one evaluation and the fastest is
- * kept (see dd4dv_sweep_config); if recomputation wins, the stage buffer is
- * freed.
+ * size, 1..16); 0 = chosen from a model of the launch; -1 = autotune: the
+ * forward and adjoint sweeps are timed at every feasible (cluster size, threads
+ * per CTA) shape, with stored and with recomputed stage states when
+ * ckpt_k = 0, and the fastest shape of each and the faster mode are kept (see
+ * dd4dv_sweep_config); if recomputation wins, the stage buffer is freed.
  * ckpt_k: trajectory storage for the adjoint.  0 = the forward sweep stores
  * every level and the two RK3 stage states of every step, and the adjoint
  * loads them (three times the memory of the states alone; on GB300 this
@@ -286,18 +286,18 @@ dd4dv_status dd4dv_launch_count(const dd4dv_ctx* ctx, long long* n);
  * stream around each launch. */
 dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps, double* ms);
 
-/* Launch shape of the sweeps: cluster size (CTAs per subdomain), threads
- * per CTA, whether the adjoint loads stored stage states (1) or recomputes
- * them (0), and (after autotuning, else 0) the measured evaluation time in
- * ms of that shape.  Any pointer may be NULL. */
-dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* ctx, int* cluster, int* threads, int* stored_stages,
-                                double* eval_ms);
+/* Launch shapes of the sweeps, shape[5] = {forward cluster size, forward
+ * threads per CTA, adjoint cluster size, adjoint threads per CTA, stored stage
+ * states (1) or recomputed (0)}; eval_ms (after autotuning, else 0) = the
+ * measured forward + adjoint time of those shapes.  Either pointer may be NULL. */
+dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* ctx, int* shape, double* eval_ms);
 
-/* Force a launch shape (e.g. one found by an earlier autotuning run):
- * cluster 1..16, threads 256 or 512, stored_stages 1 (needs ckpt_k = 0 and the
- * stage buffer) or 0.  Results are the same for every shape up to the order of
- * the per-CTA partial sums of J. */
-dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, int cluster, int threads, int stored_stages);
+/* Force launch shapes (e.g. ones an earlier autotuning run reported), same
+ * layout as dd4dv_sweep_config: cluster sizes 1..16 (<= smallest box height),
+ * threads a multiple of 32 in 64..512, stored stages 1 only with ckpt_k = 0
+ * and the stage buffer present.  Results are the same for every shape up to
+ * the order of the per-CTA partial sums of J. */
+dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape);
 
 /* The cluster size (CTAs per subdomain) the sweeps use. */
 dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* ctx, int* n);

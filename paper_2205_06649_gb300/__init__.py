@@ -176,18 +176,22 @@ class Context:
 
     # ---- queries ----
     def cluster_size(self) -> int:
+        """Cluster size of the adjoint sweep."""
         n = C.c_int()
         self._check(lib.dd4dv_cluster_size(self._h, C.byref(n)))
         return n.value
 
     def sweep_config(self) -> dict:
-        c, t, sg, ms = C.c_int(), C.c_int(), C.c_int(), C.c_double()
-        self._check(lib.dd4dv_sweep_config(self._h, C.byref(c), C.byref(t), C.byref(sg), C.byref(ms)))
-        return {"cluster": c.value, "threads": t.value, "stored_stages": bool(sg.value),
-                "eval_ms": ms.value}
+        sh = np.zeros(5, dtype=np.int32)
+        ms = C.c_double()
+        self._check(lib.dd4dv_sweep_config(self._h, C.c_void_p(sh.ctypes.data), C.byref(ms)))
+        return {"forward": [int(sh[0]), int(sh[1])], "adjoint": [int(sh[2]), int(sh[3])],
+                "stored_stages": bool(sh[4]), "eval_ms": ms.value}
 
-    def set_sweep_config(self, cluster: int, threads: int, stored_stages: bool):
-        self._check(lib.dd4dv_set_sweep_config(self._h, cluster, threads, int(stored_stages)))
+    def set_sweep_config(self, forward, adjoint, stored_stages: bool):
+        """forward, adjoint: (cluster size, threads per CTA)."""
+        sh = np.array([forward[0], forward[1], adjoint[0], adjoint[1], int(stored_stages)], dtype=np.int32)
+        self._check(lib.dd4dv_set_sweep_config(self._h, C.c_void_p(sh.ctypes.data)))
 
     def pt_steps(self) -> int:
         n = C.c_longlong()

@@ -80,9 +80,9 @@ PROTOTYPES = {
     "dd4dv_pt_steps": (C.c_int, [_CTX, c_ll_p]),
     "dd4dv_launch_count": (C.c_int, [_CTX, c_ll_p]),
     "dd4dv_cluster_size": (C.c_int, [_CTX, c_int_p]),
-    "dd4dv_sweep_config": (C.c_int, [_CTX, c_int_p, c_int_p, c_int_p, c_double_p]),
+    "dd4dv_sweep_config": (C.c_int, [_CTX, _P, c_double_p]),
     "dd4dv_profile_sweeps": (C.c_int, [_CTX, _P, C.c_int, _P]),
-    "dd4dv_set_sweep_config": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_int]),
+    "dd4dv_set_sweep_config": (C.c_int, [_CTX, _P]),
     "dd4dv_forward_noalloc": (C.c_int, [C.POINTER(dd4dv_model), _P, _P, C.c_void_p]),
     "dd4dv_last_error": (C.c_char_p, [_CTX]),
 }

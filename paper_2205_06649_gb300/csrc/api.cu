@@ -68,7 +68,8 @@ struct dd4dv_ctx {
   int* order_d = nullptr;
   long long ctrl_total = 0, traj_elems = 0, ptraj_total = 0, pt_steps = 0;
   int max_nx = 0, max_ny = 0, min_ny = 0, max_levels = 0, max_pts = 0;
-  int cl = 1, R = 1, W = 3, nthreads = 256;
+  int cl = 1, R = 1, W = 3, nthreads = 256;        // adjoint (and TLM base) sweep shape
+  int cl_f = 1, R_f = 1, nt_f = 256;               // forward sweep shape
   double tune_ms = 0.0;
   size_t tsize = 8;
 
@@ -254,7 +255,7 @@ SweepArgs<T> sweep_args(dd4dv_ctx* ctx) {
   a.sc_w = ctx->sc_w_d;
   a.lvl_sc = ctx->lvl_sc_d;
   a.part = ctx->part;
-  a.cl_max = ctx->cl;
+  a.cl_max = 16;   // part[] stride: room for the largest cluster
   a.active = nullptr;
   a.active_value = 0;
   a.lam_a = ctx->lam_a;
@@ -307,7 +308,8 @@ void forward_sweep(dd4dv_ctx* ctx, const int* active, int av, bool full = false)
     a.ckpt = 0;
     a.stg = nullptr;
   }
-  KL(launch_forward<T>(a, ctx->cl, ctx->nthreads, ctx->st));
+  a.R = ctx->R_f;
+  KL(launch_forward<T>(a, ctx->cl_f, ctx->nt_f, ctx->st));
 }
 
 template <typename T>
@@ -315,7 +317,7 @@ void eval_T(dd4dv_ctx* ctx, const double* w, double* J, double* grad, double* pa
             int av, const double* scale) {
   init_states<T>(ctx, w, ctx->vw, active, av);
   forward_sweep<T>(ctx, active, av);
-  KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, w, ctx->part, ctx->cl, ctx->vconst, ctx->dec.lambda,
+  KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, w, ctx->part, ctx->cl_f, ctx->vconst, ctx->dec.lambda,
                        ctx->dec.mu, J, parts, active, av, ctx->st));
   if (grad) {
     SweepArgs<T> a = sweep_args<T>(ctx);
@@ -396,74 +398,103 @@ auto by_precision(dd4dv_ctx* ctx, F&& f) {
   return f(double{});
 }
 
-// Times one J / grad J evaluation (at w = 0) for every feasible launch shape
-// (CTAs per subdomain x threads per CTA) and keeps the fastest.  The sweeps'
-// results do not depend on the shape except for the order of the per-CTA
-// partial sums of J.
+// The project's autotuner: for every feasible launch shape -- cluster size
+// (CTAs per subdomain) x threads per CTA -- and, when the stage buffer exists,
+// for stored and for recomputed stage states, it times the forward and the
+// adjoint sweep separately (CUDA events around each launch, evaluation at
+// w = 0) and keeps the fastest shape of each sweep and the faster stage mode.
+// Thread counts include ones that divide a CTA's points evenly.  The search
+// stops early when it has used a time budget of 40 evaluations (at least
+// 2 s).  Results do not depend on the shapes except for the order of the
+// per-CTA partial sums of J.
 void autotune(dd4dv_ctx* ctx) {
   const bool f32 = ctx->m.precision == 1;
-  const size_t smem_cap = 232448;
+  int dev = 0, cap = 232448;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   CK(cudaMemsetAsync(ctx->io_a, 0, ctx->ctrl_total * sizeof(double), ctx->st));
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  double best = 1e300;
-  int best_cl = ctx->cl, best_nt = ctx->nthreads;
-  bool best_stg = ctx->use_stg;
+  cudaEvent_t ev[4];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  auto smem_f = [&](int R) { return f32 ? smem_forward<float>(R, ctx->W) : smem_forward<double>(R, ctx->W); };
+  auto smem_a = [&](int R) { return f32 ? smem_adjoint<float>(R, ctx->W) : smem_adjoint<double>(R, ctx->W); };
+  // one evaluation's kernels at the shape (c, nt); returns false if not launchable
+  auto run = [&](int c, int nt, float* tf, float* ta) -> bool {
+    const int R = (ctx->max_ny + c - 1) / c;
+    ctx->cl_f = ctx->cl = c;
+    ctx->R_f = ctx->R = R;
+    ctx->nt_f = ctx->nthreads = nt;
+    try {
+      by_precision(ctx, [&](auto tt) {
+        using T = decltype(tt);
+        init_states<T>(ctx, ctx->io_a, ctx->vw, nullptr, 0);
+        CK(cudaEventRecord(ev[0], ctx->st));
+        forward_sweep<T>(ctx, nullptr, 0);
+        CK(cudaEventRecord(ev[1], ctx->st));
+        SweepArgs<T> a = sweep_args<T>(ctx);
+        CK(cudaEventRecord(ev[2], ctx->st));
+        KL(launch_adjoint<T>(a, ctx->cl, ctx->nthreads, ctx->st));
+        CK(cudaEventRecord(ev[3], ctx->st));
+        return 0;
+      });
+    } catch (const Fail&) {
+      cudaGetLastError();
+      ctx->err.clear();
+      return false;
+    }
+    CK(cudaEventSynchronize(ev[3]));
+    CK(cudaEventElapsedTime(tf, ev[0], ev[1]));
+    CK(cudaEventElapsedTime(ta, ev[2], ev[3]));
+    return true;
+  };
+  std::vector<int> cls;
+  for (int c : {1, 2, 3, 4, 5, 6, 7, 8, 16})
+    if (c <= ctx->min_ny && smem_a((ctx->max_ny + c - 1) / c) <= (size_t)cap) cls.push_back(c);
+  const int nts[] = {512, 448, 384, 320, 256, 192};
+  // reference time of the starting shape sets the budget
+  float tf0 = 0, ta0 = 0;
+  const int c0 = ctx->cl, n0 = ctx->nthreads;
+  run(c0, n0, &tf0, &ta0);
+  run(c0, n0, &tf0, &ta0);
+  const double budget_ms = std::max(2000.0, 40.0 * (tf0 + ta0));
+  double spent = 0.0;
+  struct Best { double t = 1e300; int c = 0, nt = 0; };
+  Best best_f[2], best_a[2];
   const bool have_stg = ctx->stg != nullptr;
   for (int use : {1, 0}) {
-  if (use && !have_stg) continue;
+    if (use && !have_stg) continue;
+    ctx->use_stg = use;
+    for (int c : cls)
+      for (int nt : nts) {
+        if (spent > budget_ms) break;
+        float tf = 0, ta = 0, tf2 = 0, ta2 = 0;
+        if (!run(c, nt, &tf, &ta)) continue;
+        if (!run(c, nt, &tf2, &ta2)) continue;
+        spent += tf + ta + tf2 + ta2;
+        tf = std::min(tf, tf2);
+        ta = std::min(ta, ta2);
+        if (smem_f((ctx->max_ny + c - 1) / c) <= (size_t)cap && tf < best_f[use].t) best_f[use] = {tf, c, nt};
+        if (ta < best_a[use].t) best_a[use] = {ta, c, nt};
+      }
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  int use = 0;
+  if (have_stg && best_f[1].c && best_a[1].c &&
+      (!best_f[0].c || best_f[1].t + best_a[1].t < best_f[0].t + best_a[0].t))
+    use = 1;
+  if (!best_f[use].c || !best_a[use].c) {   // nothing measured: keep the starting shape
+    best_f[use] = {tf0, c0, n0};
+    best_a[use] = {ta0, c0, n0};
+  }
   ctx->use_stg = use;
-  for (int c : {1, 2, 3, 4, 5, 6, 7, 8, 16}) {
-    if (c > ctx->min_ny) break;
-    const int R = (ctx->max_ny + c - 1) / c;
-    const size_t sm = f32 ? smem_adjoint<float>(R, ctx->W) : smem_adjoint<double>(R, ctx->W);
-    if (sm > smem_cap) continue;
-    for (int nt : {256, 512}) {
-      ctx->cl = c;
-      ctx->R = R;
-      ctx->nthreads = nt;
-      double t = 0.0;
-      bool ok = true;
-      for (int rep = 0; rep < 3 && ok; ++rep) {
-        CK(cudaEventRecord(e0, ctx->st));
-        try {
-          by_precision(ctx, [&](auto tt) {
-            using T = decltype(tt);
-            eval_T<T>(ctx, ctx->io_a, ctx->io_p, ctx->io_b, nullptr, nullptr, 0, nullptr);
-            return 0;
-          });
-        } catch (const Fail&) {
-          ok = false;       // shape not launchable (e.g. cluster too large)
-          cudaGetLastError();
-          ctx->err.clear();
-          break;
-        }
-        CK(cudaEventRecord(e1, ctx->st));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (rep > 0) t += ms;
-      }
-      if (ok && t / 2 < best * 0.98) {
-        best = t / 2;
-        best_cl = c;
-        best_nt = nt;
-        best_stg = use;
-      }
-    }
-  }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  ctx->cl = best_cl;
-  ctx->R = (ctx->max_ny + best_cl - 1) / best_cl;
-  ctx->nthreads = best_nt;
-  ctx->use_stg = best_stg;
-  ctx->dec.cluster = best_cl;
-  ctx->tune_ms = best;
+  ctx->cl_f = best_f[use].c;
+  ctx->nt_f = best_f[use].nt;
+  ctx->R_f = (ctx->max_ny + ctx->cl_f - 1) / ctx->cl_f;
+  ctx->cl = best_a[use].c;
+  ctx->nthreads = best_a[use].nt;
+  ctx->R = (ctx->max_ny + ctx->cl - 1) / ctx->cl;
+  ctx->dec.cluster = ctx->cl;
+  ctx->tune_ms = best_f[use].t + best_a[use].t;
   sync(ctx);
-  if (!best_stg && ctx->stg) {   // recomputing the stages won: give the memory back
+  if (!use && ctx->stg) {   // recomputing the stages won: give the memory back
     auto it = std::find(ctx->dec_allocs.begin(), ctx->dec_allocs.end(), ctx->stg);
     if (it != ctx->dec_allocs.end()) ctx->dec_allocs.erase(it);
     cudaFree(ctx->stg);
@@ -742,6 +773,9 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
     ctx->R = (max_ny + cl - 1) / cl;
   }
   ctx->cl = cl;
+  ctx->cl_f = cl;
+  ctx->R_f = ctx->R;
+  ctx->nt_f = ctx->nthreads;
 
   // device tables and buffers
   ctx->free_dec();
@@ -1133,7 +1167,7 @@ dd4dv_status dd4dv_eval_forward(dd4dv_ctx* ctx, const double* w_all, double* J_a
       using T = decltype(t);
       init_states<T>(ctx, ctx->io_c, ctx->vw, nullptr, 0);
       forward_sweep<T>(ctx, nullptr, 0);
-      KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, ctx->io_c, ctx->part, ctx->cl, ctx->vconst,
+      KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, ctx->io_c, ctx->part, ctx->cl_f, ctx->vconst,
                            ctx->dec.lambda, ctx->dec.mu, J, pa, nullptr, 0, ctx->st));
       return 0;
     });
@@ -1675,7 +1709,7 @@ dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps,
         CK(cudaEventRecord(ev[0], ctx->st));
         forward_sweep<T>(ctx, nullptr, 0);
         CK(cudaEventRecord(ev[1], ctx->st));
-        KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, ctx->io_a, ctx->part, ctx->cl, ctx->vconst,
+        KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, ctx->io_a, ctx->part, ctx->cl_f, ctx->vconst,
                              ctx->dec.lambda, ctx->dec.mu, ctx->io_p, nullptr, nullptr, 0, ctx->st));
         SweepArgs<T> a = sweep_args<T>(ctx);
         CK(cudaEventRecord(ev[2], ctx->st));
@@ -1704,33 +1738,41 @@ dd4dv_status dd4dv_profile_sweeps(dd4dv_ctx* ctx, const double* w_all, int reps,
   });
 }
 
-dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* cctx, int* cluster, int* threads, int* stored_stages,
-                                double* eval_ms) {
+dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* cctx, int* shape, double* eval_ms) {
   auto* ctx = const_cast<dd4dv_ctx*>(cctx);
   if (!ctx) return DD4DV_EINVAL;
   if (!ctx->has_dec) return DD4DV_ESTATE;
-  if (cluster) *cluster = ctx->cl;
-  if (threads) *threads = ctx->nthreads;
-  if (stored_stages) *stored_stages = ctx->use_stg ? 1 : 0;
+  if (shape) {
+    shape[0] = ctx->cl_f;
+    shape[1] = ctx->nt_f;
+    shape[2] = ctx->cl;
+    shape[3] = ctx->nthreads;
+    shape[4] = ctx->use_stg ? 1 : 0;
+  }
   if (eval_ms) *eval_ms = ctx->tune_ms;
   return DD4DV_OK;
 }
 
-dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, int cluster, int threads, int stored_stages) {
+dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape) {
   return guard(ctx, [&] {
     require_dec(ctx);
-    if (cluster < 1 || cluster > 16 || cluster > ctx->min_ny)
-      fail(ctx, DD4DV_EINVAL, "cluster must be 1..16 and <= the smallest box height %d", ctx->min_ny);
-    if (threads != 256 && threads != 512) fail(ctx, DD4DV_EINVAL, "threads must be 256 or 512");
-    if (stored_stages && !ctx->stg) fail(ctx, DD4DV_EINVAL, "no stage buffer (ckpt_k != 0 or freed by the autotuner)");
-    const int R = (ctx->max_ny + cluster - 1) / cluster;
-    const size_t need = ctx->m.precision == 1 ? smem_adjoint<float>(R, ctx->W) : smem_adjoint<double>(R, ctx->W);
-    if (need > 232448) fail(ctx, DD4DV_EINVAL, "cluster size %d needs too much shared memory", cluster);
-    ctx->cl = cluster;
-    ctx->R = R;
-    ctx->nthreads = threads;
-    ctx->use_stg = stored_stages != 0;
-    ctx->dec.cluster = cluster;
+    if (!shape) fail(ctx, DD4DV_EINVAL, "shape is NULL");
+    const int cf = shape[0], tf = shape[1], ca = shape[2], ta = shape[3], sg = shape[4];
+    for (int c : {cf, ca})
+      if (c < 1 || c > 16 || c > ctx->min_ny)
+        fail(ctx, DD4DV_EINVAL, "cluster sizes must be 1..16 and <= the smallest box height %d", ctx->min_ny);
+    for (int t : {tf, ta})
+      if (t < 64 || t > 512 || t % 32) fail(ctx, DD4DV_EINVAL, "threads must be a multiple of 32 in 64..512");
+    if (sg && !ctx->stg) fail(ctx, DD4DV_EINVAL, "no stage buffer (ckpt_k != 0 or freed by the autotuner)");
+    const int Rf = (ctx->max_ny + cf - 1) / cf, Ra = (ctx->max_ny + ca - 1) / ca;
+    const bool f32 = ctx->m.precision == 1;
+    if ((f32 ? smem_forward<float>(Rf, ctx->W) : smem_forward<double>(Rf, ctx->W)) > 232448 ||
+        (f32 ? smem_adjoint<float>(Ra, ctx->W) : smem_adjoint<double>(Ra, ctx->W)) > 232448)
+      fail(ctx, DD4DV_EINVAL, "shape needs too much shared memory");
+    ctx->cl_f = cf; ctx->nt_f = tf; ctx->R_f = Rf;
+    ctx->cl = ca; ctx->nthreads = ta; ctx->R = Ra;
+    ctx->use_stg = sg != 0;
+    ctx->dec.cluster = ca;
     ctx->drop_graphs();
     return DD4DV_OK;
   });

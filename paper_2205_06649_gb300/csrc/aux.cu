@@ -142,8 +142,8 @@ __global__ void finalize_J_kernel(const SubDesc* subs, const double* w, const do
   if (threadIdx.x == 0) {
     double Jo = 0.0, Jm = 0.0;
     for (int r = 0; r < ncl; ++r) {
-      Jo += part[((size_t)s * ncl + r) * 2 + 0];
-      Jm += part[((size_t)s * ncl + r) * 2 + 1];
+      Jo += part[((size_t)s * 16 + r) * 2 + 0];   // stride: SweepArgs::cl_max = 16
+      Jm += part[((size_t)s * 16 + r) * 2 + 1];
     }
     Jm += vconst[s];
     const double Jb = 0.5 * ww;

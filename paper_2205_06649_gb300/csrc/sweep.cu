@@ -39,6 +39,9 @@ struct Geo {
   int s, rank, CL, R0, Rn, nx, ny, L, a, R2, W, P, flags;
   int Rprev, Rnext;   // own-row counts of the south / north neighbour CTA
   SubDesc d;
+  T* gh;              // ghost cache: 3 slots of [6 R columns | 6 W rows] values
+  int* gh_tag;        // level held by each slot (-1: none)
+  int gh_len;         // values per slot
 };
 
 __device__ __forceinline__ void split_rows(int ny, int CL, int rank, int& R0, int& Rn) {
@@ -79,7 +82,7 @@ __device__ void load_rows(const SweepArgs<T>& a, const Geo<T>& g, RowSmem<T>& rs
 enum { K_STATE = 0, K_ADJ = 1, K_DELTA = 2 };
 
 // Boundary-trajectory value for variable v at global (j, i) blended between
-// levels nA and nB with weights wA, wB.
+// levels nA and nB with weights wA, wB (read from HBM).
 template <typename T>
 __device__ __forceinline__ T bnd_val(const SweepArgs<T>& a, int nA, int nB, T wA, T wB, int v, int j,
                                      int i) {
@@ -91,6 +94,100 @@ __device__ __forceinline__ T bnd_val(const SweepArgs<T>& a, int nA, int nB, T wA
   return wA * xa + wB * xb;
 }
 
+// ---- ghost cache --------------------------------------------------------
+// The ghost values a CTA needs at one level -- the west/east columns of its
+// own rows when the box has frozen lateral edges, the south/north rows when
+// its stripe touches a frozen box edge -- are copied into a slot of a 3-level
+// shared-memory ring with cp.async one step before they are used, so that the
+// completion after each stage reads shared memory instead of waiting on HBM.
+// Slot of level n: n mod 3; a lookup whose level is not in its slot falls back
+// to HBM (results never depend on the cache).
+// Slot layout: columns [side][var][R], then rows [side][var][W].
+
+__device__ __forceinline__ void cp_async_4or8(void* dst, const void* src, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename T>
+__device__ void ghost_prefetch(const SweepArgs<T>& a, const Geo<T>& g, int n) {
+  if constexpr (sizeof(T) == 8) return;   // FP64 path: no cache (registers, ALU-bound)
+  if (g.gh_len == 0 || n < 0 || n > a.nsteps) return;
+  const int slot = n % 3;
+  T* dst = g.gh + (size_t)slot * g.gh_len;
+  const size_t plane = (size_t)a.nlat * a.nlon;
+  const T* src = a.bnd + (size_t)n * 3 * plane;
+  const int R = g.R2 - 2;
+  if (!(g.flags & F_PERIODIC)) {
+    const int iw = (g.d.i0 - 1 + a.nlon) % a.nlon, ie = (g.d.i0 + g.nx) % a.nlon;
+    for (int idx = threadIdx.x; idx < 6 * g.Rn; idx += blockDim.x) {
+      const int side = idx / (3 * g.Rn);
+      const int rem = idx - side * 3 * g.Rn;
+      const int v = rem / g.Rn, rr = rem - v * g.Rn;
+      const int j = g.d.j0 + g.R0 + rr;
+      cp_async_4or8(dst + (side * 3 + v) * R + rr,
+                    src + ((size_t)v * a.nlat + j) * a.nlon + (side ? ie : iw), (int)sizeof(T));
+    }
+  }
+  const bool south = g.rank == 0 && !(g.flags & F_SWALL);
+  const bool north = g.rank == g.CL - 1 && !(g.flags & F_NWALL);
+  if (south || north) {
+    for (int idx = threadIdx.x; idx < 6 * g.nx; idx += blockDim.x) {
+      const int side = idx / (3 * g.nx);
+      if ((side == 0 && !south) || (side == 1 && !north)) continue;
+      const int rem = idx - side * 3 * g.nx;
+      const int v = rem / g.nx, k = rem - v * g.nx;
+      const int j = side ? g.d.j0 + g.ny : g.d.j0 - 1;
+      cp_async_4or8(dst + 6 * R + (side * 3 + v) * g.W + k,
+                    src + ((size_t)v * a.nlat + j) * a.nlon + (g.d.i0 + k) % a.nlon, (int)sizeof(T));
+    }
+  }
+  cp_async_commit();
+  if (threadIdx.x == 0) g.gh_tag[slot] = n;
+}
+
+// Ghost column of own row rr (side 0 = west, 1 = east) and ghost row value at
+// column k (side 0 = south, 1 = north), blended between levels nA and nB.
+template <typename T>
+__device__ __forceinline__ T gh_col(const SweepArgs<T>& a, const Geo<T>& g, int nA, int nB, T wA, T wB,
+                                    int side, int v, int rr) {
+  if constexpr (sizeof(T) == 8) {
+    const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + g.nx) % a.nlon;
+    return bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.R0 + rr, i);
+  }
+  const int R = g.R2 - 2;
+  const int sA = nA % 3, sB = nB % 3;
+  if (g.gh_tag[sA] == nA && (wB == (T)0 || g.gh_tag[sB] == nB)) {
+    const int o = (side * 3 + v) * R + rr;
+    const T xa = g.gh[(size_t)sA * g.gh_len + o];
+    if (wB == (T)0) return xa;
+    return wA * xa + wB * g.gh[(size_t)sB * g.gh_len + o];
+  }
+  const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + g.nx) % a.nlon;
+  return bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.R0 + rr, i);
+}
+
+template <typename T>
+__device__ __forceinline__ T gh_row(const SweepArgs<T>& a, const Geo<T>& g, int nA, int nB, T wA, T wB,
+                                    int side, int v, int k) {
+  if constexpr (sizeof(T) == 8)
+    return bnd_val(a, nA, nB, wA, wB, v, side ? g.d.j0 + g.ny : g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
+  const int R = g.R2 - 2;
+  const int sA = nA % 3, sB = nB % 3;
+  if (g.gh_tag[sA] == nA && (wB == (T)0 || g.gh_tag[sB] == nB)) {
+    const int o = 6 * R + (side * 3 + v) * g.W + k;
+    const T xa = g.gh[(size_t)sA * g.gh_len + o];
+    if (wB == (T)0) return xa;
+    return wA * xa + wB * g.gh[(size_t)sB * g.gh_len + o];
+  }
+  return bnd_val(a, nA, nB, wA, wB, v, side ? g.d.j0 + g.ny : g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
+}
+
 // Complete a buffer whose own rows were just written by this CTA: cluster
 // barrier, halo rows from the neighbour CTAs (DSMEM) or from the box-edge rule
 // (wall mirror, frozen boundary trajectory, or zero), ghost columns of the own
@@ -98,6 +195,7 @@ __device__ __forceinline__ T bnd_val(const SweepArgs<T>& a, int nA, int nB, T wA
 template <typename T>
 __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const Geo<T>& g, T* X,
                              int kind, int nA, int nB, T wA, T wB) {
+  if constexpr (sizeof(T) == 4) cp_async_wait_all();   // this thread's ghost copies land first
   cl.sync();
   const int nx = g.nx;
   const bool periodic = g.flags & F_PERIODIC;
@@ -117,7 +215,7 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
         val = (kind == K_ADJ) ? (T)0 : ((v == 2) ? -X[off(g, v, 0, k)] : X[off(g, v, 0, k)]);
       } else {
         val = (kind == K_STATE)
-                  ? bnd_val(a, nA, nB, wA, wB, v, g.d.j0 - 1, (g.d.i0 + k) % a.nlon)
+                  ? gh_row(a, g, nA, nB, wA, wB, 0, v, k)
                   : (T)0;
       }
       X[off(g, v, -1, k)] = val;
@@ -129,7 +227,7 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
                               : ((v == 2) ? -X[off(g, v, g.Rn - 1, k)] : X[off(g, v, g.Rn - 1, k)]);
       } else {
         val = (kind == K_STATE)
-                  ? bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.ny, (g.d.i0 + k) % a.nlon)
+                  ? gh_row(a, g, nA, nB, wA, wB, 1, v, k)
                   : (T)0;
       }
       X[off(g, v, g.Rn, k)] = val;
@@ -145,8 +243,7 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
     if (periodic) {
       val = side == 0 ? X[off(g, v, rr, nx - 1)] : X[off(g, v, rr, 0)];
     } else if (kind == K_STATE) {
-      const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + nx) % a.nlon;
-      val = bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.R0 + rr, i);
+      val = gh_col(a, g, nA, nB, wA, wB, side, v, rr);
     } else {
       val = (T)0;
     }
@@ -173,6 +270,7 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
     const int k = rem - (rr - r_lo) * nx;
     X[off(g, v, rr, k)] = src[((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k];
   }
+  if constexpr (sizeof(T) == 4) cp_async_wait_all();
   __syncthreads();
   const bool periodic = g.flags & F_PERIODIC;
   if (g.rank == 0) {
@@ -180,7 +278,7 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
       const int v = idx / nx, k = idx - v * nx;
       X[off(g, v, -1, k)] = (g.flags & F_SWALL)
                                 ? ((v == 2) ? -X[off(g, v, 0, k)] : X[off(g, v, 0, k)])
-                                : bnd_val(a, nA, nB, wA, wB, v, g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
+                                : gh_row(a, g, nA, nB, wA, wB, 0, v, k);
     }
   }
   if (g.rank == g.CL - 1) {
@@ -189,7 +287,7 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
       X[off(g, v, g.Rn, k)] =
           (g.flags & F_NWALL)
               ? ((v == 2) ? -X[off(g, v, g.Rn - 1, k)] : X[off(g, v, g.Rn - 1, k)])
-              : bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.ny, (g.d.i0 + k) % a.nlon);
+              : gh_row(a, g, nA, nB, wA, wB, 1, v, k);
     }
   }
   for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
@@ -201,8 +299,7 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
     if (periodic) {
       val = side == 0 ? X[off(g, v, rr, nx - 1)] : X[off(g, v, rr, 0)];
     } else {
-      const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + nx) % a.nlon;
-      val = bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.R0 + rr, i);
+      val = gh_col(a, g, nA, nB, wA, wB, side, v, rr);
     }
     X[off(g, v, rr, side == 0 ? -1 : nx)] = val;
   }
@@ -228,6 +325,7 @@ __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X
     const int k = rem - (rr - r_lo) * nx;
     X[b][off(g, v, rr, k)] = src[b][((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k];
   }
+  if constexpr (sizeof(T) == 4) cp_async_wait_all();
   __syncthreads();
   const bool periodic = g.flags & F_PERIODIC;
   const int ne = 2 * 3 * nx;      // box-edge halo rows (both sides, all vars)
@@ -243,13 +341,12 @@ __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X
       if (side == 0 && g.rank == 0) {
         Y[off(g, v, -1, k)] = (g.flags & F_SWALL)
                                   ? ((v == 2) ? -Y[off(g, v, 0, k)] : Y[off(g, v, 0, k)])
-                                  : bnd_val(a, nA[b], nB[b], wA[b], wB[b], v, g.d.j0 - 1,
-                                            (g.d.i0 + k) % a.nlon);
+                                  : gh_row(a, g, nA[b], nB[b], wA[b], wB[b], 0, v, k);
       } else if (side == 1 && g.rank == g.CL - 1) {
         Y[off(g, v, g.Rn, k)] =
             (g.flags & F_NWALL)
                 ? ((v == 2) ? -Y[off(g, v, g.Rn - 1, k)] : Y[off(g, v, g.Rn - 1, k)])
-                : bnd_val(a, nA[b], nB[b], wA[b], wB[b], v, g.d.j0 + g.ny, (g.d.i0 + k) % a.nlon);
+                : gh_row(a, g, nA[b], nB[b], wA[b], wB[b], 1, v, k);
       }
     } else {
       j -= ne;
@@ -261,8 +358,7 @@ __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X
       if (periodic) {
         val = side == 0 ? Y[off(g, v, rr, nx - 1)] : Y[off(g, v, rr, 0)];
       } else {
-        const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + nx) % a.nlon;
-        val = bnd_val(a, nA[b], nB[b], wA[b], wB[b], v, g.d.j0 + g.R0 + rr, i);
+        val = gh_col(a, g, nA[b], nB[b], wA[b], wB[b], side, v, rr);
       }
       Y[off(g, v, rr, side == 0 ? -1 : nx)] = val;
     }
@@ -538,9 +634,15 @@ __device__ __forceinline__ void store_level(const SweepArgs<T>& a, const Geo<T>&
   store_block(g, X, a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp);
 }
 
+// Ghost-cache length per slot (FP32 forward / adjoint sweeps only).
+template <typename T>
+__host__ __device__ constexpr int ghost_len(bool cache, int R, int W) {
+  return (cache && sizeof(T) == 4) ? 6 * R + 6 * W : 0;
+}
+
 template <typename T>
 __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs, RowSmem<T>& rs,
-                      double** scratch) {
+                      double** scratch, bool cache) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* p = reinterpret_cast<T*>(smem_raw);
   for (int b = 0; b < nbuf; ++b) {
@@ -559,19 +661,27 @@ __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs
   uintptr_t q = reinterpret_cast<uintptr_t>(p);
   q = (q + 15) & ~uintptr_t(15);
   *scratch = reinterpret_cast<double*>(q);
+  q += 64 * sizeof(double);
+  // ghost cache: 3 slots of 6 R + 6 W values, then 3 tags
+  Geo<T>& gm = const_cast<Geo<T>&>(g);
+  gm.gh_len = ghost_len<T>(cache, a.R, a.W);
+  gm.gh = reinterpret_cast<T*>(q);
+  gm.gh_tag = reinterpret_cast<int*>(q + 3 * (size_t)gm.gh_len * sizeof(T));
+  if (threadIdx.x < 3) gm.gh_tag[threadIdx.x] = -1;
+  __syncthreads();
 }
 
 template <typename T>
-size_t smem_bytes(int nbuf, int R, int W) {
+size_t smem_bytes(int nbuf, int R, int W, bool cache) {
   return (size_t)nbuf * 3 * (R + 2) * W * sizeof(T) + 8 * (size_t)(R + 2) * sizeof(T) + 16 +
-         64 * sizeof(double);
+         64 * sizeof(double) + 3 * (size_t)ghost_len<T>(cache, R, W) * sizeof(T) + 3 * sizeof(int) + 16;
 }
 
 // ---------------------------------------------------------------------------
 // Forward sweep: x(a) (stored at level 0 by the init kernel) -> x(a+1..b),
 // trajectory stored at every level, J_o and J_mu partial sums per CTA.
 template <typename T>
-__global__ void __launch_bounds__(512) fwd_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(512, sizeof(T) == 8 ? 2 : 1) fwd_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;
@@ -579,17 +689,20 @@ __global__ void __launch_bounds__(512) fwd_kernel(SweepArgs<T> a) {
   T* buf[3];
   RowSmem<T> rs;
   double* scratch;
-  carve(a, g, 3, buf, rs, &scratch);
+  carve(a, g, 3, buf, rs, &scratch, true);
   T* X = buf[0];
   T* S1 = buf[1];
   T* S2 = buf[2];
   load_rows(a, g, rs);
+  ghost_prefetch(a, g, g.a);
+  if (g.L > 0) ghost_prefetch(a, g, g.a + 1);
   load_level(a, g, X, 0, g.a);   // includes a CTA barrier
   double Jo = 0.0, Jm = 0.0;
   obs_level(a, g, X, 0, Jo);
   overlap_level(a, g, X, 0, Jm);
   for (int l = 0; l < g.L; ++l) {
     const int n = g.a + l;
+    if (n + 2 <= g.d.b) ghost_prefetch(a, g, n + 2);   // used by the next step
     stage<T, DEV>(a, g, rs, S1, X, X, (T)0, (T)1);
     complete_buf(cl, a, g, S1, K_STATE, n + 1, n + 1, (T)1, (T)0);
     // stores read the buffer with another thread mapping: after the barrier
@@ -666,7 +779,7 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
 // Adjoint sweep: lambda(b) = forcing(b); lambda(n) = M_n^T lambda(n+1) + forcing(n),
 // the RK3 stages recomputed from the stored x(n).  Writes lambda(a) to lam_a.
 template <typename T>
-__global__ void __launch_bounds__(512) adj_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(512, sizeof(T) == 8 ? 2 : 1) adj_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;
@@ -674,13 +787,15 @@ __global__ void __launch_bounds__(512) adj_kernel(SweepArgs<T> a) {
   T* buf[5];
   RowSmem<T> rs;
   double* scratch;
-  carve(a, g, 5, buf, rs, &scratch);
+  carve(a, g, 5, buf, rs, &scratch, true);
   T* X = buf[0];
   T* X1 = buf[1];
   T* X2 = buf[2];   // also lambda_x1
   T* Lp = buf[3];
   T* L2 = buf[4];
   load_rows(a, g, rs);
+  ghost_prefetch(a, g, g.a + g.L);
+  if (g.L > 0) ghost_prefetch(a, g, g.a + g.L - 1);
   for (int i = threadIdx.x; i < 3 * g.P; i += blockDim.x) Lp[i] = (T)0;
   const T dt = (T)a.dt, Bth = (T)a.Bth, gBth = (T)a.gBth, href = (T)a.h_ref;
   const T c23 = (T)(2.0 / 3.0), c13 = (T)(1.0 / 3.0);
@@ -722,6 +837,7 @@ __global__ void __launch_bounds__(512) adj_kernel(SweepArgs<T> a) {
   }
   for (int l = l1 - 1; l >= l0; --l) {
     const int n = g.a + l;
+    if (l > 0) ghost_prefetch(a, g, n - 1);   // used by the next (earlier) step
     if (a.stg && !K) {   // x(n) and the stage states stored by the forward sweep
       T* bufs[3] = {X, X1, X2};
       const T* srcs[3] = {a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp,
@@ -867,7 +983,7 @@ __global__ void __launch_bounds__(512) tlm_kernel(SweepArgs<T> a) {
   T* buf[6];
   RowSmem<T> rs;
   double* scratch;
-  carve(a, g, 6, buf, rs, &scratch);
+  carve(a, g, 6, buf, rs, &scratch, false);
   T *X = buf[0], *S1 = buf[1], *S2 = buf[2], *D = buf[3], *D1 = buf[4], *D2 = buf[5];
   load_rows(a, g, rs);
   load_level(a, g, X, 0, g.a);
@@ -940,9 +1056,9 @@ cudaError_t launch_cluster(K kernel, const SweepArgs<T>& a, int cl, int nthreads
 
 }  // namespace
 
-template <typename T> size_t smem_forward(int R, int W) { return smem_bytes<T>(3, R, W); }
-template <typename T> size_t smem_adjoint(int R, int W) { return smem_bytes<T>(5, R, W); }
-template <typename T> size_t smem_tlm(int R, int W) { return smem_bytes<T>(6, R, W); }
+template <typename T> size_t smem_forward(int R, int W) { return smem_bytes<T>(3, R, W, true); }
+template <typename T> size_t smem_adjoint(int R, int W) { return smem_bytes<T>(5, R, W, true); }
+template <typename T> size_t smem_tlm(int R, int W) { return smem_bytes<T>(6, R, W, false); }
 
 template <typename T>
 int occupancy_adjoint(int R, int W, int nthreads) {

@@ -135,6 +135,22 @@ def test_fp32_state_path_within_1e5_of_fp64_oracle():
         assert rel(gs[s], go.numpy()) <= 1e-3, s
 
 
+def test_mixed_forward_and_adjoint_shapes_agree():
+    """Forward and adjoint sweeps launched with different cluster sizes and
+    thread counts (the autotuner picks them separately) give the same results."""
+    wl = workloads.preset("ragged")
+    st, inp, _ = _setup(wl)
+    w = np.concatenate([rand_w(lp.nctrl, seed=650 + s).numpy() for s, lp in enumerate(st.locals)])
+    res = []
+    for fwd, adj in (((1, 256), (2, 256)), ((3, 192), (1, 320)), ((2, 448), (4, 128))):
+        ctx = make_context(wl, st, inp, cluster=2)
+        ctx.set_sweep_config(fwd, adj, True)
+        res.append(ctx.eval(w))
+        ctx.destroy()
+    for J, g in res[1:]:
+        assert rel(J, res[0][0]) <= 1e-14 and np.array_equal(g, res[0][1])
+
+
 def test_cluster_sizes_agree():
     wl = workloads.preset("ragged")
     st, inp, _ = _setup(wl)
@@ -190,7 +206,8 @@ def test_autotuned_launch_shape_matches_oracle():
     st, inp, _ = _setup(wl)
     ctx = make_context(wl, st, inp, cluster=-1)
     cfg = ctx.sweep_config()
-    assert cfg["cluster"] >= 1 and cfg["threads"] in (256, 512) and cfg["eval_ms"] > 0
+    assert cfg["forward"][0] >= 1 and cfg["adjoint"][0] >= 1 and cfg["eval_ms"] > 0
+    assert cfg["forward"][1] % 32 == 0 and cfg["adjoint"][1] % 32 == 0
     w = np.concatenate([rand_w(lp.nctrl, seed=800 + s).numpy() for s, lp in enumerate(st.locals)])
     _check_eval(ctx, st, w, st.xb_traj, st.background_prev())
 
