@@ -271,8 +271,23 @@ SweepArgs<T> sweep_args(dd4dv_ctx* ctx) {
 double h_ref_of(dd4dv_ctx* ctx) { return ctx->m.precision == 1 ? ctx->m.h_ref : 0.0; }
 
 // V w -> initial states (level 0 of every trajectory).  vw_buf receives L w.
+// Largest ny * (nx | 1) plane of the decomposition (odd shared-memory row
+// pitch), and whether it fits the fused shared-memory control-transform kernels.
+static int max_plane(dd4dv_ctx* ctx) {
+  int m = 0;
+  for (const SubDesc& d : ctx->subs_h) m = std::max(m, d.ny * (d.nx | 1));
+  return m;
+}
+static bool fused_v(dd4dv_ctx* ctx) { return (size_t)max_plane(ctx) * sizeof(double) <= 200 * 1024; }
+
 template <typename T>
 void init_states(dd4dv_ctx* ctx, const double* w, double* vw_buf, const int* active, int av) {
+  if (fused_v(ctx)) {
+    RFArgs ra{ctx->subs_d, ctx->n_sub, ctx->rf_alpha, ctx->rf_c, ctx->rf_passes, active, av};
+    KL(launch_vinit<T>(ctx->subs_d, ctx->n_sub, ctx->xb_a, w, ctx->sigma_d, ra, ctx->corr_len > 0.0 ? 1 : 0,
+                       h_ref_of(ctx), static_cast<T*>(ctx->traj), active, av, max_plane(ctx), ctx->st));
+    return;
+  }
   const double* src = w;
   if (ctx->corr_len > 0.0) {
     KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, w, nullptr, vw_buf, active, av, ctx->max_pts, ctx->st));
@@ -288,6 +303,12 @@ void init_states(dd4dv_ctx* ctx, const double* w, double* vw_buf, const int* act
 // out = V^T y  (+ w, times scale) for the subdomains in the mask.
 void apply_VT(dd4dv_ctx* ctx, const double* y, const double* w, const double* scale, double* out,
               const int* active, int av) {
+  if (fused_v(ctx)) {
+    RFArgs ra{ctx->subs_d, ctx->n_sub, ctx->rf_alpha, ctx->rf_c, ctx->rf_passes, active, av};
+    KL(launch_vgrad(ctx->subs_d, ctx->n_sub, w, y, ctx->sigma_d, ra, ctx->corr_len > 0.0 ? 1 : 0, scale, out,
+                    active, av, max_plane(ctx), ctx->st));
+    return;
+  }
   KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, y, ctx->sigma_d, ctx->vw2, active, av, ctx->max_pts, ctx->st));
   if (ctx->corr_len > 0.0) {
     RFArgs ra{ctx->subs_d, ctx->n_sub, ctx->rf_alpha, ctx->rf_c, ctx->rf_passes, active, av};

@@ -604,6 +604,92 @@ __global__ void finite_check_kernel(const double* a, long long n, int* flag) {
     if (!isfinite(a[i])) atomicExch(flag, 1);
 }
 
+// Fused control transform, one CTA per (subdomain, variable) with the
+// variable's ny x nx plane staged in shared memory:
+//   forward (V):   x(a) = x_b(a) + sigma_v L_lat L_lon w  -> trajectory level 0
+//   adjoint (V^T): grad = scale_s (w + L_lon L_lat (sigma_v y))
+// Rows (lon lines) are filtered by one thread per row, columns by one thread
+// per column, in the same operation order as the separate kernels.
+__device__ void rf_line_smem(double* x, int n, int stride, double alpha, double c, int npass) {
+  const double b = 1.0 - alpha;
+  for (int p = 0; p < npass; ++p) {
+    double q = 0.0;
+    for (int i = 0; i < n; ++i) {
+      q = alpha * q + b * x[i * stride];
+      x[i * stride] = q;
+    }
+    q = 0.0;
+    for (int i = n - 1; i >= 0; --i) {
+      q = alpha * q + b * x[i * stride];
+      x[i * stride] = q;
+    }
+  }
+  for (int i = 0; i < n; ++i) x[i * stride] *= c;
+}
+
+template <typename T>
+__global__ void vinit_kernel(const SubDesc* subs, const double* xb_a, const double* w, const double* sigma,
+                             RFArgs rf, int use_rf, double h_ref, T* traj, const int* active,
+                             int active_value) {
+  extern __shared__ double pl[];
+  const int s = blockIdx.x, v = blockIdx.y;
+  if (!is_active(active, active_value, s)) return;
+  const SubDesc d = subs[s];
+  const int n = d.ny * d.nx;
+  const int pitch = d.nx | 1;   // odd row pitch: row-wise passes are free of bank conflicts
+  const double* src = w + d.ctrl_off + (size_t)v * n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = i / d.nx, k = i - r * d.nx;
+    pl[r * pitch + k] = src[i];
+  }
+  __syncthreads();
+  if (use_rf) {
+    for (int r = threadIdx.x; r < d.ny; r += blockDim.x) rf_line_smem(pl + r * pitch, d.nx, 1, rf.alpha, rf.c, rf.npass);
+    __syncthreads();
+    for (int k = threadIdx.x; k < d.nx; k += blockDim.x) rf_line_smem(pl + k, d.ny, pitch, rf.alpha, rf.c, rf.npass);
+    __syncthreads();
+  }
+  const double sg = sigma[v];
+  const double* xb = xb_a + d.ctrl_off + (size_t)v * n;
+  T* dst = traj + d.traj_off + (size_t)v * d.ny * d.nxp;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = i / d.nx, k = i - r * d.nx;
+    double x = xb[i] + sg * pl[r * pitch + k];
+    if (v == 0) x -= h_ref;
+    dst[(size_t)r * d.nxp + k] = (T)x;
+  }
+}
+
+__global__ void vgrad_kernel(const SubDesc* subs, const double* w, const double* y, const double* sigma,
+                             RFArgs rf, int use_rf, const double* scale, double* grad, const int* active,
+                             int active_value) {
+  extern __shared__ double pl[];
+  const int s = blockIdx.x, v = blockIdx.y;
+  if (!is_active(active, active_value, s)) return;
+  const SubDesc d = subs[s];
+  const int n = d.ny * d.nx;
+  const int pitch = d.nx | 1;
+  const size_t o = d.ctrl_off + (size_t)v * n;
+  const double sg = sigma[v];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = i / d.nx, k = i - r * d.nx;
+    pl[r * pitch + k] = sg * y[o + i];
+  }
+  __syncthreads();
+  if (use_rf) {
+    for (int k = threadIdx.x; k < d.nx; k += blockDim.x) rf_line_smem(pl + k, d.ny, pitch, rf.alpha, rf.c, rf.npass);
+    __syncthreads();
+    for (int r = threadIdx.x; r < d.ny; r += blockDim.x) rf_line_smem(pl + r * pitch, d.nx, 1, rf.alpha, rf.c, rf.npass);
+    __syncthreads();
+  }
+  const double sc = scale ? scale[s] : 1.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int r = i / d.nx, k = i - r * d.nx;
+    const double gv = (w ? w[o + i] : 0.0) + pl[r * pitch + k];
+    grad[o + i] = scale ? sc * gv : gv;
+  }
+}
+
 inline unsigned blocks_for(long long n, int t, int cap = 152 * 16) {
   long long b = (n + t - 1) / t;
   if (b < 1) b = 1;
@@ -612,6 +698,37 @@ inline unsigned blocks_for(long long n, int t, int cap = 152 * 16) {
 }
 
 }  // namespace
+
+template <typename T>
+cudaError_t launch_vinit(const SubDesc* subs, int n_sub, const double* xb_a, const double* w,
+                         const double* sigma, const RFArgs& rf, int use_rf, double h_ref, T* traj,
+                         const int* active, int active_value, int max_plane, cudaStream_t st) {
+  const size_t smem = (size_t)max_plane * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(vinit_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  vinit_kernel<T><<<dim3(n_sub, 3), 256, smem, st>>>(subs, xb_a, w, sigma, rf, use_rf, h_ref, traj, active,
+                                                      active_value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_vgrad(const SubDesc* subs, int n_sub, const double* w, const double* y, const double* sigma,
+                         const RFArgs& rf, int use_rf, const double* scale, double* grad, const int* active,
+                         int active_value, int max_plane, cudaStream_t st) {
+  const size_t smem = (size_t)max_plane * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(vgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  vgrad_kernel<<<dim3(n_sub, 3), 256, smem, st>>>(subs, w, y, sigma, rf, use_rf, scale, grad, active,
+                                                  active_value);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_rf_rows(double* x, const RFArgs& a, int max_ny, cudaStream_t st) {
   dim3 grid((3 * max_ny + 127) / 128, a.n_sub);
@@ -750,6 +867,9 @@ cudaError_t launch_finite_check(const double* a, long long n, int* flag, cudaStr
 }
 
 #define DD4DV_INST(T)                                                                              \
+  template cudaError_t launch_vinit<T>(const SubDesc*, int, const double*, const double*,           \
+                                       const double*, const RFArgs&, int, double, T*, const int*,  \
+                                       int, int, cudaStream_t);                                    \
   template cudaError_t launch_init_state<T>(const SubDesc*, int, const double*, const double*,     \
                                             const double*, int, double, T*, const int*, int, int,  \
                                             cudaStream_t);                                         \

@@ -114,6 +114,14 @@ struct RFArgs {
 cudaError_t launch_rf_rows(double* x, const RFArgs& a, int max_ny, cudaStream_t st);
 cudaError_t launch_rf_cols(double* x, const RFArgs& a, int max_nx, cudaStream_t st);
 
+// fused V / V^T (one CTA per subdomain and variable, plane in shared memory)
+template <typename T>
+cudaError_t launch_vinit(const SubDesc* subs, int n_sub, const double* xb_a, const double* w,
+                         const double* sigma, const RFArgs& rf, int use_rf, double h_ref, T* traj,
+                         const int* active, int active_value, int max_plane, cudaStream_t st);
+cudaError_t launch_vgrad(const SubDesc* subs, int n_sub, const double* w, const double* y, const double* sigma,
+                         const RFArgs& rf, int use_rf, const double* scale, double* grad, const int* active,
+                         int active_value, int max_plane, cudaStream_t st);
 template <typename T>
 cudaError_t launch_init_state(const SubDesc* subs, int n_sub, const double* xb_a, const double* vw,
                               const double* sigma, int scale_sigma, double h_ref, T* traj,
