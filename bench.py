@@ -134,7 +134,7 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
-def build_problem(wl, precision, stream, inputs=None, shape=""):
+def build_problem(wl, precision, stream, inputs=None, shape="", ckpt_k=0):
     """Library context with truth run, synthetic observations and decomposition."""
     import paper_2205_06649_gb300 as dd
     inp = inputs if inputs is not None else workloads.generate(wl)
@@ -149,7 +149,7 @@ def build_problem(wl, precision, stream, inputs=None, shape=""):
     ctx.set_observations(inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)
     ctx.set_decomposition(wl.P1, wl.P2, wl.Q, wl.o_lon, wl.o_lat, wl.o_t, inp["lon_cuts"],
                           inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam,
-                          cluster=-1 if not shape else 0)
+                          cluster=-1 if not shape else 0, ckpt_k=ckpt_k)
     if shape:
         cf, tf, ca, ta, sg = (int(x) for x in shape.split(","))
         ctx.set_sweep_config((cf, tf), (ca, ta), bool(sg))
@@ -290,6 +290,38 @@ def run_reference(args):
     return 0
 
 
+def eval_mode(args, ctx, wl, prec, stream, torch):
+    """Steps of one batched J and grad J evaluation of every subdomain
+    (device-resident controls), timed with CUDA events on the library stream."""
+    rng = np.random.default_rng(0)
+    w = torch.tensor(0.3 * rng.standard_normal(ctx.ctrl_total), device="cuda")
+    for _ in range(args.warmup):
+        ctx.eval(w)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = ctx.launch_count()
+    with ClockSampler(0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.eval(w)
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.profile_sweeps(np.zeros(ctx.ctrl_total), reps=3)
+    line = {"metric": "fwd+adjoint grid-point-steps/s (one batched evaluation per step)",
+            "value": ctx.pt_steps() * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
+            "config": {"workload": wl_desc(wl), "n_sub": ctx.n_sub, "pt_steps_per_eval": ctx.pt_steps(),
+                       "sweep_launch": ctx.sweep_config(), "ckpt_k": args.ckpt},
+            "sweeps_ms": {"forward": prof["forward_ms"], "adjoint": prof["adjoint_ms"]},
+            "clocks": clk.summary(), "gpu_launches": ctx.launch_count() - l0}
+    print(json.dumps(line), flush=True)
+    ctx.destroy()
+    return 0
+
+
 def wl_desc(wl):
     return (f"{wl.name}: {wl.nlon}x{wl.nlat} grid, {wl.nsteps} steps, {wl.P1}x{wl.P2}x{wl.Q} "
             f"subdomains ({'uneven' if wl.uneven else 'equal'}), overlap {wl.o_lon} pts / {wl.o_t} steps, "
@@ -309,6 +341,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip FP32 and time-to-analysis legs")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="only run this many evaluations (for an ncu launch list) and exit")
+    ap.add_argument("--mode", default="outer", choices=["outer", "eval"],
+                    help="outer: a step is one outer iteration (default); eval: a step is one batched "
+                         "J and grad J evaluation of all subdomains (for workloads too large for the "
+                         "outer-iteration bench)")
+    ap.add_argument("--ckpt", type=int, default=0, help="ckpt_k of the decomposition (0, -1 or k > 0)")
     ap.add_argument("--shape", default="",
                     help="fwd_cluster,fwd_threads,adj_cluster,adj_threads,stored_stages: force the "
                          "sweep launch shapes (e.g. ones an autotuned run reported) instead of autotuning")
@@ -332,7 +369,7 @@ def main():
     wl = workloads.preset(args.workload)
     prec = 0 if args.precision == "f64" else 1
     stream = torch.cuda.Stream()
-    ctx, inp, truth, obs = build_problem(wl, prec, stream.cuda_stream, shape=args.shape)
+    ctx, inp, truth, obs = build_problem(wl, prec, stream.cuda_stream, shape=args.shape, ckpt_k=args.ckpt)
     solver = solver_for(wl)
     zeros = torch.zeros(ctx.ctrl_total, dtype=torch.float64, device="cuda")
 
@@ -343,6 +380,9 @@ def main():
         torch.cuda.synchronize()
         log(f"profile run: {args.profile_evals} evaluations, cluster {ctx.cluster_size()}")
         return 0
+
+    if args.mode == "eval":
+        return eval_mode(args, ctx, wl, prec, stream, torch)
 
     for _ in range(args.warmup):
         ctx.set_controls(zeros)
