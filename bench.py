@@ -140,10 +140,16 @@ def build_problem(wl, precision, stream, inputs=None, shape="", ckpt_k=0):
     inp = inputs if inputs is not None else workloads.generate(wl)
     ctx = dd.Context(wl.nlon, wl.nlat, inp["dt"], wl.nsteps, precision=precision,
                      h_ref=workloads.H_REF, stream=stream)
-    truth = ctx.forward(inp["x_t0"])
+    import torch
+    # truth run and H(truth) on the device; the trajectory is freed afterwards
+    # (the large workload's is 52 GB)
+    truth_traj = ctx.forward(torch.as_tensor(inp["x_t0"], device="cuda"))
+    hx = ctx.observe(truth_traj, inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"]).cpu().numpy()
+    del truth_traj
+    torch.cuda.empty_cache()
+    truth = inp["x_t0"][None]
     so = np.asarray(wl.sigma_o)[inp["obs_var"]]
-    y = ctx.observe(truth, inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"]) \
-        + so * inp["obs_noise"]
+    y = hx + so * inp["obs_noise"]
     ctx.set_background(inp["x_b0"])
     ctx.set_background_error(wl.sigma_b, wl.corr_len, wl.rf_passes)
     ctx.set_observations(inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)

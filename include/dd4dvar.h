@@ -98,7 +98,9 @@ typedef struct {
  * ckpt_k: trajectory storage for the adjoint.  0 = the forward sweep stores
  * every level and the two RK3 stage states of every step, and the adjoint
  * loads them (three times the memory of the states alone; on GB300 this
- * trades FP64 arithmetic for otherwise idle HBM bandwidth); -1 = store every
+ * trades FP64 arithmetic for otherwise idle HBM bandwidth) -- the stage buffer
+ * is allocated only if it leaves 4 GB + 5 % of the device memory free, else
+ * the adjoint recomputes the stages as with -1; -1 = store every
  * level, the adjoint recomputes the stage states; k > 0 = checkpointing:
  * evaluations store only the levels 0, k, 2k, ... and the adjoint
  * recomputes each k-step segment from its checkpoint before running back
@@ -146,16 +148,23 @@ typedef struct {
 } dd4dv_stats;
 
 /* Create a context on the current CUDA device.  stream: a cudaStream_t to
- * order all work on (NULL = the context creates its own).  Errors: EINVAL
- * (sizes, dt <= 0, nsteps < 0, lat range), ECUDA, ENOMEM. */
+ * order all work on (NULL = the context creates its own).  Device memory held
+ * from here on: a few global states and a chunk of at most 512 MB of global
+ * levels (global runs and host transfers of global trajectories go through
+ * it; the environment variable DD4DV_GLOBAL_CHUNK_LEVELS = 2..4096, read
+ * here, sets its number of levels instead).  Errors: EINVAL (sizes, dt <= 0,
+ * nsteps < 0, lat range), ECUDA, ENOMEM. */
 dd4dv_status dd4dv_create(const dd4dv_model* model, void* cuda_stream, dd4dv_ctx** out);
 
 /* Free the context and all its device memory.  NULL is accepted. */
 dd4dv_status dd4dv_destroy(dd4dv_ctx* ctx);
 
 /* Background initial state u_0^b (Definition "DA problem setup"): host array
- * [3][nlat][nlon].  Runs the background forecast u^b = M(u_0^b) over the
- * window on the device (Algorithm 1, background step).  ENONFINITE on NaN/Inf. */
+ * [3][nlat][nlon], copied.  The background forecast u^b = M(u_0^b) over the
+ * window (Algorithm 1, background step) runs on the device when the
+ * decomposition is set and at dd4dv_reset_exchange; it is streamed into the
+ * boundary trajectory and the overlap targets a chunk of levels at a time, so
+ * no separate global FP64 trajectory is kept.  ENONFINITE on NaN/Inf. */
 dd4dv_status dd4dv_set_background(dd4dv_ctx* ctx, const double* xb0);
 
 /* Background-error covariance B = V V^T (Sec. 4, Eq. EqV).  sigma_b[3]:

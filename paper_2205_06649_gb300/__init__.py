@@ -331,13 +331,42 @@ class Context:
         self._check(lib.dd4dv_analysis(self._h, C.c_void_p(out.ctypes.data), 0))
         return out
 
-    def forward(self, x0) -> np.ndarray:
+    def forward(self, x0):
+        """Global model run from x0 [3, nlat, nlon]: trajectory [nsteps+1, 3,
+        nlat, nlon].  A CUDA float64 tensor in gives a device tensor out
+        (no host copy); a host array gives a numpy array."""
+        if _is_torch_cuda(x0):
+            import torch
+            x0 = x0.contiguous()
+            out = torch.empty((self.nsteps + 1, 3, self.nlat, self.nlon), dtype=torch.float64, device=x0.device)
+            call = lambda: lib.dd4dv_forward(self._h, _ptr(x0, np.float64, True), _ptr(out, np.float64, True), 1)
+            self._check(self._device_call(call, x0, out))
+            return out
         x0 = np.ascontiguousarray(x0, dtype=np.float64)
         out = np.zeros((self.nsteps + 1, 3, self.nlat, self.nlon))
         self._check(lib.dd4dv_forward(self._h, C.c_void_p(x0.ctypes.data), C.c_void_p(out.ctypes.data), 0))
         return out
 
-    def observe(self, traj, level, var, fi, fj) -> np.ndarray:
+    def observe(self, traj, level, var, fi, fj):
+        """H applied to a global trajectory at the given sites.  A CUDA tensor
+        trajectory is read in place and gives a device tensor out."""
+        if _is_torch_cuda(traj):
+            import torch
+            dev = traj.device
+            traj = traj.contiguous()
+            lv = torch.as_tensor(np.asarray(level, dtype=np.int32), device=dev)
+            vr = torch.as_tensor(np.asarray(var, dtype=np.int32), device=dev)
+            fi_d = torch.as_tensor(np.asarray(fi, dtype=np.float64), device=dev)
+            fj_d = torch.as_tensor(np.asarray(fj, dtype=np.float64), device=dev)
+            out = torch.empty(len(lv), dtype=torch.float64, device=dev)
+            if len(lv) == 0:
+                return out
+            call = lambda: lib.dd4dv_observe(self._h, _ptr(traj, np.float64, True), len(lv),
+                                             _ptr(lv, np.int32, True), _ptr(vr, np.int32, True),
+                                             _ptr(fi_d, np.float64, True), _ptr(fj_d, np.float64, True),
+                                             _ptr(out, np.float64, True), 1)
+            self._check(self._device_call(call, traj, lv, vr, fi_d, fj_d, out))
+            return out
         traj = np.ascontiguousarray(traj, dtype=np.float64)
         lv = np.ascontiguousarray(level, dtype=np.int32)
         vr = np.ascontiguousarray(var, dtype=np.int32)

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -46,9 +47,10 @@ struct dd4dv_ctx {
   size_t gtraj = 0;           // (nsteps+1)*gstate
 
   bool has_bg = false, has_berr = false, has_obs = false, has_dec = false;
-  double* xb_traj = nullptr;  // global background trajectory (FP64)
-  double* gscratch = nullptr; // 3 global states for the global model
-  double* gtraj_io = nullptr; // global trajectory staging (FP64)
+  double* xb0 = nullptr;      // background initial state (FP64, one global state)
+  double* gscratch = nullptr; // 3 global states: 2 RK3 stages + input/output staging
+  double* gchunk = nullptr;   // gchunk_lv consecutive global levels (FP64): chunked global
+  int gchunk_lv = 2;          // runs and host transfers of global trajectories
 
   double sigma_b[3] = {1, 1, 1};
   double corr_len = 0;
@@ -246,6 +248,14 @@ SweepArgs<T> sweep_args(dd4dv_ctx* ctx) {
   for (int v = 0; v < 3; ++v) a.isb2[v] = 1.0 / (ctx->sigma_b[v] * ctx->sigma_b[v]);
   a.lam = ctx->dec.lambda;
   a.mu = ctx->dec.mu;
+  a.dt_s = (T)a.dt;
+  a.Bth_s = (T)a.Bth;
+  a.gBth_s = (T)a.gBth;
+  a.href_s = (T)a.h_ref;
+  for (int v = 0; v < 3; ++v) {
+    a.isb2_s[v] = (T)a.isb2[v];
+    a.musb2_s[v] = (T)(a.mu * a.isb2[v]);
+  }
   a.obs = ctx->obs_d;
   a.lvl_obs = ctx->lvl_obs_d;
   a.obs_force = ctx->obs_force_d;
@@ -377,33 +387,72 @@ void exchange_T(dd4dv_ctx* ctx, const double* w) {
   ctx->fwd_pending = false;
 }
 
+// The background trajectory (global model run of x_b(t0)), streamed through
+// the chunk buffer into the frozen boundary trajectory B and the overlap
+// targets (the state before the first exchange), and, with xb_a set, into the
+// restricted background at each window's first level.
+template <typename T>
+void background_pass(dd4dv_ctx* ctx, bool xb_a);
+
 template <typename T>
 void reset_exchange_T(dd4dv_ctx* ctx) {
-  const long long n = (long long)ctx->gtraj;
-  KL(launch_bnd_from_global<T>(ctx->xb_traj, n, h_ref_of(ctx), ctx->m.nlon, ctx->m.nlat,
-                               static_cast<T*>(ctx->bnd), ctx->st));
-  KL(launch_restrict<T>(ctx->subs_d, ctx->n_sub, ctx->m.nlon, ctx->m.nlat, ctx->xb_traj, h_ref_of(ctx),
-                        static_cast<T*>(ctx->tgt), ctx->max_pts, ctx->max_levels, ctx->st));
+  background_pass<T>(ctx, false);
   CK(cudaMemsetAsync(ctx->vconst, 0, ctx->n_sub * sizeof(double), ctx->st));
   ctx->fwd_pending = false;
+}
+
+// One RK3 step of the global model: x (device) -> nx (device), FP64.
+void global_step(dd4dv_ctx* ctx, const double* x, double* nx) {
+  double* s1 = ctx->gscratch;
+  double* s2 = ctx->gscratch + ctx->gstate;
+  KL(launch_global_stage(x, x, s1, 0.0, 1.0, ctx->rows_d, ctx->Bth, ctx->gBth, ctx->m.dt, ctx->m.nlon,
+                         ctx->m.nlat, ctx->st));
+  KL(launch_global_stage(x, s1, s2, 0.75, 0.25, ctx->rows_d, ctx->Bth, ctx->gBth, ctx->m.dt,
+                         ctx->m.nlon, ctx->m.nlat, ctx->st));
+  KL(launch_global_stage(x, s2, nx, 1.0 / 3.0, 2.0 / 3.0, ctx->rows_d, ctx->Bth, ctx->gBth, ctx->m.dt,
+                         ctx->m.nlon, ctx->m.nlat, ctx->st));
 }
 
 // Global model run x0 (device) -> out trajectory (device, FP64).
 void global_run(dd4dv_ctx* ctx, const double* x0, double* out) {
   const size_t G = ctx->gstate;
   CK(cudaMemcpyAsync(out, x0, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-  double* s1 = ctx->gscratch;
-  double* s2 = ctx->gscratch + G;
-  for (int n = 0; n < ctx->m.nsteps; ++n) {
-    const double* x = out + (size_t)n * G;
-    double* nx = out + (size_t)(n + 1) * G;
-    KL(launch_global_stage(x, x, s1, 0.0, 1.0, ctx->rows_d, ctx->Bth, ctx->gBth, ctx->m.dt,
-                           ctx->m.nlon, ctx->m.nlat, ctx->st));
-    KL(launch_global_stage(x, s1, s2, 0.75, 0.25, ctx->rows_d, ctx->Bth, ctx->gBth, ctx->m.dt,
-                           ctx->m.nlon, ctx->m.nlat, ctx->st));
-    KL(launch_global_stage(x, s2, nx, 1.0 / 3.0, 2.0 / 3.0, ctx->rows_d, ctx->Bth, ctx->gBth,
-                           ctx->m.dt, ctx->m.nlon, ctx->m.nlat, ctx->st));
+  for (int n = 0; n < ctx->m.nsteps; ++n) global_step(ctx, out + (size_t)n * G, out + (size_t)(n + 1) * G);
+}
+
+// Global model run from x0 (device) without a whole-trajectory buffer: the
+// levels are produced in the chunk buffer, gchunk_lv at a time, and handed to
+// sink(g0, g1, levels) (levels g0..g1, level-major FP64) in order.  The last
+// level of a chunk is the first of the next.
+template <typename Sink>
+void global_run_chunked(dd4dv_ctx* ctx, const double* x0, Sink&& sink) {
+  const size_t G = ctx->gstate;
+  const int K = ctx->gchunk_lv - 1;
+  double* c = ctx->gchunk;
+  CK(cudaMemcpyAsync(c, x0, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  for (int g0 = 0;;) {
+    const int g1 = std::min(g0 + K, ctx->m.nsteps);
+    for (int n = g0; n < g1; ++n) global_step(ctx, c + (size_t)(n - g0) * G, c + (size_t)(n - g0 + 1) * G);
+    sink(g0, g1, c);
+    if (g1 >= ctx->m.nsteps) break;
+    CK(cudaMemcpyAsync(c, c + (size_t)(g1 - g0) * G, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    g0 = g1;
   }
+}
+
+template <typename T>
+void background_pass(dd4dv_ctx* ctx, bool xb_a) {
+  const size_t G = ctx->gstate;
+  const int nlon = ctx->m.nlon, nlat = ctx->m.nlat;
+  global_run_chunked(ctx, ctx->xb0, [&](int g0, int g1, const double* lv) {
+    const long long n = (long long)(g1 - g0 + 1) * G;
+    KL(launch_bnd_from_global<T>(lv, n, h_ref_of(ctx), nlon, nlat, static_cast<T*>(ctx->bnd) + (size_t)g0 * G,
+                                 ctx->st));
+    KL(launch_restrict<T>(ctx->subs_d, ctx->n_sub, nlon, nlat, lv, g0, g1, h_ref_of(ctx),
+                          static_cast<T*>(ctx->tgt), ctx->max_pts, ctx->st));
+    if (xb_a) KL(launch_restrict_level(ctx->subs_d, ctx->n_sub, nlon, nlat, lv, g0, g1, ctx->xb_a, ctx->max_pts,
+                                       ctx->st));
+  });
 }
 
 // Copies a host input into a device buffer when device_ptrs == 0.
@@ -818,11 +867,6 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   ctx->ckpt = d.ckpt_k > 0 ? d.ckpt_k : 0;
   ctx->seg = nullptr;
   if (d.ckpt_k > 0) ctx->seg = dalloc<unsigned char>(ctx, std::max<long long>(1, segl) * ctx->tsize, &L);
-  if (d.ckpt_k == 0) {
-    ctx->stg_elems = stgl;
-    ctx->stg = dalloc<unsigned char>(ctx, std::max<long long>(1, stgl) * ctx->tsize, &L);
-    ctx->use_stg = true;
-  }
   ctx->tgt = dalloc<unsigned char>(ctx, ctx->traj_elems * ctx->tsize, &L);
   ctx->bnd = dalloc<unsigned char>(ctx, ctx->gtraj * ctx->tsize, &L);
   const size_t C = (size_t)ctrl;
@@ -864,6 +908,20 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   ctx->lon_cov_d = dalloc<int>(ctx, lon_cov.size(), &L);
   ctx->lat_cov_d = dalloc<int>(ctx, lat_cov.size(), &L);
   ctx->t_cov_d = dalloc<int>(ctx, t_cov.size(), &L);
+  // Stored stage states (ckpt_k = 0) are twice the trajectory: allocate them
+  // last, and only if they leave a reserve of 4 GB + 5 % of the device free;
+  // otherwise the adjoint recomputes the stages.
+  if (d.ckpt_k == 0) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const double need = (double)std::max<long long>(1, stgl) * ctx->tsize;
+    const double reserve = 4.0 * (1ull << 30) + 0.05 * (double)total_b;
+    if (need + reserve <= (double)free_b) {
+      ctx->stg_elems = stgl;
+      ctx->stg = dalloc<unsigned char>(ctx, std::max<long long>(1, stgl) * ctx->tsize, &L);
+      ctx->use_stg = true;
+    }
+  }
   h2d(ctx, ctx->subs_d, subs.data(), subs.size() * sizeof(SubDesc));
   h2d(ctx, ctx->order_d, order.data(), order.size() * sizeof(int));
   if (!recs.empty()) h2d(ctx, ctx->obs_d, recs.data(), recs.size() * sizeof(ObsRec));
@@ -886,12 +944,13 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   ctx->dec = d;
   ctx->dec.lon_cuts = ctx->dec.lat_cuts = ctx->dec.t_cuts = nullptr;
   ctx->dec.cluster = cl;
-  KL(launch_restrict_level(ctx->subs_d, n_sub, nlon, nlat, ctx->xb_traj, ctx->xb_a, max_pts, ctx->st));
   by_precision(ctx, [&](auto t) {
     using T = decltype(t);
-    reset_exchange_T<T>(ctx);
+    background_pass<T>(ctx, true);
     return 0;
   });
+  CK(cudaMemsetAsync(ctx->vconst, 0, n_sub * sizeof(double), ctx->st));
+  ctx->fwd_pending = false;
   sync(ctx);
   ctx->has_dec = true;
   if (d.cluster < 0) autotune(ctx);
@@ -902,9 +961,9 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
 dd4dv_ctx::~dd4dv_ctx() {
   free_dec();
   cudaFree(rows_d);
-  cudaFree(xb_traj);
+  cudaFree(xb0);
   cudaFree(gscratch);
-  cudaFree(gtraj_io);
+  cudaFree(gchunk);
   cudaFree(sigma_d);
   cudaFree(counter_d);
   cudaFree(scal_d);
@@ -993,9 +1052,16 @@ dd4dv_status dd4dv_create(const dd4dv_model* model, void* cuda_stream, dd4dv_ctx
     ctx->gstate = 3ULL * m.nlat * m.nlon;
     ctx->gtraj = (size_t)(m.nsteps + 1) * ctx->gstate;
     ctx->rows_d = dalloc<RowConst>(ctx, m.nlat);
-    ctx->xb_traj = dalloc<double>(ctx, ctx->gtraj);
+    ctx->xb0 = dalloc<double>(ctx, ctx->gstate);
     ctx->gscratch = dalloc<double>(ctx, 3 * ctx->gstate);
-    ctx->gtraj_io = dalloc<double>(ctx, ctx->gtraj);
+    // chunk of global levels: at most 512 MB, at least 2 levels, at most the whole trajectory
+    const size_t lv_bytes = ctx->gstate * sizeof(double);
+    ctx->gchunk_lv = (int)std::max<size_t>(2, std::min<size_t>({(size_t)m.nsteps + 1, (512u << 20) / lv_bytes, 4096}));
+    if (const char* e = std::getenv("DD4DV_GLOBAL_CHUNK_LEVELS")) {   // override (tests of the chunking)
+      const int k = std::atoi(e);
+      if (k >= 2 && k <= 4096) ctx->gchunk_lv = k;
+    }
+    ctx->gchunk = dalloc<double>(ctx, (size_t)ctx->gchunk_lv * ctx->gstate);
     ctx->sigma_d = dalloc<double>(ctx, 3);
     ctx->counter_d = dalloc<int>(ctx, 4);
     ctx->scal_d = dalloc<double>(ctx, 8);
@@ -1036,11 +1102,7 @@ dd4dv_status dd4dv_set_background(dd4dv_ctx* ctx, const double* xb0) {
     if (!xb0) fail(ctx, DD4DV_EINVAL, "xb0 is NULL");
     if (!all_finite(xb0, ctx->gstate)) fail(ctx, DD4DV_ENONFINITE, "background contains NaN or Inf");
     ctx->free_dec();
-    h2d(ctx, ctx->gscratch + 2 * ctx->gstate, xb0, ctx->gstate * sizeof(double));
-    // the global run needs the initial state outside its scratch: stage it in the io trajectory
-    CK(cudaMemcpyAsync(ctx->gtraj_io, ctx->gscratch + 2 * ctx->gstate, ctx->gstate * sizeof(double),
-                       cudaMemcpyDeviceToDevice, ctx->st));
-    global_run(ctx, ctx->gtraj_io, ctx->xb_traj);
+    h2d(ctx, ctx->xb0, xb0, ctx->gstate * sizeof(double));
     sync(ctx);
     ctx->has_bg = true;
     return DD4DV_OK;
@@ -1366,17 +1428,21 @@ dd4dv_status dd4dv_boundary_trajectory(dd4dv_ctx* ctx, double* traj, int device_
   return guard(ctx, [&] {
     require_dec(ctx);
     if (!traj) fail(ctx, DD4DV_EINVAL, "NULL argument");
-    double* out = device_ptrs ? traj : ctx->gtraj_io;
-    by_precision(ctx, [&](auto t) {
-      using T = decltype(t);
-      KL(launch_bnd_to_global<T>(static_cast<const T*>(ctx->bnd), (long long)ctx->gtraj, h_ref_of(ctx),
-                                 ctx->m.nlon, ctx->m.nlat, out, ctx->st));
-      return 0;
-    });
-    if (!device_ptrs) {
-      d2h(ctx, traj, out, ctx->gtraj * sizeof(double));
-      sync(ctx);
+    const size_t G = ctx->gstate;
+    const int levels = ctx->m.nsteps + 1;
+    const int chunk = device_ptrs ? levels : ctx->gchunk_lv;   // host output: through the chunk buffer
+    for (int g0 = 0; g0 < levels; g0 += chunk) {
+      const int nl = std::min(chunk, levels - g0);
+      double* out = device_ptrs ? traj : ctx->gchunk;
+      by_precision(ctx, [&](auto t) {
+        using T = decltype(t);
+        KL(launch_bnd_to_global<T>(static_cast<const T*>(ctx->bnd) + (size_t)g0 * G, (long long)nl * G,
+                                   h_ref_of(ctx), ctx->m.nlon, ctx->m.nlat, out, ctx->st));
+        return 0;
+      });
+      if (!device_ptrs) d2h(ctx, traj + (size_t)g0 * G, out, (size_t)nl * G * sizeof(double));
     }
+    if (!device_ptrs) sync(ctx);
     return DD4DV_OK;
   });
 }
@@ -1385,7 +1451,7 @@ dd4dv_status dd4dv_analysis(dd4dv_ctx* ctx, double* xa0, int device_ptrs) {
   return guard(ctx, [&] {
     require_dec(ctx);
     if (!xa0) fail(ctx, DD4DV_EINVAL, "NULL argument");
-    double* out = device_ptrs ? xa0 : ctx->gtraj_io;
+    double* out = device_ptrs ? xa0 : ctx->gscratch + 2 * ctx->gstate;
     by_precision(ctx, [&](auto t) {
       using T = decltype(t);
       KL(launch_bnd_to_global<T>(static_cast<const T*>(ctx->bnd), (long long)ctx->gstate, h_ref_of(ctx),
@@ -1403,18 +1469,18 @@ dd4dv_status dd4dv_analysis(dd4dv_ctx* ctx, double* xa0, int device_ptrs) {
 dd4dv_status dd4dv_forward(dd4dv_ctx* ctx, const double* x0, double* traj, int device_ptrs) {
   return guard(ctx, [&] {
     if (!x0 || !traj) fail(ctx, DD4DV_EINVAL, "NULL argument");
-    double* out = device_ptrs ? traj : ctx->gtraj_io;
-    const double* in = x0;
-    if (!device_ptrs) {
-      if (!all_finite(x0, ctx->gstate)) fail(ctx, DD4DV_ENONFINITE, "x0 contains NaN or Inf");
-      h2d(ctx, ctx->gtraj_io, x0, ctx->gstate * sizeof(double));
-      in = ctx->gtraj_io;
+    if (device_ptrs) {
+      global_run(ctx, x0, traj);
+      return DD4DV_OK;
     }
-    global_run(ctx, in, out);
-    if (!device_ptrs) {
-      d2h(ctx, traj, out, ctx->gtraj * sizeof(double));
-      sync(ctx);
-    }
+    if (!all_finite(x0, ctx->gstate)) fail(ctx, DD4DV_ENONFINITE, "x0 contains NaN or Inf");
+    const size_t G = ctx->gstate;
+    double* in = ctx->gscratch + 2 * G;
+    h2d(ctx, in, x0, G * sizeof(double));
+    global_run_chunked(ctx, in, [&](int g0, int g1, const double* lv) {
+      d2h(ctx, traj + (size_t)g0 * G, lv, (size_t)(g1 - g0 + 1) * G * sizeof(double));
+    });
+    sync(ctx);
     return DD4DV_OK;
   });
 }
@@ -1427,7 +1493,7 @@ dd4dv_status dd4dv_observe(dd4dv_ctx* ctx, const double* traj, long long n, cons
     if (n == 0) return DD4DV_OK;
     if (!traj || !level || !var || !fi || !fj || !out) fail(ctx, DD4DV_EINVAL, "NULL argument");
     if (device_ptrs) {
-      KL(launch_observe(traj, n, level, var, fi, fj, ctx->m.nlon, ctx->m.nlat, out, ctx->st));
+      KL(launch_observe(traj, 0, ctx->m.nsteps, n, level, var, fi, fj, ctx->m.nlon, ctx->m.nlat, out, ctx->st));
       return DD4DV_OK;
     }
     for (long long k = 0; k < n; ++k) {
@@ -1437,18 +1503,24 @@ dd4dv_status dd4dv_observe(dd4dv_ctx* ctx, const double* traj, long long n, cons
     }
     std::vector<void*> tmp;
     try {
-      double* dt = dalloc<double>(ctx, ctx->gtraj, &tmp);
       int* dl = dalloc<int>(ctx, n, &tmp);
       int* dv = dalloc<int>(ctx, n, &tmp);
       double* dfi = dalloc<double>(ctx, n, &tmp);
       double* dfj = dalloc<double>(ctx, n, &tmp);
       double* dout = dalloc<double>(ctx, n, &tmp);
-      h2d(ctx, dt, traj, ctx->gtraj * sizeof(double));
       h2d(ctx, dl, level, n * sizeof(int));
       h2d(ctx, dv, var, n * sizeof(int));
       h2d(ctx, dfi, fi, n * sizeof(double));
       h2d(ctx, dfj, fj, n * sizeof(double));
-      KL(launch_observe(dt, n, dl, dv, dfi, dfj, ctx->m.nlon, ctx->m.nlat, dout, ctx->st));
+      // the trajectory goes up a chunk of levels at a time
+      const size_t G = ctx->gstate;
+      const int levels = ctx->m.nsteps + 1;
+      for (int g0 = 0; g0 < levels; g0 += ctx->gchunk_lv) {
+        const int nl = std::min(ctx->gchunk_lv, levels - g0);
+        h2d(ctx, ctx->gchunk, traj + (size_t)g0 * G, (size_t)nl * G * sizeof(double));
+        KL(launch_observe(ctx->gchunk, g0, g0 + nl - 1, n, dl, dv, dfi, dfj, ctx->m.nlon, ctx->m.nlat, dout,
+                          ctx->st));
+      }
       d2h(ctx, out, dout, n * sizeof(double));
       sync(ctx);
     } catch (...) {
@@ -1662,10 +1734,10 @@ dd4dv_status dd4dv_run(dd4dv_ctx* ctx, const dd4dv_solver* solver, double* xa0, 
       by_precision(ctx, [&](auto t) {
         using T = decltype(t);
         KL(launch_bnd_to_global<T>(static_cast<const T*>(ctx->bnd), (long long)ctx->gstate, h_ref_of(ctx),
-                                   ctx->m.nlon, ctx->m.nlat, ctx->gtraj_io, ctx->st));
+                                   ctx->m.nlon, ctx->m.nlat, ctx->gscratch + 2 * ctx->gstate, ctx->st));
         return 0;
       });
-      d2h(ctx, xa0, ctx->gtraj_io, ctx->gstate * sizeof(double));
+      d2h(ctx, xa0, ctx->gscratch + 2 * ctx->gstate, ctx->gstate * sizeof(double));
       sync(ctx);
     }
     return conv ? DD4DV_OK : DD4DV_NOTCONV;

@@ -256,17 +256,19 @@ __global__ void assemble_kernel(ExchArgs<T> a) {
   }
 }
 
-// Restriction of a global FP64 trajectory to every subdomain's window x box.
+// Restriction of a global FP64 trajectory to every subdomain's window x box,
+// for the global levels g0..g1 that `glob` holds (level g0 first).
 template <typename T>
-__global__ void restrict_kernel(const SubDesc* subs, int nlon, int nlat, const double* glob,
+__global__ void restrict_kernel(const SubDesc* subs, int nlon, int nlat, const double* glob, int g0,
                                 double h_ref, T* traj) {
   const int s = blockIdx.z;
   const SubDesc d = subs[s];
-  const int l = blockIdx.y;
-  if (l > d.b - d.a) return;
+  const int n = g0 + (int)blockIdx.y;
+  if (n < d.a || n > d.b) return;
+  const int l = n - d.a;
   const int npt = 3 * d.ny * d.nx;
   const size_t plane = (size_t)nlat * nlon;
-  const double* src = glob + (size_t)(d.a + l) * 3 * plane;
+  const double* src = glob + (size_t)blockIdx.y * 3 * plane;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npt; i += gridDim.x * blockDim.x) {
     const int v = i / (d.ny * d.nx);
     const int rem = i - v * d.ny * d.nx;
@@ -294,13 +296,14 @@ __global__ void export_traj_kernel(const SubDesc* subs, const T* traj, double h_
   }
 }
 
-__global__ void restrict_level_kernel(const SubDesc* subs, int nlon, int nlat,
-                                      const double* glob_traj, double* xb_a) {
+__global__ void restrict_level_kernel(const SubDesc* subs, int nlon, int nlat, const double* glob,
+                                      int g0, int g1, double* xb_a) {
   const int s = blockIdx.y;
   const SubDesc d = subs[s];
+  if (d.a < g0 || d.a > g1) return;
   const int npt = 3 * d.ny * d.nx;
   const size_t plane = (size_t)nlat * nlon;
-  const double* src = glob_traj + (size_t)d.a * 3 * plane;
+  const double* src = glob + (size_t)(d.a - g0) * 3 * plane;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < npt; i += gridDim.x * blockDim.x) {
     const int v = i / (d.ny * d.nx);
     const int rem = i - v * d.ny * d.nx;
@@ -374,16 +377,20 @@ __global__ void global_stage_kernel(const double* x, const double* y, double* ou
 
 // H: bilinear interpolation in index space (lon periodic), corners in the
 // order (j0,i0), (j0,i1), (j1,i0), (j1,i1), zero-weight corners skipped.
-__global__ void observe_kernel(const double* traj, long long n, const int* level, const int* var,
-                               const double* fi, const double* fj, int nlon, int nlat, double* out) {
+// `traj` holds the global levels g0..g1; observations at other levels are
+// left untouched.
+__global__ void observe_kernel(const double* traj, int g0, int g1, long long n, const int* level,
+                               const int* var, const double* fi, const double* fj, int nlon, int nlat,
+                               double* out) {
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
        k += (long long)gridDim.x * blockDim.x) {
+    if (level[k] < g0 || level[k] > g1) continue;
     const double x = fi[k], y = fj[k];
     const int i0 = (int)floor(x), j0 = (int)floor(y);
     const double di = x - i0, dj = y - j0;
     const int i1 = (i0 + 1) % nlon;
     const size_t P = (size_t)nlat * nlon;
-    const double* src = traj + ((size_t)level[k] * 3 + var[k]) * P;
+    const double* src = traj + ((size_t)(level[k] - g0) * 3 + var[k]) * P;
     double acc = 0.0;
     acc += ((1.0 - dj) * (1.0 - di)) * src[(size_t)j0 * nlon + i0 % nlon];
     if (di != 0.0) acc += ((1.0 - dj) * di) * src[(size_t)j0 * nlon + i1];
@@ -792,9 +799,9 @@ cudaError_t launch_sum_vconst(const double* vpart, int n_sub, int vblocks, doubl
 
 template <typename T>
 cudaError_t launch_restrict(const SubDesc* subs, int n_sub, int nlon, int nlat, const double* glob,
-                            double h_ref, T* traj, int max_pts, int max_levels, cudaStream_t st) {
-  dim3 grid(blocks_for(max_pts, 256, 16), max_levels, n_sub);
-  restrict_kernel<T><<<grid, 256, 0, st>>>(subs, nlon, nlat, glob, h_ref, traj);
+                            int g0, int g1, double h_ref, T* traj, int max_pts, cudaStream_t st) {
+  dim3 grid(blocks_for(max_pts, 256, 16), g1 - g0 + 1, n_sub);
+  restrict_kernel<T><<<grid, 256, 0, st>>>(subs, nlon, nlat, glob, g0, h_ref, traj);
   return cudaGetLastError();
 }
 template <typename T>
@@ -818,10 +825,10 @@ cudaError_t launch_bnd_to_global(const T* bnd, long long n, double h_ref, int nl
                                                                (long long)nlon * nlat, glob);
   return cudaGetLastError();
 }
-cudaError_t launch_restrict_level(const SubDesc* subs, int n_sub, int nlon, int nlat,
-                                  const double* glob_traj, double* xb_a, int max_pts, cudaStream_t st) {
+cudaError_t launch_restrict_level(const SubDesc* subs, int n_sub, int nlon, int nlat, const double* glob,
+                                  int g0, int g1, double* xb_a, int max_pts, cudaStream_t st) {
   dim3 grid(blocks_for(max_pts, 256, 64), n_sub);
-  restrict_level_kernel<<<grid, 256, 0, st>>>(subs, nlon, nlat, glob_traj, xb_a);
+  restrict_level_kernel<<<grid, 256, 0, st>>>(subs, nlon, nlat, glob, g0, g1, xb_a);
   return cudaGetLastError();
 }
 
@@ -832,11 +839,12 @@ cudaError_t launch_global_stage(const double* x, const double* y, double* out, d
   global_stage_kernel<<<grid, 128, 0, st>>>(x, y, out, ca, cb, rows, Bth, gBth, dt, nlon, nlat);
   return cudaGetLastError();
 }
-cudaError_t launch_observe(const double* traj, long long n, const int* level, const int* var,
-                           const double* fi, const double* fj, int nlon, int nlat, double* out,
-                           cudaStream_t st) {
+cudaError_t launch_observe(const double* traj, int g0, int g1, long long n, const int* level,
+                           const int* var, const double* fi, const double* fj, int nlon, int nlat,
+                           double* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  observe_kernel<<<blocks_for(n, 256), 256, 0, st>>>(traj, n, level, var, fi, fj, nlon, nlat, out);
+  observe_kernel<<<blocks_for(n, 256), 256, 0, st>>>(traj, g0, g1, n, level, var, fi, fj, nlon, nlat,
+                                                     out);
   return cudaGetLastError();
 }
 
@@ -875,8 +883,8 @@ cudaError_t launch_finite_check(const double* a, long long n, int* flag, cudaStr
                                             cudaStream_t);                                         \
   template cudaError_t launch_targets<T>(const ExchArgs<T>&, cudaStream_t);                        \
   template cudaError_t launch_assemble<T>(const ExchArgs<T>&, cudaStream_t);                       \
-  template cudaError_t launch_restrict<T>(const SubDesc*, int, int, int, const double*, double, T*, \
-                                          int, int, cudaStream_t);                                 \
+  template cudaError_t launch_restrict<T>(const SubDesc*, int, int, int, const double*, int, int,  \
+                                          double, T*, int, cudaStream_t);                          \
   template cudaError_t launch_export_traj<T>(const SubDesc*, int, const T*, double, double*, int,  \
                                              int, cudaStream_t);                                   \
   template cudaError_t launch_bnd_from_global<T>(const double*, long long, double, int, int, T*,   \

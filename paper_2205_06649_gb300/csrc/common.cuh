@@ -73,6 +73,10 @@ struct SweepArgs {
   int nlon, nlat, nsteps;
   double isb2[3];             // 1 / sigma_b^2 per variable
   double lam, mu;
+  // the same constants rounded once to the state precision on the host, so
+  // that the FP32 sweeps run no FP64 conversion per stage or level
+  T dt_s, Bth_s, gBth_s, href_s;
+  T isb2_s[3], musb2_s[3];    // 1 / sigma_b^2 and mu / sigma_b^2
   const ObsRec* obs;          // per-subdomain, per-level sorted
   const int* lvl_obs;         // obs ranges per (subdomain, level)
   double* obs_force;          // lambda * omega * d / sigma_o^2 per obs record
@@ -155,7 +159,7 @@ cudaError_t launch_sum_vconst(const double* vpart, int n_sub, int vblocks, doubl
 
 template <typename T>
 cudaError_t launch_restrict(const SubDesc* subs, int n_sub, int nlon, int nlat, const double* glob,
-                            double h_ref, T* traj, int max_pts, int max_levels, cudaStream_t st);
+                            int g0, int g1, double h_ref, T* traj, int max_pts, cudaStream_t st);
 template <typename T>
 cudaError_t launch_export_traj(const SubDesc* subs, int n_sub, const T* traj, double h_ref,
                                double* out, int max_pts, int max_levels, cudaStream_t st);
@@ -165,16 +169,16 @@ cudaError_t launch_bnd_from_global(const double* glob, long long n, double h_ref
 template <typename T>
 cudaError_t launch_bnd_to_global(const T* bnd, long long n, double h_ref, int nlon, int nlat,
                                  double* glob, cudaStream_t st);
-cudaError_t launch_restrict_level(const SubDesc* subs, int n_sub, int nlon, int nlat,
-                                  const double* glob_traj, double* xb_a, int max_pts, cudaStream_t st);
+cudaError_t launch_restrict_level(const SubDesc* subs, int n_sub, int nlon, int nlat, const double* glob,
+                                  int g0, int g1, double* xb_a, int max_pts, cudaStream_t st);
 
 // global model (whole sphere), FP64
 cudaError_t launch_global_stage(const double* x, const double* y, double* out, double ca, double cb,
                                 const RowConst* rows, double Bth, double gBth, double dt, int nlon,
                                 int nlat, cudaStream_t st);
-cudaError_t launch_observe(const double* traj, long long n, const int* level, const int* var,
-                           const double* fi, const double* fj, int nlon, int nlat, double* out,
-                           cudaStream_t st);
+cudaError_t launch_observe(const double* traj, int g0, int g1, long long n, const int* level,
+                           const int* var, const double* fi, const double* fj, int nlon, int nlat,
+                           double* out, cudaStream_t st);
 
 // L-BFGS (batched, one block per subdomain)
 struct LbState {

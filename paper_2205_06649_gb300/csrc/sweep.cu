@@ -534,7 +534,8 @@ __device__ void obs_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, in
   }
 }
 
-// Overlap penalty at level l over own points: J_mu += 1/2 c sum_v (x - m)^2 / sb^2.
+// Overlap penalty at level l over own points: Jm2 += c sum_v (x - m)^2 / sb^2
+// (twice the J_mu contribution; the caller halves the total, which is exact).
 // The differences and this level's partial sum are formed in the state
 // precision; the partial is added to the FP64 accumulator once per level (on
 // the FP64 path this is all FP64).
@@ -545,7 +546,7 @@ __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X
   const bool any_s = d.wL || d.wR || d.wS || d.wN;
   if (!any_t && !any_s) return;
   const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
-  const T i0 = (T)a.isb2[0], i1 = (T)a.isb2[1], i2 = (T)a.isb2[2];
+  const T i0 = a.isb2_s[0], i1 = a.isb2_s[1], i2 = a.isb2_s[2];
   T part = (T)0;
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
     const int rr = idx / g.nx, k = idx - rr * g.nx;
@@ -559,7 +560,7 @@ __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X
     const T e2 = X[off(g, 2, rr, k)] - tg[go + 2 * pl];
     part += (T)c * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
   }
-  Jm += 0.5 * (double)part;
+  Jm += (double)part;
 }
 
 template <typename T>
@@ -598,7 +599,7 @@ __device__ __forceinline__ bool setup_geo(const SweepArgs<T>& a, cg::cluster_gro
 template <typename T, bool DEV>
 __device__ void stage(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs, T* out,
                       const T* X, const T* Y, T cx, T cy) {
-  const T dt = (T)a.dt, Bth = (T)a.Bth, gBth = (T)a.gBth, href = (T)a.h_ref;
+  const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
   const int P = g.P;
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
     const int rr = idx / g.nx, k = idx - rr * g.nx;
@@ -716,6 +717,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 8 ? 2 : 1) fwd_kernel(SweepA
     obs_level(a, g, X, l + 1, Jo);
     overlap_level(a, g, X, l + 1, Jm);
   }
+  Jm *= 0.5;
   block_reduce2<T>(Jo, Jm, scratch);
   if (threadIdx.x == 0) {
     a.part[((size_t)g.s * a.cl_max + g.rank) * 2 + 0] = Jo;
@@ -745,7 +747,7 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
   const bool any_s = d.wL || d.wR || d.wS || d.wN;
   if ((any_t || any_s) && a.mu != 0.0) {
     const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
-    const T m0 = (T)(a.mu * a.isb2[0]), m1 = (T)(a.mu * a.isb2[1]), m2 = (T)(a.mu * a.isb2[2]);
+    const T m0 = a.musb2_s[0], m1 = a.musb2_s[1], m2 = a.musb2_s[2];
     const size_t pl = (size_t)g.ny * d.nxp;
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
       const int rr = idx / g.nx, k = idx - rr * g.nx;
@@ -797,7 +799,7 @@ __global__ void __launch_bounds__(512, sizeof(T) == 8 ? 2 : 1) adj_kernel(SweepA
   ghost_prefetch(a, g, g.a + g.L);
   if (g.L > 0) ghost_prefetch(a, g, g.a + g.L - 1);
   for (int i = threadIdx.x; i < 3 * g.P; i += blockDim.x) Lp[i] = (T)0;
-  const T dt = (T)a.dt, Bth = (T)a.Bth, gBth = (T)a.gBth, href = (T)a.h_ref;
+  const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
   const T c23 = (T)(2.0 / 3.0), c13 = (T)(1.0 / 3.0);
   const int wall_s = (g.flags & F_SWALL) ? 1 : 0;
   const int wall_n = (g.flags & F_NWALL) ? 2 : 0;
@@ -961,7 +963,7 @@ __device__ void store_delta(const SweepArgs<T>& a, const Geo<T>& g, const T* D, 
 template <typename T, bool DEV>
 __device__ void stage_tl(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs, T* dout,
                          const T* DX, const T* Y, const T* DY, T cx, T cy) {
-  const T dt = (T)a.dt, Bth = (T)a.Bth, gBth = (T)a.gBth, href = (T)a.h_ref;
+  const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
     const int rr = idx / g.nx, k = idx - rr * g.nx;
     const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;

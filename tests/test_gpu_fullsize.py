@@ -95,3 +95,47 @@ def test_batching_workload_properties_at_full_size():
         b = float((MTy[oc[s]:oc[s + 1]] * dwg[oc[s]:oc[s + 1]]).sum())
         worst = max(worst, abs(a - b) / abs(a))
     assert worst <= 1e-12, worst
+
+
+def test_large_workload_fits_and_satisfies_properties_at_full_size():
+    """2048 uneven subdomains of the 2048 x 1024 / 1024-step workload (3.3e9
+    pt-steps per evaluation) in one launch per sweep, FP64: the context fits
+    in device memory (stage states recomputed when storing them would not
+    fit), J is finite and positive, the Taylor remainder of J falls as e^2, and
+    the global model conserves mass over the 1024 steps."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("large")
+    inp = workloads.generate(wl)
+    so = np.asarray(wl.sigma_o)[inp["obs_var"]]
+    c0 = dd.Context(wl.nlon, wl.nlat, inp["dt"], wl.nsteps)
+    truth = c0.forward(torch.as_tensor(inp["x_t0"], device="cuda"))
+    lat = np.radians(workloads.LAT_MIN_DEG) + (np.arange(wl.nlat) + 0.5) * np.radians(160.0) / wl.nlat
+    cw = torch.as_tensor(np.cos(lat), device="cuda")[None, :, None]
+    m = (cw * truth[:, 0]).sum(dim=(1, 2)).cpu().numpy()
+    assert np.max(np.abs(m - m[0])) <= 1e-12 * m[0]
+    y = c0.observe(truth, inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"]).cpu().numpy() \
+        + so * inp["obs_noise"]
+    c0.destroy()
+    del truth, cw
+    torch.cuda.empty_cache()
+    ctx = _lib_ctx(wl, inp, y, so, 0, cluster=0)
+    try:
+        assert ctx.n_sub == 2048
+        assert ctx.pt_steps() > 3.0e9
+        rng = np.random.default_rng(13)
+        w = torch.tensor(0.3 * rng.standard_normal(ctx.ctrl_total), device="cuda")
+        dw = torch.tensor(rng.standard_normal(ctx.ctrl_total), device="cuda")
+        J, g = ctx.eval(w)
+        J = J.cpu().numpy()
+        assert np.all(np.isfinite(J)) and np.all(J > 0)
+        oc = ctx.offsets
+        gd = (g * dw).cpu().numpy()
+        gd = np.array([gd[oc[s]:oc[s + 1]].sum() for s in range(ctx.n_sub)])
+        r = []
+        for e in (1e-2, 1e-3):
+            Je = ctx.eval(w + e * dw, grad=False).cpu().numpy()
+            r.append(np.abs(Je - J - e * gd))
+        assert 80.0 < np.median(r[0] / r[1]) < 120.0, np.median(r[0] / r[1])
+    finally:
+        ctx.destroy()
+        torch.cuda.empty_cache()
