@@ -244,7 +244,10 @@ dd4dv_status dd4dv_trajectories(dd4dv_ctx* ctx, const double* w_all, double* tra
  * partition-of-unity sum (Eq. rest). */
 dd4dv_status dd4dv_exchange(dd4dv_ctx* ctx, const double* w_all, int device_ptrs);
 
-/* Return the exchange state to l = 0 (background everywhere). */
+/* Return the exchange state to l = 0 (background everywhere).  Two device
+ * copies when dd4dv_set_decomposition could keep a copy of that state (it
+ * does when the copy leaves 4 GB + 5 % of the device free), else a rerun of
+ * the background forecast. */
 dd4dv_status dd4dv_reset_exchange(dd4dv_ctx* ctx);
 
 /* The current assembled (boundary) trajectory [nsteps+1][3][nlat][nlon]. */

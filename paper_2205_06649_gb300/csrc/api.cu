@@ -83,6 +83,8 @@ struct dd4dv_ctx {
   bool use_stg = false;
   void* tgt = nullptr;
   void* bnd = nullptr;
+  void* tgt0 = nullptr;       // copies of tgt and bnd at l = 0 (when they fit), so that
+  void* bnd0 = nullptr;       // dd4dv_reset_exchange is two device copies
   double *xb_a = nullptr, *w = nullptr, *w_prev = nullptr, *g = nullptr, *wt = nullptr,
          *gt = nullptr, *p = nullptr, *S = nullptr, *Y = nullptr, *rho = nullptr;
   double *vw = nullptr, *vw2 = nullptr, *lam_a = nullptr, *J = nullptr, *Jt = nullptr,
@@ -396,7 +398,12 @@ void background_pass(dd4dv_ctx* ctx, bool xb_a);
 
 template <typename T>
 void reset_exchange_T(dd4dv_ctx* ctx) {
-  background_pass<T>(ctx, false);
+  if (ctx->bnd0 && ctx->tgt0) {
+    CK(cudaMemcpyAsync(ctx->bnd, ctx->bnd0, ctx->gtraj * ctx->tsize, cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(ctx->tgt, ctx->tgt0, ctx->traj_elems * ctx->tsize, cudaMemcpyDeviceToDevice, ctx->st));
+  } else {
+    background_pass<T>(ctx, false);
+  }
   CK(cudaMemsetAsync(ctx->vconst, 0, ctx->n_sub * sizeof(double), ctx->st));
   ctx->fwd_pending = false;
 }
@@ -864,6 +871,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   ctx->stg = nullptr;
   ctx->stg_elems = 0;
   ctx->use_stg = false;
+  ctx->bnd0 = ctx->tgt0 = nullptr;
   ctx->ckpt = d.ckpt_k > 0 ? d.ckpt_k : 0;
   ctx->seg = nullptr;
   if (d.ckpt_k > 0) ctx->seg = dalloc<unsigned char>(ctx, std::max<long long>(1, segl) * ctx->tsize, &L);
@@ -949,6 +957,20 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
     background_pass<T>(ctx, true);
     return 0;
   });
+  // keep the l = 0 exchange state for dd4dv_reset_exchange if it leaves the
+  // same reserve as the stage buffer free; otherwise a reset reruns the
+  // background forecast
+  {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const double need = (double)(ctx->gtraj + ctx->traj_elems) * ctx->tsize;
+    if (need + 4.0 * (1ull << 30) + 0.05 * (double)total_b <= (double)free_b) {
+      ctx->bnd0 = dalloc<unsigned char>(ctx, ctx->gtraj * ctx->tsize, &L);
+      ctx->tgt0 = dalloc<unsigned char>(ctx, ctx->traj_elems * ctx->tsize, &L);
+      CK(cudaMemcpyAsync(ctx->bnd0, ctx->bnd, ctx->gtraj * ctx->tsize, cudaMemcpyDeviceToDevice, ctx->st));
+      CK(cudaMemcpyAsync(ctx->tgt0, ctx->tgt, ctx->traj_elems * ctx->tsize, cudaMemcpyDeviceToDevice, ctx->st));
+    }
+  }
   CK(cudaMemsetAsync(ctx->vconst, 0, n_sub * sizeof(double), ctx->st));
   ctx->fwd_pending = false;
   sync(ctx);

@@ -682,7 +682,7 @@ size_t smem_bytes(int nbuf, int R, int W, bool cache) {
 // Forward sweep: x(a) (stored at level 0 by the init kernel) -> x(a+1..b),
 // trajectory stored at every level, J_o and J_mu partial sums per CTA.
 template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 8 ? 2 : 1) fwd_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(512, 2) fwd_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;
@@ -781,7 +781,7 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
 // Adjoint sweep: lambda(b) = forcing(b); lambda(n) = M_n^T lambda(n+1) + forcing(n),
 // the RK3 stages recomputed from the stored x(n).  Writes lambda(a) to lam_a.
 template <typename T>
-__global__ void __launch_bounds__(512, sizeof(T) == 8 ? 2 : 1) adj_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;

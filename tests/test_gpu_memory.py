@@ -63,13 +63,16 @@ def test_chunked_global_runs_match_whole_trajectory(monkeypatch, precision):
 def test_stage_buffer_dropped_when_memory_is_short():
     """With stored stage states requested (ckpt_k = 0) but less free device
     memory than they need plus the reserve (4 GB + 5 % of the device), the
-    decomposition recomputes the stages and gives the same J and gradient."""
+    decomposition recomputes the stages and gives the same J and gradient;
+    without room for a copy of the l = 0 exchange state, a reset reruns the
+    background forecast and restores the same boundary trajectory."""
     wl = workloads.preset("small")
     st, inp, _ = oracle.build_setup(wl)
     ref = make_context(wl, st, inp)
     assert ref.sweep_config()["stored_stages"] == 1
     w = np.concatenate([rand_w(lp.nctrl, seed=70 + s).numpy() for s, lp in enumerate(st.locals)])
     J0, g0 = ref.eval(w)
+    B0 = ref.boundary_trajectory()
     ref.destroy()
     torch.cuda.empty_cache()
     free, total = torch.cuda.mem_get_info()
@@ -79,9 +82,14 @@ def test_stage_buffer_dropped_when_memory_is_short():
         ctx = make_context(wl, st, inp)
         assert ctx.sweep_config()["stored_stages"] == 0
         J1, g1 = ctx.eval(w)
+        ctx.outer_step()
+        changed = not np.array_equal(ctx.boundary_trajectory(), B0)
+        ctx.reset_exchange()
+        B1 = ctx.boundary_trajectory()
         ctx.destroy()
     finally:
         del hog
         torch.cuda.empty_cache()
     assert np.max(np.abs(J1 - J0) / np.abs(J0)) <= 1e-12
     assert rel(g1, g0) <= 1e-11
+    assert changed and np.array_equal(B1, B0)
