@@ -13,6 +13,7 @@ Plain, slow, FP64 PyTorch-CPU code written from the paper:
   bcov.py           B = V V^T, diagonal or recursive filter (Sec. 4, Eq. EqV)
   local.py          local functional J_s, gradient, TLM (Sec. 3.3, Alg. 6)
   lbfgs.py          local L-BFGS (Alg. 2/3, Remark after Alg. 5)
+  gauss_newton.py   local Gauss-Newton with CG inner solves (Alg. 5-7)
   dd4dvar.py        outer loop with exchange and gather (Alg. 1), global J
   problem.py        builds a Setup from a workload of ``workloads``
 
@@ -28,5 +29,6 @@ from .decomposition import Decomposition, Sub, bilinear_support, obs_membership 
 from .bcov import BOp, rf_alpha, rf_norm, rf_matrix  # noqa: F401
 from .local import Setup, LocalProblem, Observations, observe, assemble  # noqa: F401
 from .lbfgs import lbfgs, LbfgsResult  # noqa: F401
+from .gauss_newton import residuals, gn_operator, gn_hessvec, cg, gauss_newton, CgResult, GnResult  # noqa: F401
 from .dd4dvar import dd4dvar, global_J, rmse, DDResult  # noqa: F401
 from .problem import build_setup  # noqa: F401

@@ -29,6 +29,7 @@ import torch
 
 from .bcov import BOp
 from .decomposition import bilinear_support
+from .gauss_newton import gauss_newton
 from .lbfgs import lbfgs
 from .local import Setup, assemble
 from .swe import BoxGeom, Ghosts, rk3_step
@@ -48,7 +49,10 @@ class DDResult:
 
 
 def dd4dvar(st: Setup, max_outer: int = 10, eps: float = 1e-6, m: int = 5,
-            local_iters: int = 20, gtol: float = 1e-6) -> DDResult:
+            local_iters: int = 20, gtol: float = 1e-6, local_solver: str = "lbfgs",
+            gn_iters: int = 3, cg_iters: int = 10, cg_tol: float = 1e-6) -> DDResult:
+    """local_solver "lbfgs" (Algorithm 2/3 with L-BFGS) or "gn" (Gauss-Newton
+    with CG inner solves, Algorithms 6-7; gauss_newton.py)."""
     B = st.xb_traj.clone()
     prev = st.background_prev()
     w = [torch.zeros(lp.nctrl, dtype=F64) for lp in st.locals]
@@ -60,6 +64,14 @@ def dd4dvar(st: Setup, max_outer: int = 10, eps: float = 1e-6, m: int = 5,
         new_w = []
         Jl = []
         for lp, ws in zip(st.locals, w):
+            if local_solver == "gn":
+                res = gauss_newton(lp, ws, B, prev, gn_iters=gn_iters, cg_iters=cg_iters,
+                                   cg_tol=cg_tol, gtol=gtol)
+                evals += 1 + res.iters
+                new_w.append(res.w)
+                Jl.append(res.J)
+                continue
+
             def fg(v, lp=lp):
                 J, g, _ = lp.J_and_grad(v, B, prev)
                 return J, g
