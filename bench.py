@@ -494,6 +494,26 @@ def main():
                 "speedup": (t64 / t32) if t32 else None,
                 "outer_fp64": len(h64), "outer_fp32": len(h32)}
             ctx32.destroy()
+            # Gauss-Newton local solver (Algorithms 6-7) on the FP64 path: one
+            # outer step timed like the L-BFGS step, and its time to the same
+            # analysis RMSE target
+            gn_solver = dd.solver_defaults(lbfgs_m=wl.lbfgs_m, max_local_iters=wl.local_iters,
+                                           max_outer=wl.max_outer, local_solver=1, gn_iters=3,
+                                           cg_iters=10, cg_tol=1e-6)
+            for _ in range(2):
+                ctx.set_controls(zeros)
+                ctx.reset_exchange()
+                ctx.outer_step(gn_solver)
+            ms_gn, st_gn, _ = timed_steps(ctx, gn_solver, args.steps, zeros, stream, torch)
+            hgn = time_to_analysis(ctx, gn_solver, truth[0], wl.max_outer, torch, stream, zeros)
+            tgn = next((t for t, r, _ in hgn if r <= target), None)
+            extras["gauss_newton"] = {
+                "settings": {"gn_iters": 3, "cg_iters": 10, "cg_tol": 1e-6},
+                "value": st_gn.pt_steps / (ms_gn / 1e3), "unit": UNIT, "ms_per_step": ms_gn / args.steps,
+                "pt_steps": "evaluations (forward + adjoint) and Gauss-Newton products (tangent-linear + "
+                            "adjoint) per subdomain",
+                "rmse_h_final": hgn[-1][1], "s_to_target": tgn, "outer": len(hgn),
+                "speedup_vs_lbfgs_fp64": (t64 / tgn) if tgn else None}
 
         cpu = None
         if not args.no_cpu_baseline and world == 1:

@@ -134,6 +134,19 @@ typedef struct {
                               L-BFGS direction, line-search trial, exchange) is
                               captured once as a CUDA graph and replayed;
                               0: launched eagerly.  Same results.        */
+  int local_solver;        /* 0: L-BFGS (above); 1: Gauss-Newton (Algorithm 5
+                              as Algorithm 6) with conjugate-gradient inner
+                              solves of (I + G^T G) dw = -grad J_s in the
+                              control variable (the B-preconditioned system
+                              of Algorithm 7; CG gives the Lanczos iterates) */
+  int gn_iters;            /* Gauss-Newton iterations per outer iteration
+                              (each: one J/grad evaluation, one CG solve);
+                              a subdomain stops early when
+                              ||g|| <= gtol_rel ||g_0||                      */
+  int cg_iters;            /* CG iterations per Gauss-Newton iteration; one
+                              Gauss-Newton product (tangent-linear sweep +
+                              adjoint sweep) each                            */
+  double cg_tol;           /* CG stop: ||r|| <= cg_tol ||r_0||              */
 } dd4dv_solver;
 
 typedef struct {
@@ -237,6 +250,17 @@ dd4dv_status dd4dv_traj_layout(const dd4dv_ctx* ctx, long long* offsets);
 /* Local trajectories at w_all (forward model only), packed layout, FP64, full h. */
 dd4dv_status dd4dv_trajectories(dd4dv_ctx* ctx, const double* w_all, double* traj_all,
                                 int device_ptrs);
+
+/* Gauss-Newton product of every local problem (test instrument and building
+ * block of local_solver = 1): Ap = (I + G^T G) p with G = dr/dw the
+ * derivative, at w_all, of the weighted residuals of J_s = 1/2 w.w +
+ * 1/2 r.r (observation misfits sqrt(lambda omega) (H x - y) / sigma_o and
+ * overlap mismatches sqrt(mu) (x - x^t) / sigma_b per covering neighbour t).
+ * Formed matrix-free: V p, the tangent-linear sweep (Algorithm 6 TLM), the
+ * adjoint sweep forced by lambda H^T W H dx + mu c dx / sigma_b^2 (Algorithm 6
+ * ADJ), V^T.  Packed control layout for w_all, p_all, Ap_all. */
+dd4dv_status dd4dv_gn_hessvec(dd4dv_ctx* ctx, const double* w_all, const double* p_all, double* Ap_all,
+                              int device_ptrs);
 
 /* Exchange step of Algorithm 1 for given local controls: run every local
  * model at w_all, record the local trajectories as the neighbour data of the

@@ -54,7 +54,8 @@ def _ptr(x, dtype, device: bool):
 
 def solver_defaults(**kw) -> _abi.dd4dv_solver:
     s = _abi.dd4dv_solver(lbfgs_m=5, max_local_iters=20, max_trials=20, max_outer=10,
-                          eps_outer=1e-6, gtol_rel=1e-6, c1=1e-4, use_graphs=1)
+                          eps_outer=1e-6, gtol_rel=1e-6, c1=1e-4, use_graphs=1, local_solver=0,
+                          gn_iters=3, cg_iters=10, cg_tol=1e-6)
     for k, v in kw.items():
         setattr(s, k, v)
     return s
@@ -294,6 +295,23 @@ class Context:
         call = lambda: lib.dd4dv_adjoint(self._h, _ptr(w, np.float64, dev), _ptr(y, np.float64, dev),
                                          _ptr(out, np.float64, dev), int(dev))
         self._check(self._device_call(call, w, y, out) if dev else call())
+        return out
+
+    def gn_hessvec(self, w, p):
+        """Gauss-Newton product (I + G^T G) p of every local problem at w
+        (packed control layout)."""
+        self._fwd_token += 1
+        dev = _is_torch_cuda(w)
+        if dev:
+            import torch
+            out = torch.empty(self.ctrl_total, dtype=torch.float64, device=w.device)
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            p = np.ascontiguousarray(p, dtype=np.float64)
+            out = np.zeros(self.ctrl_total)
+        call = lambda: lib.dd4dv_gn_hessvec(self._h, _ptr(w, np.float64, dev), _ptr(p, np.float64, dev),
+                                            _ptr(out, np.float64, dev), int(dev))
+        self._check(self._device_call(call, w, p, out) if dev else call())
         return out
 
     def trajectories(self, w):

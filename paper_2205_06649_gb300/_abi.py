@@ -36,7 +36,8 @@ class dd4dv_decomp(C.Structure):
 class dd4dv_solver(C.Structure):
     _fields_ = [("lbfgs_m", C.c_int), ("max_local_iters", C.c_int), ("max_trials", C.c_int),
                 ("max_outer", C.c_int), ("eps_outer", C.c_double), ("gtol_rel", C.c_double),
-                ("c1", C.c_double), ("use_graphs", C.c_int)]
+                ("c1", C.c_double), ("use_graphs", C.c_int), ("local_solver", C.c_int),
+                ("gn_iters", C.c_int), ("cg_iters", C.c_int), ("cg_tol", C.c_double)]
 
 
 class dd4dv_stats(C.Structure):
@@ -65,6 +66,7 @@ PROTOTYPES = {
     "dd4dv_eval_backward": (C.c_int, [_CTX, _P, _P, C.c_int]),
     "dd4dv_tlm": (C.c_int, [_CTX, _P, _P, _P, C.c_int]),
     "dd4dv_adjoint": (C.c_int, [_CTX, _P, _P, _P, C.c_int]),
+    "dd4dv_gn_hessvec": (C.c_int, [_CTX, _P, _P, _P, C.c_int]),
     "dd4dv_traj_layout": (C.c_int, [_CTX, _P]),
     "dd4dv_trajectories": (C.c_int, [_CTX, _P, _P, C.c_int]),
     "dd4dv_exchange": (C.c_int, [_CTX, _P, C.c_int]),

@@ -98,6 +98,10 @@ struct dd4dv_ctx {
   double* sc_w_d = nullptr;
   int *lon_cov_d = nullptr, *lat_cov_d = nullptr, *t_cov_d = nullptr;
   LbState* lbst = nullptr;
+  // Gauss-Newton local solver (allocated on first use)
+  double *cg_r = nullptr, *cg_p = nullptr, *cg_Ap = nullptr, *cg_dw = nullptr;
+  CgState* cgst = nullptr;
+  void* gn_dx = nullptr;
   int* phase_d = nullptr;
   int* counter_d = nullptr;
   int* counter_h = nullptr;   // pinned
@@ -274,6 +278,7 @@ SweepArgs<T> sweep_args(dd4dv_ctx* ctx) {
   a.yforce = nullptr;
   a.dx_out = nullptr;
   a.dx0 = nullptr;
+  a.gn_dx = nullptr;
   a.R = ctx->R;
   a.W = ctx->W;
   a.err = ctx->err_d;
@@ -359,6 +364,72 @@ void eval_T(dd4dv_ctx* ctx, const double* w, double* J, double* grad, double* pa
     KL(launch_adjoint<T>(a, ctx->cl, ctx->nthreads, ctx->st));
     apply_VT(ctx, ctx->lam_a, w, scale, grad, active, av);
   }
+}
+
+// Cluster size and rows per CTA of the tangent-linear sweep (six buffers):
+// the smallest cluster (>= the evaluation's) whose stripes fit in shared memory.
+void tlm_shape(dd4dv_ctx* ctx, int* cl, int* R) {
+  for (int c = ctx->cl; c <= std::min(16, ctx->min_ny); ++c) {
+    const int r = (ctx->max_ny + c - 1) / c;
+    const size_t need = ctx->m.precision == 1 ? smem_tlm<float>(r, ctx->W) : smem_tlm<double>(r, ctx->W);
+    if (need <= 232448 && (c <= 8 || c == 16)) {
+      *cl = c;
+      *R = r;
+      return;
+    }
+  }
+  fail(ctx, DD4DV_EINVAL, "boxes too large for the tangent-linear sweep");
+}
+
+// out = V p (packed control layout) for the subdomains in the mask.
+void apply_V(dd4dv_ctx* ctx, const double* p, double* out, const int* active, int av) {
+  const double* src = p;
+  if (ctx->corr_len > 0.0) {
+    KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, p, nullptr, ctx->vw2, active, av, ctx->max_pts, ctx->st));
+    RFArgs ra{ctx->subs_d, ctx->n_sub, ctx->rf_alpha, ctx->rf_c, ctx->rf_passes, active, av};
+    KL(launch_rf_rows(ctx->vw2, ra, ctx->max_ny, ctx->st));
+    KL(launch_rf_cols(ctx->vw2, ra, ctx->max_nx, ctx->st));
+    src = ctx->vw2;
+  }
+  KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, src, ctx->sigma_d, out, active, av, ctx->max_pts, ctx->st));
+}
+
+// Work buffers of the Gauss-Newton solver, allocated with the decomposition's
+// on first use.
+void ensure_gn(dd4dv_ctx* ctx) {
+  if (ctx->gn_dx) return;
+  auto& L = ctx->dec_allocs;
+  const size_t C = (size_t)ctx->ctrl_total;
+  ctx->cg_r = dalloc<double>(ctx, C, &L);
+  ctx->cg_p = dalloc<double>(ctx, C, &L);
+  ctx->cg_Ap = dalloc<double>(ctx, C, &L);
+  ctx->cg_dw = dalloc<double>(ctx, C, &L);
+  ctx->cgst = dalloc<CgState>(ctx, ctx->n_sub, &L);
+  ctx->gn_dx = dalloc<unsigned char>(ctx, std::max<long long>(1, ctx->traj_elems) * ctx->tsize, &L);
+}
+
+// Gauss-Newton product Ap = (I + G^T G) p for the subdomains in the mask, at
+// the linearisation point whose trajectory (and stage states) the last
+// forward sweep stored: V p, tangent-linear sweep (dx and H dx), adjoint sweep
+// forced by dx, then p + V^T lambda(a).
+template <typename T>
+void gn_product_T(dd4dv_ctx* ctx, const double* p, double* Ap, const int* active, int av) {
+  int tl_cl = 0, tl_R = 0;
+  tlm_shape(ctx, &tl_cl, &tl_R);
+  apply_V(ctx, p, ctx->io_c, active, av);
+  SweepArgs<T> a = sweep_args<T>(ctx);
+  a.active = active;
+  a.active_value = av;
+  a.dx0 = ctx->io_c;
+  a.gn_dx = static_cast<T*>(ctx->gn_dx);
+  a.R = tl_R;
+  KL(launch_tlm<T>(a, tl_cl, ctx->nthreads, ctx->st));
+  SweepArgs<T> b = sweep_args<T>(ctx);
+  b.active = active;
+  b.active_value = av;
+  b.gn_dx = static_cast<T*>(ctx->gn_dx);
+  KL(launch_adjoint<T>(b, ctx->cl, ctx->nthreads, ctx->st));
+  apply_VT(ctx, ctx->lam_a, p, nullptr, Ap, active, av);
 }
 
 template <typename T>
@@ -872,6 +943,9 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   ctx->stg_elems = 0;
   ctx->use_stg = false;
   ctx->bnd0 = ctx->tgt0 = nullptr;
+  ctx->cg_r = ctx->cg_p = ctx->cg_Ap = ctx->cg_dw = nullptr;
+  ctx->cgst = nullptr;
+  ctx->gn_dx = nullptr;
   ctx->ckpt = d.ckpt_k > 0 ? d.ckpt_k : 0;
   ctx->seg = nullptr;
   if (d.ckpt_k > 0) ctx->seg = dalloc<unsigned char>(ctx, std::max<long long>(1, segl) * ctx->tsize, &L);
@@ -1320,15 +1394,8 @@ dd4dv_status dd4dv_tlm(dd4dv_ctx* ctx, const double* w_all, const double* dw_all
   return guard(ctx, [&] {
     require_dec(ctx);
     if (!w_all || !dw_all || !dx_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
-    // the tangent-linear sweep holds six buffers: use the smallest cluster
-    // (>= the evaluation's) whose stripes fit in shared memory
-    int tl_cl = -1, tl_R = 0;
-    for (int c = ctx->cl; c <= std::min(16, ctx->min_ny); ++c) {
-      const int R = (ctx->max_ny + c - 1) / c;
-      const size_t need = ctx->m.precision == 1 ? smem_tlm<float>(R, ctx->W) : smem_tlm<double>(R, ctx->W);
-      if (need <= 232448 && (c <= 8 || c == 16)) { tl_cl = c; tl_R = R; break; }
-    }
-    if (tl_cl < 0) fail(ctx, DD4DV_EINVAL, "boxes too large for the tangent-linear sweep");
+    int tl_cl = 0, tl_R = 0;
+    tlm_shape(ctx, &tl_cl, &tl_R);
     const size_t C = ctx->ctrl_total;
     const double* w = stage_in(ctx, w_all, ctx->io_a, C, device_ptrs);
     const double* dw = stage_in(ctx, dw_all, ctx->io_b, C, device_ptrs);
@@ -1336,16 +1403,7 @@ dd4dv_status dd4dv_tlm(dd4dv_ctx* ctx, const double* w_all, const double* dw_all
     by_precision(ctx, [&](auto t) {
       using T = decltype(t);
       init_states<T>(ctx, w, ctx->vw, nullptr, 0);
-      // dx(a) = V dw into vw2
-      const double* src = dw;
-      if (ctx->corr_len > 0.0) {
-        KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, dw, nullptr, ctx->vw2, nullptr, 0, ctx->max_pts, ctx->st));
-        RFArgs ra{ctx->subs_d, ctx->n_sub, ctx->rf_alpha, ctx->rf_c, ctx->rf_passes, nullptr, 0};
-        KL(launch_rf_rows(ctx->vw2, ra, ctx->max_ny, ctx->st));
-        KL(launch_rf_cols(ctx->vw2, ra, ctx->max_nx, ctx->st));
-        src = ctx->vw2;
-      }
-      KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, src, ctx->sigma_d, ctx->io_c, nullptr, 0, ctx->max_pts, ctx->st));
+      apply_V(ctx, dw, ctx->io_c, nullptr, 0);   // dx(a) = V dw
       SweepArgs<T> a = sweep_args<T>(ctx);
       a.dx0 = ctx->io_c;
       a.dx_out = out;
@@ -1389,6 +1447,32 @@ dd4dv_status dd4dv_adjoint(dd4dv_ctx* ctx, const double* w_all, const double* y_
     ctx->fwd_pending = false;
     if (!device_ptrs) {
       d2h(ctx, dw_all, out, C * sizeof(double));
+      sync(ctx);
+    }
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_gn_hessvec(dd4dv_ctx* ctx, const double* w_all, const double* p_all, double* Ap_all,
+                              int device_ptrs) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!w_all || !p_all || !Ap_all) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    ensure_gn(ctx);
+    const size_t C = ctx->ctrl_total;
+    const double* w = stage_in(ctx, w_all, ctx->io_a, C, device_ptrs);
+    const double* pv = stage_in(ctx, p_all, ctx->io_b, C, device_ptrs);
+    double* out = device_ptrs ? Ap_all : ctx->cg_Ap;
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      init_states<T>(ctx, w, ctx->vw, nullptr, 0);
+      forward_sweep<T>(ctx, nullptr, 0);   // linearisation trajectory
+      gn_product_T<T>(ctx, pv, out, nullptr, 0);
+      return 0;
+    });
+    ctx->fwd_pending = false;
+    if (!device_ptrs) {
+      d2h(ctx, Ap_all, out, C * sizeof(double));
       sync(ctx);
     }
     return DD4DV_OK;
@@ -1561,6 +1645,9 @@ static void check_solver(dd4dv_ctx* ctx, const dd4dv_solver* s) {
   if (s->max_local_iters < 0 || s->max_trials < 1 || s->max_outer < 0) fail(ctx, DD4DV_EINVAL, "bad iteration limits");
   if (!(s->c1 > 0.0 && s->c1 < 1.0)) fail(ctx, DD4DV_EINVAL, "c1 must be in (0,1)");
   if (!(s->gtol_rel >= 0.0) || !(s->eps_outer >= 0.0)) fail(ctx, DD4DV_EINVAL, "tolerances must be >= 0");
+  if (s->local_solver != 0 && s->local_solver != 1) fail(ctx, DD4DV_EINVAL, "local_solver must be 0 or 1");
+  if (s->local_solver == 1 && (s->gn_iters < 0 || s->cg_iters < 0 || !(s->cg_tol >= 0.0)))
+    fail(ctx, DD4DV_EINVAL, "gn_iters, cg_iters and cg_tol must be >= 0");
 }
 
 }  // extern "C"
@@ -1590,11 +1677,96 @@ static cudaGraphExec_t capture_graph(dd4dv_ctx* ctx, F&& f, long long* nk) {
   return ge;
 }
 
-// One outer iteration of Algorithm 1.  The host loop only reads two counters
-// per step (subdomains still in a line search / needing a direction); the
-// device work of each step is one graph launch when sv.use_graphs is set.
+// One outer iteration with the Gauss-Newton local solver: for each
+// Gauss-Newton iteration, a batched J / grad J evaluation at w (which also
+// stores the linearisation trajectory), CG on (I + G^T G) dw = -grad J with
+// one batched Gauss-Newton product per CG iteration (masked to the
+// subdomains still iterating), w += dw; a last evaluation for the
+// statistics; then the Exchange.
+template <typename T>
+static void gn_outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* stats) {
+  ensure_gn(ctx);
+  CgArgs ca{};
+  ca.subs = ctx->subs_d;
+  ca.n_sub = ctx->n_sub;
+  ca.g = ctx->g;
+  ca.r = ctx->cg_r;
+  ca.p = ctx->cg_p;
+  ca.Ap = ctx->cg_Ap;
+  ca.dw = ctx->cg_dw;
+  ca.st = ctx->cgst;
+  ca.phase = ctx->phase_d;
+  ca.counter = ctx->counter_d;
+  ca.max_iter = sv.cg_iters;
+  ca.tol = sv.cg_tol;
+  ca.gtol = sv.gtol_rel;
+  std::vector<long long> sub_pts(ctx->n_sub);
+  for (int s = 0; s < ctx->n_sub; ++s) {
+    const SubDesc& d = ctx->subs_h[s];
+    sub_pts[s] = (long long)d.nx * d.ny * (d.b - d.a);
+  }
+  long long evals = 0, sub_evals = 0, pts = 0;
+  for (int it = 0;; ++it) {
+    eval_T<T>(ctx, ctx->w, ctx->J, ctx->g, nullptr, nullptr, 0, nullptr);
+    ++evals;
+    sub_evals += ctx->n_sub;
+    pts += ctx->pt_steps;
+    const bool last = it >= sv.gn_iters;
+    CgArgs c0 = ca;
+    c0.first = it == 0;
+    if (last) c0.max_iter = 0;   // norms for the statistics only
+    KL(launch_cg_start(c0, ctx->st));
+    if (last) break;
+    d2h(ctx, ctx->counter_h, ctx->counter_d, sizeof(int));
+    CK(cudaStreamSynchronize(ctx->st));
+    if (ctx->counter_h[0] == 0) break;
+    for (int k = 0; k < sv.cg_iters; ++k) {
+      d2h(ctx, ctx->phase_h, ctx->phase_d, ctx->n_sub * sizeof(int));
+      gn_product_T<T>(ctx, ctx->cg_p, ctx->cg_Ap, ctx->phase_d, 1);
+      KL(launch_cg_step(ca, ctx->st));
+      d2h(ctx, ctx->counter_h, ctx->counter_d, sizeof(int));
+      CK(cudaStreamSynchronize(ctx->st));
+      for (int s = 0; s < ctx->n_sub; ++s)
+        if (ctx->phase_h[s] == 1) pts += sub_pts[s];
+      if (ctx->counter_h[0] == 0) break;
+    }
+    KL(launch_axpy(ctx->w, ctx->cg_dw, ctx->ctrl_total, ctx->st));
+  }
+  exchange_T<T>(ctx, ctx->w);
+  KL(launch_max_abs_diff(ctx->w, ctx->w_prev, ctx->ctrl_total, ctx->scal_d, ctx->st));
+  CK(cudaMemcpyAsync(ctx->w_prev, ctx->w, ctx->ctrl_total * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  d2h(ctx, ctx->scal_h, ctx->scal_d, sizeof(double));
+  std::vector<double> J(ctx->n_sub);
+  std::vector<CgState> cs(ctx->n_sub);
+  d2h(ctx, J.data(), ctx->J, ctx->n_sub * sizeof(double));
+  d2h(ctx, cs.data(), ctx->cgst, ctx->n_sub * sizeof(CgState));
+  sync(ctx);
+  if (stats) {
+    stats->outer_iters += 1;
+    stats->evals += evals;
+    stats->sub_evals += sub_evals;
+    stats->pt_steps += pts;
+    stats->dw_inf = ctx->scal_h[0];
+    double Js = 0.0, gmax = 0.0;
+    for (int s = 0; s < ctx->n_sub; ++s) {
+      Js += J[s];
+      if (cs[s].g0n > 0.0) gmax = std::max(gmax, std::sqrt(cs[s].rr0) / cs[s].g0n);
+    }
+    stats->J_sum = Js;
+    stats->gnorm_rel_max = gmax;
+  }
+}
+
+// One outer iteration of Algorithm 1.  With L-BFGS the host loop only reads
+// two counters per step (subdomains still in a line search / needing a
+// direction); the device work of each step is one graph launch when
+// sv.use_graphs is set.
 template <typename T>
 static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* stats) {
+  if (sv.local_solver == 1) {
+    gn_outer_step_T<T>(ctx, sv, stats);
+    return;
+  }
   LbArgs la{};
   la.subs = ctx->subs_d;
   la.n_sub = ctx->n_sub;

@@ -848,6 +848,124 @@ cudaError_t launch_observe(const double* traj, int g0, int g1, long long n, cons
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Conjugate gradients (Hestenes-Stiefel) on (I + G^T G) dw = -g per subdomain,
+// the inner solve of the Gauss-Newton iteration (Algorithm 7 in the control
+// variable).  The products A p come from the sweeps between the kernels.
+__global__ void cg_start_kernel(CgArgs a) {
+  __shared__ double sh[33];
+  __shared__ int go;
+  const int s = blockIdx.x;
+  const SubDesc d = a.subs[s];
+  const int n = 3 * d.ny * d.nx;
+  const size_t off = d.ctrl_off;
+  const double* g = a.g + off;
+  const double gg = dot(g, g, n, sh);
+  if (threadIdx.x == 0) {
+    CgState c = a.st[s];
+    if (a.first) c.g0n = sqrt(gg);
+    c.rr = c.rr0 = gg;
+    c.k = 0;
+    const bool run = c.g0n > 0.0 && sqrt(gg) > a.gtol * c.g0n && gg > 0.0 && a.max_iter > 0;
+    c.status = run ? 0 : 4;
+    a.st[s] = c;
+    a.phase[s] = run ? 1 : 0;
+    if (run) atomicAdd(a.counter, 1);
+    go = run;
+  }
+  __syncthreads();
+  double* r = a.r + off;
+  double* p = a.p + off;
+  double* dw = a.dw + off;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    dw[i] = 0.0;
+    if (go) {
+      r[i] = -g[i];
+      p[i] = -g[i];
+    }
+  }
+}
+
+__global__ void cg_step_kernel(CgArgs a) {
+  __shared__ double sh[33];
+  __shared__ double alpha, beta;
+  __shared__ int mode;   // 0 skip, 1 update and continue, 2 update and stop
+  const int s = blockIdx.x;
+  if (a.phase[s] != 1) return;
+  const SubDesc d = a.subs[s];
+  const int n = 3 * d.ny * d.nx;
+  const size_t off = d.ctrl_off;
+  double* r = a.r + off;
+  double* p = a.p + off;
+  double* dw = a.dw + off;
+  const double* Ap = a.Ap + off;
+  const double pAp = dot(p, Ap, n, sh);
+  if (threadIdx.x == 0) {
+    CgState c = a.st[s];
+    if (!(pAp > 0.0)) {
+      c.status = 3;
+      a.st[s] = c;
+      a.phase[s] = 0;
+      mode = 0;
+    } else {
+      alpha = c.rr / pAp;
+      mode = 1;
+    }
+  }
+  __syncthreads();
+  if (mode == 0) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    dw[i] += alpha * p[i];
+    r[i] -= alpha * Ap[i];
+  }
+  const double rr1 = dot(r, r, n, sh);   // block_sum barriers order the updates above
+  if (threadIdx.x == 0) {
+    CgState c = a.st[s];
+    c.k += 1;
+    if (rr1 <= a.tol * a.tol * c.rr0) {
+      c.status = 1;
+      mode = 2;
+    } else if (c.k >= a.max_iter) {
+      c.status = 2;
+      mode = 2;
+    } else {
+      beta = rr1 / c.rr;
+      mode = 1;
+      atomicAdd(a.counter, 1);
+    }
+    c.rr = rr1;
+    a.st[s] = c;
+    if (mode == 2) a.phase[s] = 0;
+  }
+  __syncthreads();
+  if (mode != 1) return;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = r[i] + beta * p[i];
+}
+
+__global__ void axpy_kernel(double* y, const double* x, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+
+cudaError_t launch_cg_start(const CgArgs& a, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  cg_start_kernel<<<a.n_sub, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_cg_step(const CgArgs& a, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  cg_step_kernel<<<a.n_sub, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_axpy(double* y, const double* x, long long n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  axpy_kernel<<<blocks_for(n, 256), 256, 0, st>>>(y, x, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_lb_start(const LbArgs& a, cudaStream_t st) {
   lb_start_kernel<<<a.n_sub, 256, 0, st>>>(a);
   return cudaGetLastError();

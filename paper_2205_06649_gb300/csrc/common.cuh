@@ -93,6 +93,10 @@ struct SweepArgs {
   const double* yforce;       // external adjoint forcing (packed FP64 trajectories) or nullptr
   double* dx_out;             // tangent-linear output (packed FP64 trajectories)
   const double* dx0;          // tangent-linear initial perturbation (packed control layout)
+  T* gn_dx;                   // Gauss-Newton products: the tangent-linear sweep stores dx here
+                              // (trajectory layout) and sets obs_force = lambda w H dx; the
+                              // adjoint sweep then takes its overlap forcing mu c dx / sb^2
+                              // from it instead of mu c (x - m) / sb^2
   int R;                      // max rows per CTA
   int W;                      // shared-memory row pitch (>= max nx + 2)
   int* err;                   // device error word (0 = ok)
@@ -200,6 +204,25 @@ struct LbArgs {
 cudaError_t launch_lb_start(const LbArgs& a, cudaStream_t st);
 cudaError_t launch_lb_direction(const LbArgs& a, cudaStream_t st);
 cudaError_t launch_lb_linesearch(const LbArgs& a, cudaStream_t st);
+// Batched conjugate gradients for the Gauss-Newton normal equations, one
+// block per subdomain (fixed-order block reductions).
+struct CgState {
+  double rr, rr0, g0n;
+  int k, status;   // status: 0 running, 1 converged, 2 iteration limit, 3 p.Ap <= 0, 4 skipped
+};
+struct CgArgs {
+  const SubDesc* subs; int n_sub;
+  const double* g;                     // gradient at the linearisation point (rhs = -g)
+  double *r, *p, *Ap, *dw;             // packed control layout
+  CgState* st;
+  int* phase;                          // [n_sub] 1 = solving (sweep mask)
+  int* counter;                        // # still solving
+  int max_iter, first;                 // first: this is the first Gauss-Newton iteration
+  double tol, gtol;
+};
+cudaError_t launch_cg_start(const CgArgs& a, cudaStream_t st);
+cudaError_t launch_cg_step(const CgArgs& a, cudaStream_t st);
+cudaError_t launch_axpy(double* y, const double* x, long long n, cudaStream_t st);   // y += x
 cudaError_t launch_max_abs_diff(const double* a, const double* b, long long n, double* out,
                                 cudaStream_t st);
 cudaError_t launch_finite_check(const double* a, long long n, int* flag, cudaStream_t st);

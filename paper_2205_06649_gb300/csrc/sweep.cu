@@ -534,6 +534,29 @@ __device__ void obs_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, in
   }
 }
 
+// Linearised observation forcing for Gauss-Newton products: with D the
+// tangent-linear state at level l, obs_force = lambda w (H D) for the
+// observations of level l whose lower corner row is one of this CTA's rows.
+template <typename T>
+__device__ void obs_level_lin(const SweepArgs<T>& a, const Geo<T>& g, const T* D, int l) {
+  const int o0 = a.lvl_obs[g.d.obs_lvl + l], o1 = a.lvl_obs[g.d.obs_lvl + l + 1];
+  for (int o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
+    const ObsRec ob = a.obs[o];
+    const int rr = ob.r0 - g.R0;
+    if (rr < 0 || rr >= g.Rn) continue;
+    const T* P = D + ob.var * g.P;
+    double acc = 0.0;
+    const double wj0 = 1.0 - ob.dj, wi0 = 1.0 - ob.di;
+    acc += (wj0 * wi0) * (double)P[(rr + 1) * g.W + ob.k0 + 1];
+    if (ob.di != 0.0) acc += (wj0 * ob.di) * (double)P[(rr + 1) * g.W + ob.k1 + 1];
+    if (ob.dj != 0.0) {
+      acc += (ob.dj * wi0) * (double)P[(rr + 2) * g.W + ob.k0 + 1];
+      if (ob.di != 0.0) acc += (ob.dj * ob.di) * (double)P[(rr + 2) * g.W + ob.k1 + 1];
+    }
+    a.obs_force[o] = a.lam * ob.w * acc;
+  }
+}
+
 // Overlap penalty at level l over own points: Jm2 += c sum_v (x - m)^2 / sb^2
 // (twice the J_mu contribution; the caller halves the total, which is exact).
 // The differences and this level's partial sum are formed in the state
@@ -745,7 +768,22 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
   }
   const bool any_t = (l < d.tA) || (l > g.L - d.tB);
   const bool any_s = d.wL || d.wR || d.wS || d.wN;
-  if ((any_t || any_s) && a.mu != 0.0) {
+  if ((any_t || any_s) && a.mu != 0.0 && a.gn_dx) {   // Gauss-Newton product: mu c dx / sb^2
+    const T* dx = a.gn_dx + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
+    const T m0 = a.musb2_s[0], m1 = a.musb2_s[1], m2 = a.musb2_s[2];
+    const size_t pl = (size_t)g.ny * d.nxp;
+    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+      const int rr = idx / g.nx, k = idx - rr * g.nx;
+      const int r = g.R0 + rr;
+      const int c = overlap_count(g, l, r, k);
+      if (c == 0) continue;
+      const size_t go = (size_t)r * d.nxp + k;
+      const T cc = (T)c;
+      Lb[off(g, 0, rr, k)] += cc * m0 * dx[go];
+      Lb[off(g, 1, rr, k)] += cc * m1 * dx[go + pl];
+      Lb[off(g, 2, rr, k)] += cc * m2 * dx[go + 2 * pl];
+    }
+  } else if ((any_t || any_s) && a.mu != 0.0) {
     const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
     const T m0 = a.musb2_s[0], m1 = a.musb2_s[1], m2 = a.musb2_s[2];
     const size_t pl = (size_t)g.ny * d.nxp;
@@ -913,7 +951,8 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
 }
 
 // Tangent-linear sweep: x and dx advanced together; x stored to the
-// trajectory, dx to the packed FP64 output.
+// trajectory, dx to the packed FP64 output and/or, for Gauss-Newton products,
+// to gn_dx in the state precision with the linearised observation forcing.
 template <typename T>
 __device__ void load_delta0(const SweepArgs<T>& a, const Geo<T>& g, T* D) {
   const double* src = a.dx0 + g.d.ctrl_off;
@@ -990,9 +1029,35 @@ __global__ void __launch_bounds__(512) tlm_kernel(SweepArgs<T> a) {
   load_rows(a, g, rs);
   load_level(a, g, X, 0, g.a);
   load_delta0(a, g, D);
-  store_delta(a, g, D, 0);
+  if (a.dx_out) store_delta(a, g, D, 0);
+  if (a.gn_dx) {
+    store_block(g, D, a.gn_dx + g.d.traj_off);
+    obs_level_lin(a, g, D, 0);
+  }
+  // Gauss-Newton products linearise about the trajectory and stage states the
+  // last forward sweep stored: load them instead of recomputing them
+  const bool lin_loaded = a.gn_dx && a.stg && a.ckpt == 0;
   for (int l = 0; l < g.L; ++l) {
     const int n = g.a + l;
+    if (lin_loaded) {
+      T* bufs[3] = {X, S1, S2};
+      const T* srcs[3] = {a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp, stage_ptr(a, g, l, 0),
+                          stage_ptr(a, g, l, 1)};
+      const int nA[3] = {n, n + 1, n};
+      const int nB[3] = {n, n + 1, n + 1};
+      const T wA[3] = {(T)1, (T)1, (T)0.5};
+      const T wB[3] = {(T)0, (T)0, (T)0.5};
+      load_states3(a, g, bufs, srcs, nA, nB, wA, wB);
+      stage_tl<T, DEV>(a, g, rs, D1, D, X, D, (T)0, (T)1);
+      complete_buf(cl, a, g, D1, K_DELTA, 0, 0, (T)1, (T)0);
+      stage_tl<T, DEV>(a, g, rs, D2, D, S1, D1, (T)0.75, (T)0.25);
+      complete_buf(cl, a, g, D2, K_DELTA, 0, 0, (T)1, (T)0);
+      stage_tl<T, DEV>(a, g, rs, D, D, S2, D2, (T)(1.0 / 3.0), (T)(2.0 / 3.0));
+      complete_buf(cl, a, g, D, K_DELTA, 0, 0, (T)1, (T)0);
+      store_block(g, D, a.gn_dx + g.d.traj_off + (size_t)(l + 1) * 3 * g.ny * g.d.nxp);
+      obs_level_lin(a, g, D, l + 1);
+      continue;
+    }
     stage_tl<T, DEV>(a, g, rs, D1, D, X, D, (T)0, (T)1);
     stage<T, DEV>(a, g, rs, S1, X, X, (T)0, (T)1);
     complete_buf(cl, a, g, S1, K_STATE, n + 1, n + 1, (T)1, (T)0);
@@ -1006,7 +1071,11 @@ __global__ void __launch_bounds__(512) tlm_kernel(SweepArgs<T> a) {
     complete_buf(cl, a, g, X, K_STATE, n + 1, n + 1, (T)1, (T)0);
     complete_buf(cl, a, g, D, K_DELTA, 0, 0, (T)1, (T)0);
     store_level(a, g, X, l + 1);
-    store_delta(a, g, D, l + 1);
+    if (a.dx_out) store_delta(a, g, D, l + 1);
+    if (a.gn_dx) {
+      store_block(g, D, a.gn_dx + g.d.traj_off + (size_t)(l + 1) * 3 * g.ny * g.d.nxp);
+      obs_level_lin(a, g, D, l + 1);
+    }
   }
   cl.sync();
 }
