@@ -328,6 +328,70 @@ def eval_mode(args, ctx, wl, prec, stream, torch):
     return 0
 
 
+# Weak-scaling experiment of Sec. 7 (Table 3): QP spatial subdomains whose
+# extended boxes are n_loc x n_loc = 32 x 32 points (Eq. nlocx: core 24 plus
+# an overlap of 4 on each side; the wall blocks take a core of 28), problem
+# size 3 n_loc^2 QP.
+SCALEUP_LAYOUT = {2: (2, 1), 4: (2, 2), 8: (4, 2), 16: (4, 4), 32: (8, 4), 64: (8, 8)}
+
+
+def scaleup_workloads(qp, nsteps=16):
+    """(decomposed workload, undecomposed workload, lon_cuts, lat_cuts) of one
+    global problem: a 24 P1 x (24 P2 + 8) grid, nsteps steps, one time
+    window, QP = P1 x P2 spatial subdomains with 32 x 32 extended boxes;
+    observations and B as in the small workload."""
+    P1, P2 = SCALEUP_LAYOUT[qp]
+    nlon, nlat = 24 * P1, 24 * P2 + 8
+    lon_cuts = [24 * k for k in range(P1 + 1)]
+    lat_cuts = [0] + [4 + 24 * k for k in range(1, P2)] + [nlat] if P2 > 1 else [0, nlat]
+    base = workloads.preset("small").replace(
+        name=f"scaleup_qp{qp}", nlon=nlon, nlat=nlat, nsteps=nsteps, P1=P1, P2=P2, Q=1,
+        o_lon=4, o_lat=4, o_t=0)
+    return base, base.replace(name=f"scaleup_qp{qp}_undecomposed", P1=1, P2=1), lon_cuts, lat_cuts
+
+
+def scaleup_mode(args, torch):
+    import paper_2205_06649_gb300 as dd
+    """Measured scale-up of one outer iteration (Sec. 6-7, Eq. measurscale,
+    Table 3), read as Sc_1,QP = T(undecomposed problem of size 3 n_loc^2 QP)
+    / T(the same problem in QP subdomains), both on this GPU (all subdomains
+    of one problem in one launch per sweep)."""
+    rows = []
+    for qp in sorted(SCALEUP_LAYOUT):
+        times = {}
+        wl_dd, wl_1, lon_cuts, lat_cuts = scaleup_workloads(qp)
+        for wl in (wl_dd, wl_1):
+            stream = torch.cuda.Stream()
+            inp = workloads.generate(wl)
+            if wl.P1 > 1:
+                inp["lon_cuts"] = np.asarray(lon_cuts)
+                inp["lat_cuts"] = np.asarray(lat_cuts)
+            try:
+                ctx, inp, truth, obs = build_problem(wl, 0, stream.cuda_stream, inputs=inp)
+            except dd.DD4DVError as e:   # one box larger than a 16-CTA cluster's shared memory
+                times[wl.P1 * wl.P2] = (None, str(e), 0)
+                continue
+            solver = solver_for(wl)
+            zeros = torch.zeros(ctx.ctrl_total, dtype=torch.float64, device="cuda")
+            for _ in range(args.warmup):
+                ctx.set_controls(zeros)
+                ctx.reset_exchange()
+                ctx.outer_step(solver)
+            ms, stats, _ = timed_steps(ctx, solver, args.steps, zeros, stream, torch)
+            times[wl.P1 * wl.P2] = (ms / args.steps, ctx.sweep_config(), ctx.n_sub)
+            ctx.destroy()
+        t1, tq = times[1][0], times[qp][0]
+        sc = (t1 / tq) if (t1 and tq) else None
+        rows.append({"QP": qp, "problem_size": 3 * 32 * 32 * qp, "grid": [wl_dd.nlon, wl_dd.nlat],
+                     "ms_undecomposed": t1, "ms_decomposed": tq,
+                     "scale_up": sc, "shape_undecomposed": times[1][1], "shape_decomposed": times[qp][1]})
+        log(f"QP={qp}: T1 {t1} ms, TQP {tq} ms, Sc {sc}")
+    print(json.dumps({"metric": "measured scale-up Sc_1,QP of one DD-4DVar outer iteration (n_loc = 32)",
+                      "unit": "ratio", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "dtype": "f64", "data": "synthetic", "rows": rows}), flush=True)
+    return 0
+
+
 def wl_desc(wl):
     return (f"{wl.name}: {wl.nlon}x{wl.nlat} grid, {wl.nsteps} steps, {wl.P1}x{wl.P2}x{wl.Q} "
             f"subdomains ({'uneven' if wl.uneven else 'equal'}), overlap {wl.o_lon} pts / {wl.o_t} steps, "
@@ -347,10 +411,11 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip FP32 and time-to-analysis legs")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="only run this many evaluations (for an ncu launch list) and exit")
-    ap.add_argument("--mode", default="outer", choices=["outer", "eval"],
+    ap.add_argument("--mode", default="outer", choices=["outer", "eval", "scaleup"],
                     help="outer: a step is one outer iteration (default); eval: a step is one batched "
                          "J and grad J evaluation of all subdomains (for workloads too large for the "
-                         "outer-iteration bench)")
+                         "outer-iteration bench); scaleup: the weak-scaling experiment of Table 3 "
+                         "(measured scale-up of one outer iteration, QP = 2..64)")
     ap.add_argument("--ckpt", type=int, default=0, help="ckpt_k of the decomposition (0, -1 or k > 0)")
     ap.add_argument("--shape", default="",
                     help="fwd_cluster,fwd_threads,adj_cluster,adj_threads,stored_stages: force the "
@@ -371,6 +436,9 @@ def main():
     import __graft_entry__ as g
     g.build()
     import paper_2205_06649_gb300 as dd
+
+    if args.mode == "scaleup":
+        return scaleup_mode(args, torch) if rank == 0 else 0
 
     wl = workloads.preset(args.workload)
     prec = 0 if args.precision == "f64" else 1

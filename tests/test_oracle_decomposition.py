@@ -135,3 +135,24 @@ def test_table3_problem_sizes():
         size = sum(3 * s.nx * s.ny for s in dec.subs)
         assert size == 3 * 32 * 32 * qp
         assert abs(size - printed) <= 0.05 * printed
+
+
+def test_scaleup_workloads_reproduce_table3_problem_sizes():
+    """The benchmark's weak-scaling workloads (Table 3): QP subdomains whose
+    extended boxes are 32 x 32; their state count 3 n_loc^2 QP is the
+    printed problem size (two digits)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "bench", os.path.join(os.path.dirname(__file__), "..", "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for qp, printed in _read_golden("table3_problem_size.txt"):
+        dd, one, lon_cuts, lat_cuts = bench.scaleup_workloads(int(qp))
+        assert dd.P1 * dd.P2 * dd.Q == int(qp) and one.P1 * one.P2 * one.Q == 1
+        assert (dd.nlon, dd.nlat) == (one.nlon, one.nlat)
+        dec = oracle.Decomposition.make(dd.nlon, dd.nlat, dd.nsteps, dd.P1, dd.P2, dd.Q, lon_cuts, lat_cuts,
+                                        [0, dd.nsteps], dd.o_lon, dd.o_lat, dd.o_t)
+        assert {(s.nx, s.ny) for s in dec.subs} == {(32, 32)}
+        size = sum(3 * s.nx * s.ny for s in dec.subs)
+        assert size == 3 * 32 * 32 * int(qp)
+        assert abs(size - printed) <= 0.05 * printed
