@@ -616,31 +616,209 @@ __device__ __forceinline__ bool setup_geo(const SweepArgs<T>& a, cg::cluster_gro
   return true;
 }
 
-// One RK3 stage on own rows: out = cx X + cy (Y + dt F(Y)).  One point per
-// thread per iteration (pairing points per thread for instruction-level
-// parallelism measured slower on GB300: it doubles register pressure).
+// One RK3 stage at own point (rr, k): out = cx X + cy (Y + dt F(Y)); the
+// three new values are also returned.
+template <typename T, bool DEV>
+__device__ __forceinline__ void stage_point(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs,
+                                            T* out, const T* X, const T* Y, T cx, T cy, int rr, int k,
+                                            T& o0, T& o1, T& o2) {
+  const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
+  const int P = g.P;
+  const int o = (rr + 1) * g.W + k + 1;
+  const int ri = rr + 1;
+  T Fh, Fu, Fv;
+  rhs_pt<T, DEV>(Y, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.BinvC[ri], rs.gA[ri], rs.c[ri + 1],
+                 rs.c[ri - 1], Bth, gBth, href, Fh, Fu, Fv);
+  if (cx == (T)0) {
+    o0 = cy * (Y[o] + dt * Fh);
+    o1 = cy * (Y[o + P] + dt * Fu);
+    o2 = cy * (Y[o + 2 * P] + dt * Fv);
+  } else {
+    o0 = cx * X[o] + cy * (Y[o] + dt * Fh);
+    o1 = cx * X[o + P] + cy * (Y[o + P] + dt * Fu);
+    o2 = cx * X[o + 2 * P] + cy * (Y[o + 2 * P] + dt * Fv);
+  }
+  out[o] = o0;
+  out[o + P] = o1;
+  out[o + 2 * P] = o2;
+}
+
+// One RK3 stage on own rows (halos completed afterwards by complete_buf).
+// One point per thread per iteration (pairing points per thread for
+// instruction-level parallelism measured slower on GB300: it doubles
+// register pressure).
 template <typename T, bool DEV>
 __device__ void stage(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs, T* out,
                       const T* X, const T* Y, T cx, T cy) {
-  const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
-  const int P = g.P;
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
     const int rr = idx / g.nx, k = idx - rr * g.nx;
-    const int o = (rr + 1) * g.W + k + 1;
-    const int ri = rr + 1;
-    T Fh, Fu, Fv;
-    rhs_pt<T, DEV>(Y, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.BinvC[ri], rs.gA[ri],
-                   rs.c[ri + 1], rs.c[ri - 1], Bth, gBth, href, Fh, Fu, Fv);
-    if (cx == (T)0) {
-      out[o] = cy * (Y[o] + dt * Fh);
-      out[o + P] = cy * (Y[o + P] + dt * Fu);
-      out[o + 2 * P] = cy * (Y[o + 2 * P] + dt * Fv);
-    } else {
-      out[o] = cx * X[o] + cy * (Y[o] + dt * Fh);
-      out[o + P] = cx * X[o + P] + cy * (Y[o + P] + dt * Fu);
-      out[o + 2 * P] = cx * X[o + 2 * P] + cy * (Y[o + 2 * P] + dt * Fv);
+    T o0, o1, o2;
+    stage_point<T, DEV>(a, g, rs, out, X, Y, cx, cy, rr, k, o0, o1, o2);
+  }
+}
+
+// ---- pushed halo exchange -------------------------------------------------
+// A phase that computes the own rows of buffer X can publish its halo data
+// itself instead of having complete_buf pull it after a barrier:
+//   1. fixed ghosts of X that do not depend on this phase (frozen boundary
+//      values, zeros);
+//   2. the edge rows 0 and Rn-1, each value also stored into the neighbour
+//      CTA's halo row (distributed shared memory), into the wall mirror row,
+//      or into the periodic ghost column;
+//   3. cluster barrier arrive (release);
+//   4. the interior rows, while the barrier completes;
+//   5. CTA barrier, then cluster barrier wait (acquire).
+// Ordering: a neighbour passes its wait only after this CTA's arrive, so it
+// can be at most one phase ahead of this CTA's interior rows.  The buffer it
+// then writes into is the next phase's output, whose halo rows no interior
+// row of the current phase reads.  Halo rows of X are read only by edge
+// rows, before the arrive.
+
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// Step 1: box-edge halo rows without a neighbour CTA or a mirror, and
+// ghost columns of a box that is not periodic.
+template <typename T>
+__device__ void fill_fixed(const SweepArgs<T>& a, const Geo<T>& g, T* X, int kind, int nA, int nB, T wA,
+                           T wB) {
+  const int nx = g.nx;
+  const bool s_fixed = g.rank == 0 && (!(g.flags & F_SWALL) || kind == K_ADJ);
+  const bool n_fixed = g.rank == g.CL - 1 && (!(g.flags & F_NWALL) || kind == K_ADJ);
+  if (s_fixed || n_fixed) {
+    for (int idx = threadIdx.x; idx < 2 * 3 * nx; idx += blockDim.x) {
+      const int side = idx / (3 * nx);
+      if (side == 0 ? !s_fixed : !n_fixed) continue;
+      const int rem = idx - side * 3 * nx;
+      const int v = rem / nx, k = rem - v * nx;
+      const bool wall = (side == 0) ? (g.flags & F_SWALL) : (g.flags & F_NWALL);
+      X[off(g, v, side == 0 ? -1 : g.Rn, k)] =
+          (kind == K_STATE && !wall) ? gh_row(a, g, nA, nB, wA, wB, side, v, k) : (T)0;
     }
   }
+  if (!(g.flags & F_PERIODIC)) {
+    for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
+      const int side = idx / (3 * g.Rn);
+      const int rem = idx - side * 3 * g.Rn;
+      const int v = rem / g.Rn, rr = rem - v * g.Rn;
+      X[off(g, v, rr, side == 0 ? -1 : nx)] = (kind == K_STATE) ? gh_col(a, g, nA, nB, wA, wB, side, v, rr) : (T)0;
+    }
+  }
+}
+
+// Step 2 for one point: its values (v0, v1, v2) go to the halo data that
+// depends on them.
+template <typename T>
+__device__ __forceinline__ void publish(const Geo<T>& g, T* X, T* snb, T* nnb, int kind, int rr, int k, T v0,
+                                        T v1, T v2) {
+  if (rr == 0) {
+    if (snb) {
+      snb[off(g, 0, g.Rprev, k)] = v0;
+      snb[off(g, 1, g.Rprev, k)] = v1;
+      snb[off(g, 2, g.Rprev, k)] = v2;
+    } else if ((g.flags & F_SWALL) && kind != K_ADJ) {
+      X[off(g, 0, -1, k)] = v0;
+      X[off(g, 1, -1, k)] = v1;
+      X[off(g, 2, -1, k)] = -v2;
+    }
+  }
+  if (rr == g.Rn - 1) {
+    if (nnb) {
+      nnb[off(g, 0, -1, k)] = v0;
+      nnb[off(g, 1, -1, k)] = v1;
+      nnb[off(g, 2, -1, k)] = v2;
+    } else if ((g.flags & F_NWALL) && kind != K_ADJ) {
+      X[off(g, 0, g.Rn, k)] = v0;
+      X[off(g, 1, g.Rn, k)] = v1;
+      X[off(g, 2, g.Rn, k)] = -v2;
+    }
+  }
+  if (g.flags & F_PERIODIC) {
+    if (k == 0) {
+      X[off(g, 0, rr, g.nx)] = v0;
+      X[off(g, 1, rr, g.nx)] = v1;
+      X[off(g, 2, rr, g.nx)] = v2;
+    }
+    if (k == g.nx - 1) {
+      X[off(g, 0, rr, -1)] = v0;
+      X[off(g, 1, rr, -1)] = v1;
+      X[off(g, 2, rr, -1)] = v2;
+    }
+  }
+}
+
+// Steps 1-5 with fn(rr, k, v0, v1, v2) computing and storing point (rr, k)
+// of X and returning its values.
+template <typename T, typename Fn>
+__device__ void phase_push(cg::cluster_group& cl, const SweepArgs<T>& a, const Geo<T>& g, T* X, int kind,
+                           int nA, int nB, T wA, T wB, Fn&& fn) {
+  fill_fixed(a, g, X, kind, nA, nB, wA, wB);
+  T* snb = g.rank > 0 ? cl.map_shared_rank(X, g.rank - 1) : nullptr;
+  T* nnb = g.rank < g.CL - 1 ? cl.map_shared_rank(X, g.rank + 1) : nullptr;
+  const int nx = g.nx;
+  const int ne = (g.Rn > 1 ? 2 : 1) * nx;
+  for (int idx = threadIdx.x; idx < ne; idx += blockDim.x) {
+    const int rr = idx < nx ? 0 : g.Rn - 1;
+    const int k = idx < nx ? idx : idx - nx;
+    T v0, v1, v2;
+    fn(rr, k, v0, v1, v2);
+    publish(g, X, snb, nnb, kind, rr, k, v0, v1, v2);
+  }
+  cluster_arrive_release();
+  const int ni = (g.Rn > 2 ? g.Rn - 2 : 0) * nx;
+  for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
+    const int rr = 1 + idx / nx, k = idx - (rr - 1) * nx;
+    T v0, v1, v2;
+    fn(rr, k, v0, v1, v2);
+    if ((g.flags & F_PERIODIC) && (k == 0 || k == nx - 1)) publish(g, X, snb, nnb, kind, rr, k, v0, v1, v2);
+  }
+  if constexpr (sizeof(T) == 4) cp_async_wait_all();   // this thread's ghost copies land first
+  __syncthreads();
+  cluster_wait_acquire();
+}
+
+// RK3 stage with pushed halo exchange (replaces stage + complete_buf).
+template <typename T, bool DEV>
+__device__ __forceinline__ void stage_push(cg::cluster_group& cl, const SweepArgs<T>& a, const Geo<T>& g,
+                                           const RowSmem<T>& rs, T* out, const T* X, const T* Y, T cx, T cy,
+                                           int nA, int nB, T wA, T wB) {
+  phase_push(cl, a, g, out, K_STATE, nA, nB, wA, wB, [&](int rr, int k, T& v0, T& v1, T& v2) {
+    stage_point<T, DEV>(a, g, rs, out, X, Y, cx, cy, rr, k, v0, v1, v2);
+  });
+}
+
+// Halo data of a buffer whose own rows are final (after forcing terms were
+// added): fixed ghosts, edge rows pushed, periodic ghosts, full cluster
+// barrier.
+template <typename T>
+__device__ void push_halos(cg::cluster_group& cl, const SweepArgs<T>& a, const Geo<T>& g, T* X, int kind) {
+  fill_fixed(a, g, X, kind, 0, 0, (T)1, (T)0);
+  T* snb = g.rank > 0 ? cl.map_shared_rank(X, g.rank - 1) : nullptr;
+  T* nnb = g.rank < g.CL - 1 ? cl.map_shared_rank(X, g.rank + 1) : nullptr;
+  const int nx = g.nx;
+  const bool periodic = g.flags & F_PERIODIC;
+  // edge rows (all columns), plus the two end columns of every row when periodic
+  const int ne = (g.Rn > 1 ? 2 : 1) * nx;
+  const int nper = periodic ? 2 * g.Rn : 0;
+  for (int idx = threadIdx.x; idx < ne + nper; idx += blockDim.x) {
+    int rr, k;
+    if (idx < ne) {
+      rr = idx < nx ? 0 : g.Rn - 1;
+      k = idx < nx ? idx : idx - nx;
+    } else {
+      const int j = idx - ne;
+      rr = j >> 1;
+      k = (j & 1) ? nx - 1 : 0;
+      if (rr == 0 || rr == g.Rn - 1) continue;   // done with the edge rows
+    }
+    publish(g, X, snb, nnb, kind, rr, k, X[off(g, 0, rr, k)], X[off(g, 1, rr, k)], X[off(g, 2, rr, k)]);
+  }
+  if constexpr (sizeof(T) == 4) cp_async_wait_all();
+  cl.sync();
 }
 
 template <typename T>
@@ -727,15 +905,12 @@ __global__ void __launch_bounds__(512, 2) fwd_kernel(SweepArgs<T> a) {
   for (int l = 0; l < g.L; ++l) {
     const int n = g.a + l;
     if (n + 2 <= g.d.b) ghost_prefetch(a, g, n + 2);   // used by the next step
-    stage<T, DEV>(a, g, rs, S1, X, X, (T)0, (T)1);
-    complete_buf(cl, a, g, S1, K_STATE, n + 1, n + 1, (T)1, (T)0);
+    stage_push<T, DEV>(cl, a, g, rs, S1, X, X, (T)0, (T)1, n + 1, n + 1, (T)1, (T)0);
     // stores read the buffer with another thread mapping: after the barrier
     if (a.stg) store_block(g, S1, stage_ptr(a, g, l, 0));
-    stage<T, DEV>(a, g, rs, S2, X, S1, (T)0.75, (T)0.25);
-    complete_buf(cl, a, g, S2, K_STATE, n, n + 1, (T)0.5, (T)0.5);
+    stage_push<T, DEV>(cl, a, g, rs, S2, X, S1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5);
     if (a.stg) store_block(g, S2, stage_ptr(a, g, l, 1));
-    stage<T, DEV>(a, g, rs, X, X, S2, (T)(1.0 / 3.0), (T)(2.0 / 3.0));
-    complete_buf(cl, a, g, X, K_STATE, n + 1, n + 1, (T)1, (T)0);
+    stage_push<T, DEV>(cl, a, g, rs, X, X, S2, (T)(1.0 / 3.0), (T)(2.0 / 3.0), n + 1, n + 1, (T)1, (T)0);
     if (a.ckpt == 0 || (l + 1) % a.ckpt == 0) store_level(a, g, X, l + 1);
     obs_level(a, g, X, l + 1, Jo);
     overlap_level(a, g, X, l + 1, Jm);
@@ -889,39 +1064,39 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       load_states3(a, g, bufs, srcs, nA, nB, wA, wB);
     } else {       // recompute the stage states from x(n)
       load_state(a, g, X, level_src(l), n, n, (T)1, (T)0);
-      stage<T, DEV>(a, g, rs, X1, X, X, (T)0, (T)1);
-      complete_buf(cl, a, g, X1, K_STATE, n + 1, n + 1, (T)1, (T)0);
-      stage<T, DEV>(a, g, rs, X2, X, X1, (T)0.75, (T)0.25);
-      complete_buf(cl, a, g, X2, K_STATE, n, n + 1, (T)0.5, (T)0.5);
+      stage_push<T, DEV>(cl, a, g, rs, X1, X, X, (T)0, (T)1, n + 1, n + 1, (T)1, (T)0);
+      stage_push<T, DEV>(cl, a, g, rs, X2, X, X1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5);
     }
     const int P = g.P;
     // lambda_x2 = 2/3 lambda' + 2/3 dt F'(x2)^T lambda'
-    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-      const int rr = idx / g.nx, k = idx - rr * g.nx;
+    phase_push(cl, a, g, L2, K_ADJ, 0, 0, (T)1, (T)0, [&](int rr, int k, T& v0, T& v1, T& v2) {
       const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
       rhs_adj_pt<T, DEV>(X2, Lp, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
                          rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
-      L2[o] = c23 * (Lp[o] + dt * Gh);
-      L2[o + P] = c23 * (Lp[o + P] + dt * Gu);
-      L2[o + 2 * P] = c23 * (Lp[o + 2 * P] + dt * Gv);
-    }
-    complete_buf(cl, a, g, L2, K_ADJ, 0, 0, (T)1, (T)0);
+      v0 = c23 * (Lp[o] + dt * Gh);
+      v1 = c23 * (Lp[o + P] + dt * Gu);
+      v2 = c23 * (Lp[o + 2 * P] + dt * Gv);
+      L2[o] = v0;
+      L2[o + P] = v1;
+      L2[o + 2 * P] = v2;
+    });
     // lambda_x1 = 1/4 lambda_x2 + 1/4 dt F'(x1)^T lambda_x2   (into X2's buffer)
     T* L1 = X2;
-    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-      const int rr = idx / g.nx, k = idx - rr * g.nx;
+    phase_push(cl, a, g, L1, K_ADJ, 0, 0, (T)1, (T)0, [&](int rr, int k, T& v0, T& v1, T& v2) {
       const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
       rhs_adj_pt<T, DEV>(X1, L2, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
                          rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
-      L1[o] = (T)0.25 * (L2[o] + dt * Gh);
-      L1[o + P] = (T)0.25 * (L2[o + P] + dt * Gu);
-      L1[o + 2 * P] = (T)0.25 * (L2[o + 2 * P] + dt * Gv);
-    }
-    complete_buf(cl, a, g, L1, K_ADJ, 0, 0, (T)1, (T)0);
+      v0 = (T)0.25 * (L2[o] + dt * Gh);
+      v1 = (T)0.25 * (L2[o + P] + dt * Gu);
+      v2 = (T)0.25 * (L2[o + 2 * P] + dt * Gv);
+      L1[o] = v0;
+      L1[o + P] = v1;
+      L1[o + 2 * P] = v2;
+    });
     // lambda(n) = 1/3 lambda' + 3/4 lambda_x2 + lambda_x1 + dt F'(x)^T lambda_x1
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
       const int rr = idx / g.nx, k = idx - rr * g.nx;
@@ -936,7 +1111,7 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
     }
     __syncthreads();
     add_forcing(a, g, Lp, X, l);
-    complete_buf(cl, a, g, Lp, K_ADJ, 0, 0, (T)1, (T)0);
+    push_halos(cl, a, g, Lp, K_ADJ);
   }
   }
   // lambda(a) -> packed control layout (FP64)
