@@ -139,3 +139,26 @@ def test_large_workload_fits_and_satisfies_properties_at_full_size():
     finally:
         ctx.destroy()
         torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("name,precision,ckpt_k,tol,samples", [
+    ("medium", 0, 0, 1e-9, (5, 42)),
+    ("differentiation", 1, 16, 2e-3, (45,)),
+])
+def test_gauss_newton_product_sampled_at_full_size(name, precision, ckpt_k, tol, samples):
+    """Gauss-Newton products (I + G^T G) p at the workload's full size, in the
+    autotuned launch configuration, on sampled subdomains against the
+    oracle's forward-then-reverse-mode product."""
+    wl = workloads.preset(name)
+    st, inp, _ = oracle.build_setup(wl)
+    ob = st.obs
+    ctx = _lib_ctx(wl, inp, ob.value, ob.sigma_o, precision, ckpt_k=ckpt_k)
+    w = np.concatenate([rand_w(lp.nctrl, seed=1100 + s, scale=0.3).numpy() for s, lp in enumerate(st.locals)])
+    p = np.concatenate([rand_w(lp.nctrl, seed=1200 + s).numpy() for s, lp in enumerate(st.locals)])
+    Ap = ctx.gn_hessvec(w, p)
+    prev = st.background_prev()
+    for s in samples:
+        ref = oracle.gn_hessvec(st.locals[s], torch.as_tensor(ctx.split_controls(w)[s]),
+                                torch.as_tensor(ctx.split_controls(p)[s]), st.xb_traj, prev).numpy()
+        assert rel(ctx.split_controls(Ap)[s], ref) <= tol, (s, rel(ctx.split_controls(Ap)[s], ref))
+    ctx.destroy()
