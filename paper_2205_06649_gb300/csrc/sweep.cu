@@ -42,7 +42,24 @@ struct Geo {
   T* gh;              // ghost cache: 3 slots of [6 R columns | 6 W rows] values
   int* gh_tag;        // level held by each slot (-1: none)
   int gh_len;         // values per slot
+  // multipliers for division by nx, Rn, ny and the loaded row count nr
+  // (mdiv below) in the per-point index mappings
+  unsigned mnx, mRn, mny, mnr;
 };
+
+// Division by a per-CTA constant d >= 1 through a precomputed multiplier
+// m = ceil(2^32 / d) (m = 0 encodes d = 1): floor(a / d) = floor(a m / 2^32)
+// exactly whenever a * d < 2^32.  (With m = (2^32 + e) / d, 0 <= e < d, the
+// product is a / d + a e / (d 2^32); the extra term is below 1 / d, the gap
+// from a / d up to the next integer, when a e < 2^32.)  Every dividend here is
+// an index into a CTA's shared-memory stripe, below 2^20, and every divisor
+// is a row length or a row count: a * d stays below 2^31.
+__host__ __device__ __forceinline__ unsigned magic_of(int d) {
+  return d <= 1 ? 0u : (unsigned)(0xFFFFFFFFu / (unsigned)d + 1u);
+}
+__device__ __forceinline__ int mdiv(int a, unsigned m) {
+  return m ? (int)__umulhi((unsigned)a, m) : a;
+}
 
 __device__ __forceinline__ void split_rows(int ny, int CL, int rank, int& R0, int& Rn) {
   const int base = ny / CL, rem = ny % CL;
@@ -126,9 +143,9 @@ __device__ void ghost_prefetch(const SweepArgs<T>& a, const Geo<T>& g, int n) {
   if (!(g.flags & F_PERIODIC)) {
     const int iw = (g.d.i0 - 1 + a.nlon) % a.nlon, ie = (g.d.i0 + g.nx) % a.nlon;
     for (int idx = threadIdx.x; idx < 6 * g.Rn; idx += blockDim.x) {
-      const int side = idx / (3 * g.Rn);
-      const int rem = idx - side * 3 * g.Rn;
-      const int v = rem / g.Rn, rr = rem - v * g.Rn;
+      const int q = mdiv(idx, g.mRn);   // side * 3 + v
+      const int side = q / 3;
+      const int v = q - 3 * side, rr = idx - q * g.Rn;
       const int j = g.d.j0 + g.R0 + rr;
       cp_async_4or8(dst + (side * 3 + v) * R + rr,
                     src + ((size_t)v * a.nlat + j) * a.nlon + (side ? ie : iw), (int)sizeof(T));
@@ -138,10 +155,10 @@ __device__ void ghost_prefetch(const SweepArgs<T>& a, const Geo<T>& g, int n) {
   const bool north = g.rank == g.CL - 1 && !(g.flags & F_NWALL);
   if (south || north) {
     for (int idx = threadIdx.x; idx < 6 * g.nx; idx += blockDim.x) {
-      const int side = idx / (3 * g.nx);
+      const int q = mdiv(idx, g.mnx);   // side * 3 + v
+      const int side = q / 3;
       if ((side == 0 && !south) || (side == 1 && !north)) continue;
-      const int rem = idx - side * 3 * g.nx;
-      const int v = rem / g.nx, k = rem - v * g.nx;
+      const int v = q - 3 * side, k = idx - q * g.nx;
       const int j = side ? g.d.j0 + g.ny : g.d.j0 - 1;
       cp_async_4or8(dst + 6 * R + (side * 3 + v) * g.W + k,
                     src + ((size_t)v * a.nlat + j) * a.nlon + (g.d.i0 + k) % a.nlon, (int)sizeof(T));
@@ -203,10 +220,10 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
   const T* south_nb = (g.rank > 0) ? cl.map_shared_rank(X, g.rank - 1) : nullptr;
   const T* north_nb = (g.rank < g.CL - 1) ? cl.map_shared_rank(X, g.rank + 1) : nullptr;
   for (int idx = threadIdx.x; idx < 2 * 3 * nx; idx += blockDim.x) {
-    const int side = idx / (3 * nx);
-    const int rem = idx - side * 3 * nx;
-    const int v = rem / nx;
-    const int k = rem - v * nx;
+    const int q = mdiv(idx, g.mnx);   // side * 3 + v
+    const int side = q / 3;
+    const int v = q - 3 * side;
+    const int k = idx - q * nx;
     T val;
     if (side == 0) {   // south halo rr = -1
       if (south_nb) {
@@ -235,10 +252,10 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
   }
   // ghost columns of own rows
   for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
-    const int side = idx / (3 * g.Rn);
-    const int rem = idx - side * 3 * g.Rn;
-    const int v = rem / g.Rn;
-    const int rr = rem - v * g.Rn;
+    const int q = mdiv(idx, g.mRn);   // side * 3 + v
+    const int side = q / 3;
+    const int v = q - 3 * side;
+    const int rr = idx - q * g.Rn;
     T val;
     if (periodic) {
       val = side == 0 ? X[off(g, v, rr, nx - 1)] : X[off(g, v, rr, 0)];
@@ -264,10 +281,10 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
   const int r_hi = (g.rank < g.CL - 1) ? g.Rn + 1 : g.Rn;
   const int nr = r_hi - r_lo;
   for (int idx = threadIdx.x; idx < 3 * nr * nx; idx += blockDim.x) {
-    const int v = idx / (nr * nx);
-    const int rem = idx - v * nr * nx;
-    const int rr = rem / nx + r_lo;
-    const int k = rem - (rr - r_lo) * nx;
+    const int q = mdiv(idx, g.mnx);   // v * nr + (rr - r_lo)
+    const int v = mdiv(q, g.mnr);
+    const int rr = q - v * nr + r_lo;
+    const int k = idx - q * nx;
     X[off(g, v, rr, k)] = src[((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k];
   }
   if constexpr (sizeof(T) == 4) cp_async_wait_all();
@@ -275,7 +292,7 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
   const bool periodic = g.flags & F_PERIODIC;
   if (g.rank == 0) {
     for (int idx = threadIdx.x; idx < 3 * nx; idx += blockDim.x) {
-      const int v = idx / nx, k = idx - v * nx;
+      const int v = mdiv(idx, g.mnx), k = idx - v * nx;
       X[off(g, v, -1, k)] = (g.flags & F_SWALL)
                                 ? ((v == 2) ? -X[off(g, v, 0, k)] : X[off(g, v, 0, k)])
                                 : gh_row(a, g, nA, nB, wA, wB, 0, v, k);
@@ -283,7 +300,7 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
   }
   if (g.rank == g.CL - 1) {
     for (int idx = threadIdx.x; idx < 3 * nx; idx += blockDim.x) {
-      const int v = idx / nx, k = idx - v * nx;
+      const int v = mdiv(idx, g.mnx), k = idx - v * nx;
       X[off(g, v, g.Rn, k)] =
           (g.flags & F_NWALL)
               ? ((v == 2) ? -X[off(g, v, g.Rn - 1, k)] : X[off(g, v, g.Rn - 1, k)])
@@ -291,10 +308,10 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
     }
   }
   for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
-    const int side = idx / (3 * g.Rn);
-    const int rem = idx - side * 3 * g.Rn;
-    const int v = rem / g.Rn;
-    const int rr = rem - v * g.Rn;
+    const int q = mdiv(idx, g.mRn);   // side * 3 + v
+    const int side = q / 3;
+    const int v = q - 3 * side;
+    const int rr = idx - q * g.Rn;
     T val;
     if (periodic) {
       val = side == 0 ? X[off(g, v, rr, nx - 1)] : X[off(g, v, rr, 0)];
@@ -317,12 +334,11 @@ __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X
   const int nr = r_hi - r_lo;
   const int per = 3 * nr * nx;
   for (int idx = threadIdx.x; idx < 3 * per; idx += blockDim.x) {
-    const int b = idx / per;
-    const int j = idx - b * per;
-    const int v = j / (nr * nx);
-    const int rem = j - v * nr * nx;
-    const int rr = rem / nx + r_lo;
-    const int k = rem - (rr - r_lo) * nx;
+    const int q = mdiv(idx, g.mnx);   // (b * 3 + v) * nr + (rr - r_lo)
+    const int bv = mdiv(q, g.mnr);
+    const int b = bv / 3, v = bv - 3 * b;
+    const int rr = q - bv * nr + r_lo;
+    const int k = idx - q * nx;
     X[b][off(g, v, rr, k)] = src[b][((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k];
   }
   if constexpr (sizeof(T) == 4) cp_async_wait_all();
@@ -330,14 +346,15 @@ __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X
   const bool periodic = g.flags & F_PERIODIC;
   const int ne = 2 * 3 * nx;      // box-edge halo rows (both sides, all vars)
   const int nc = 2 * 3 * g.Rn;    // ghost columns of own rows
+  const unsigned mb = magic_of(ne + nc);
   for (int idx = threadIdx.x; idx < 3 * (ne + nc); idx += blockDim.x) {
-    const int b = idx / (ne + nc);
+    const int b = mdiv(idx, mb);
     int j = idx - b * (ne + nc);
     T* Y = X[b];
     if (j < ne) {
-      const int side = j / (3 * nx);
-      const int rem = j - side * 3 * nx;
-      const int v = rem / nx, k = rem - v * nx;
+      const int q = mdiv(j, g.mnx);   // side * 3 + v
+      const int side = q / 3;
+      const int v = q - 3 * side, k = j - q * nx;
       if (side == 0 && g.rank == 0) {
         Y[off(g, v, -1, k)] = (g.flags & F_SWALL)
                                   ? ((v == 2) ? -Y[off(g, v, 0, k)] : Y[off(g, v, 0, k)])
@@ -350,10 +367,10 @@ __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X
       }
     } else {
       j -= ne;
-      const int side = j / (3 * g.Rn);
-      const int rem = j - side * 3 * g.Rn;
-      const int v = rem / g.Rn;
-      const int rr = rem - v * g.Rn;
+      const int q = mdiv(j, g.mRn);   // side * 3 + v
+      const int side = q / 3;
+      const int v = q - 3 * side;
+      const int rr = j - q * g.Rn;
       T val;
       if (periodic) {
         val = side == 0 ? Y[off(g, v, rr, nx - 1)] : Y[off(g, v, rr, 0)];
@@ -572,7 +589,7 @@ __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X
   const T i0 = a.isb2_s[0], i1 = a.isb2_s[1], i2 = a.isb2_s[2];
   T part = (T)0;
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-    const int rr = idx / g.nx, k = idx - rr * g.nx;
+    const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
     const int r = g.R0 + rr;
     const int c = overlap_count(g, l, r, k);
     if (c == 0) continue;
@@ -613,6 +630,10 @@ __device__ __forceinline__ bool setup_geo(const SweepArgs<T>& a, cg::cluster_gro
   g.P = g.R2 * g.W;
   if (g.rank != 0) g.flags &= ~F_SWALL;           // only the edge CTAs see the walls
   if (g.rank != g.CL - 1) g.flags &= ~F_NWALL;
+  g.mnx = magic_of(g.nx);
+  g.mRn = magic_of(g.Rn);
+  g.mny = magic_of(g.ny);
+  g.mnr = magic_of(g.Rn + (g.rank > 0) + (g.rank < g.CL - 1));
   return true;
 }
 
@@ -651,7 +672,7 @@ template <typename T, bool DEV>
 __device__ void stage(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs, T* out,
                       const T* X, const T* Y, T cx, T cy) {
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-    const int rr = idx / g.nx, k = idx - rr * g.nx;
+    const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
     T o0, o1, o2;
     stage_point<T, DEV>(a, g, rs, out, X, Y, cx, cy, rr, k, o0, o1, o2);
   }
@@ -691,10 +712,10 @@ __device__ void fill_fixed(const SweepArgs<T>& a, const Geo<T>& g, T* X, int kin
   const bool n_fixed = g.rank == g.CL - 1 && (!(g.flags & F_NWALL) || kind == K_ADJ);
   if (s_fixed || n_fixed) {
     for (int idx = threadIdx.x; idx < 2 * 3 * nx; idx += blockDim.x) {
-      const int side = idx / (3 * nx);
+      const int q = mdiv(idx, g.mnx);   // side * 3 + v
+      const int side = q / 3;
       if (side == 0 ? !s_fixed : !n_fixed) continue;
-      const int rem = idx - side * 3 * nx;
-      const int v = rem / nx, k = rem - v * nx;
+      const int v = q - 3 * side, k = idx - q * nx;
       const bool wall = (side == 0) ? (g.flags & F_SWALL) : (g.flags & F_NWALL);
       X[off(g, v, side == 0 ? -1 : g.Rn, k)] =
           (kind == K_STATE && !wall) ? gh_row(a, g, nA, nB, wA, wB, side, v, k) : (T)0;
@@ -702,9 +723,9 @@ __device__ void fill_fixed(const SweepArgs<T>& a, const Geo<T>& g, T* X, int kin
   }
   if (!(g.flags & F_PERIODIC)) {
     for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
-      const int side = idx / (3 * g.Rn);
-      const int rem = idx - side * 3 * g.Rn;
-      const int v = rem / g.Rn, rr = rem - v * g.Rn;
+      const int q = mdiv(idx, g.mRn);   // side * 3 + v
+      const int side = q / 3;
+      const int v = q - 3 * side, rr = idx - q * g.Rn;
       X[off(g, v, rr, side == 0 ? -1 : nx)] = (kind == K_STATE) ? gh_col(a, g, nA, nB, wA, wB, side, v, rr) : (T)0;
     }
   }
@@ -771,7 +792,8 @@ __device__ void phase_push(cg::cluster_group& cl, const SweepArgs<T>& a, const G
   cluster_arrive_release();
   const int ni = (g.Rn > 2 ? g.Rn - 2 : 0) * nx;
   for (int idx = threadIdx.x; idx < ni; idx += blockDim.x) {
-    const int rr = 1 + idx / nx, k = idx - (rr - 1) * nx;
+    const int q = mdiv(idx, g.mnx);
+    const int rr = 1 + q, k = idx - q * nx;
     T v0, v1, v2;
     fn(rr, k, v0, v1, v2);
     if ((g.flags & F_PERIODIC) && (k == 0 || k == nx - 1)) publish(g, X, snb, nnb, kind, rr, k, v0, v1, v2);
@@ -824,9 +846,9 @@ __device__ void push_halos(cg::cluster_group& cl, const SweepArgs<T>& a, const G
 template <typename T>
 __device__ void store_block(const Geo<T>& g, const T* X, T* dst) {
   for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
-    const int v = idx / (g.Rn * g.nx);
-    const int rem = idx - v * g.Rn * g.nx;
-    const int rr = rem / g.nx, k = rem - rr * g.nx;
+    const int q = mdiv(idx, g.mnx);   // v * Rn + rr
+    const int v = mdiv(q, g.mRn);
+    const int rr = q - v * g.Rn, k = idx - q * g.nx;
     dst[((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k] = X[off(g, v, rr, k)];
   }
 }
@@ -948,7 +970,7 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
     const T m0 = a.musb2_s[0], m1 = a.musb2_s[1], m2 = a.musb2_s[2];
     const size_t pl = (size_t)g.ny * d.nxp;
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-      const int rr = idx / g.nx, k = idx - rr * g.nx;
+      const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
       const int r = g.R0 + rr;
       const int c = overlap_count(g, l, r, k);
       if (c == 0) continue;
@@ -963,7 +985,7 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
     const T m0 = a.musb2_s[0], m1 = a.musb2_s[1], m2 = a.musb2_s[2];
     const size_t pl = (size_t)g.ny * d.nxp;
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-      const int rr = idx / g.nx, k = idx - rr * g.nx;
+      const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
       const int r = g.R0 + rr;
       const int c = overlap_count(g, l, r, k);
       if (c == 0) continue;
@@ -979,9 +1001,9 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
   const int plane = g.ny * g.nx;
   for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
     const int tg = a.sc_tgt[t];
-    const int v = tg / plane;
-    const int rem = tg - v * plane;
-    const int r = rem / g.nx, k = rem - r * g.nx;
+    const int q = mdiv(tg, g.mnx);   // v * ny + r
+    const int v = mdiv(q, g.mny);
+    const int r = q - v * g.ny, k = tg - q * g.nx;
     const int rr = r - g.R0;
     if (rr < 0 || rr >= g.Rn) continue;
     double acc = 0.0;
@@ -1099,7 +1121,7 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
     });
     // lambda(n) = 1/3 lambda' + 3/4 lambda_x2 + lambda_x1 + dt F'(x)^T lambda_x1
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-      const int rr = idx / g.nx, k = idx - rr * g.nx;
+      const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
       const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
@@ -1117,9 +1139,9 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   // lambda(a) -> packed control layout (FP64)
   double* out = a.lam_a + g.d.ctrl_off;
   for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
-    const int v = idx / (g.Rn * g.nx);
-    const int rem = idx - v * g.Rn * g.nx;
-    const int rr = rem / g.nx, k = rem - rr * g.nx;
+    const int q = mdiv(idx, g.mnx);   // v * Rn + rr
+    const int v = mdiv(q, g.mRn);
+    const int rr = q - v * g.Rn, k = idx - q * g.nx;
     out[((size_t)v * g.ny + g.R0 + rr) * g.nx + k] = (double)Lp[off(g, v, rr, k)];
   }
   cl.sync();
@@ -1137,10 +1159,10 @@ __device__ void load_delta0(const SweepArgs<T>& a, const Geo<T>& g, T* D) {
   for (int i = threadIdx.x; i < 3 * g.P; i += blockDim.x) D[i] = (T)0;
   __syncthreads();
   for (int idx = threadIdx.x; idx < 3 * nr * g.nx; idx += blockDim.x) {
-    const int v = idx / (nr * g.nx);
-    const int rem = idx - v * nr * g.nx;
-    const int rr = rem / g.nx + r_lo;
-    const int k = rem - (rr - r_lo) * g.nx;
+    const int q = mdiv(idx, g.mnx);   // v * nr + (rr - r_lo)
+    const int v = mdiv(q, g.mnr);
+    const int rr = q - v * nr + r_lo;
+    const int k = idx - q * g.nx;
     D[off(g, v, rr, k)] = (T)src[((size_t)v * g.ny + g.R0 + rr) * g.nx + k];
   }
   __syncthreads();
@@ -1167,9 +1189,9 @@ template <typename T>
 __device__ void store_delta(const SweepArgs<T>& a, const Geo<T>& g, const T* D, int l) {
   double* dst = a.dx_out + g.d.ptraj_off + (size_t)l * 3 * g.ny * g.nx;
   for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
-    const int v = idx / (g.Rn * g.nx);
-    const int rem = idx - v * g.Rn * g.nx;
-    const int rr = rem / g.nx, k = rem - rr * g.nx;
+    const int q = mdiv(idx, g.mnx);   // v * Rn + rr
+    const int v = mdiv(q, g.mRn);
+    const int rr = q - v * g.Rn, k = idx - q * g.nx;
     dst[((size_t)v * g.ny + g.R0 + rr) * g.nx + k] = (double)D[off(g, v, rr, k)];
   }
 }
@@ -1179,7 +1201,7 @@ __device__ void stage_tl(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T
                          const T* DX, const T* Y, const T* DY, T cx, T cy) {
   const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-    const int rr = idx / g.nx, k = idx - rr * g.nx;
+    const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
     const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
     T Fh, Fu, Fv;
     rhs_tl_pt<T, DEV>(Y, DY, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.BinvC[ri], rs.gA[ri],
