@@ -574,6 +574,54 @@ __device__ void obs_level_lin(const SweepArgs<T>& a, const Geo<T>& g, const T* D
   }
 }
 
+// Calls f(rr, k, c) for every own point (rr, k) of level l with overlap count
+// c > 0, spread over the CTA's threads.  At a level outside the time overlaps
+// only the spatial bands have c > 0: rows r < wS and r >= ny - wN in full,
+// and the columns k < wL and k >= nx - wR of the rows between; those points
+// alone are visited.
+template <typename T, typename F>
+__device__ __forceinline__ void for_overlap_points(const Geo<T>& g, int l, F&& f) {
+  const SubDesc& d = g.d;
+  const int nx = g.nx;
+  const bool any_t = (l < d.tA) || (l > g.L - d.tB);
+  if (any_t || d.wL + d.wR >= nx) {
+    for (int idx = threadIdx.x; idx < g.Rn * nx; idx += blockDim.x) {
+      const int rr = mdiv(idx, g.mnx), k = idx - rr * nx;
+      const int c = overlap_count(g, l, g.R0 + rr, k);
+      if (c) f(rr, k, c);
+    }
+    return;
+  }
+  // own rows [R0, R0 + Rn): full band rows at the low end (A rows) and at the
+  // high end (C rows), the rest (B rows) with wL + wR band columns each
+  const int A = max(0, min(g.Rn, d.wS - g.R0));
+  const int C = max(0, min(g.Rn - A, g.R0 + g.Rn - (g.ny - d.wN)));
+  const int B = g.Rn - A - C;
+  const int wc = d.wL + d.wR;
+  const int nA = A * nx, nC = C * nx, nB = B * wc;
+  const unsigned mwc = magic_of(wc);
+  for (int idx = threadIdx.x; idx < nA + nC + nB; idx += blockDim.x) {
+    int rr, k;
+    if (idx < nA) {
+      rr = mdiv(idx, g.mnx);
+      k = idx - rr * nx;
+    } else if (idx < nA + nC) {
+      const int j = idx - nA;
+      const int q = mdiv(j, g.mnx);
+      rr = g.Rn - C + q;
+      k = j - q * nx;
+    } else {
+      const int j = idx - nA - nC;
+      const int q = mdiv(j, mwc);
+      const int kk = j - q * wc;
+      rr = A + q;
+      k = kk < d.wL ? kk : nx - d.wR + (kk - d.wL);
+    }
+    const int c = overlap_count(g, l, g.R0 + rr, k);
+    if (c) f(rr, k, c);
+  }
+}
+
 // Overlap penalty at level l over own points: Jm2 += c sum_v (x - m)^2 / sb^2
 // (twice the J_mu contribution; the caller halves the total, which is exact).
 // The differences and this level's partial sum are formed in the state
@@ -587,19 +635,15 @@ __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X
   if (!any_t && !any_s) return;
   const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
   const T i0 = a.isb2_s[0], i1 = a.isb2_s[1], i2 = a.isb2_s[2];
+  const size_t pl = (size_t)g.ny * d.nxp;
   T part = (T)0;
-  for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-    const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
-    const int r = g.R0 + rr;
-    const int c = overlap_count(g, l, r, k);
-    if (c == 0) continue;
-    const size_t go = (size_t)r * d.nxp + k;
-    const size_t pl = (size_t)g.ny * d.nxp;
+  for_overlap_points(g, l, [&](int rr, int k, int c) {
+    const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
     const T e0 = X[off(g, 0, rr, k)] - tg[go];
     const T e1 = X[off(g, 1, rr, k)] - tg[go + pl];
     const T e2 = X[off(g, 2, rr, k)] - tg[go + 2 * pl];
     part += (T)c * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
-  }
+  });
   Jm += (double)part;
 }
 
@@ -969,32 +1013,24 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
     const T* dx = a.gn_dx + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
     const T m0 = a.musb2_s[0], m1 = a.musb2_s[1], m2 = a.musb2_s[2];
     const size_t pl = (size_t)g.ny * d.nxp;
-    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-      const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
-      const int r = g.R0 + rr;
-      const int c = overlap_count(g, l, r, k);
-      if (c == 0) continue;
-      const size_t go = (size_t)r * d.nxp + k;
+    for_overlap_points(g, l, [&](int rr, int k, int c) {
+      const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
       const T cc = (T)c;
       Lb[off(g, 0, rr, k)] += cc * m0 * dx[go];
       Lb[off(g, 1, rr, k)] += cc * m1 * dx[go + pl];
       Lb[off(g, 2, rr, k)] += cc * m2 * dx[go + 2 * pl];
-    }
+    });
   } else if ((any_t || any_s) && a.mu != 0.0) {
     const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
     const T m0 = a.musb2_s[0], m1 = a.musb2_s[1], m2 = a.musb2_s[2];
     const size_t pl = (size_t)g.ny * d.nxp;
-    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-      const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
-      const int r = g.R0 + rr;
-      const int c = overlap_count(g, l, r, k);
-      if (c == 0) continue;
-      const size_t go = (size_t)r * d.nxp + k;
+    for_overlap_points(g, l, [&](int rr, int k, int c) {
+      const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
       const T cc = (T)c;
       Lb[off(g, 0, rr, k)] += cc * m0 * (X[off(g, 0, rr, k)] - tg[go]);
       Lb[off(g, 1, rr, k)] += cc * m1 * (X[off(g, 1, rr, k)] - tg[go + pl]);
       Lb[off(g, 2, rr, k)] += cc * m2 * (X[off(g, 2, rr, k)] - tg[go + 2 * pl]);
-    }
+    });
   }
   __syncthreads();
   const int t0 = a.lvl_sc[d.sc_lvl + l], t1 = a.lvl_sc[d.sc_lvl + l + 1];
