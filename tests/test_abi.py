@@ -71,3 +71,18 @@ def test_create_rejects_bad_model_without_touching_the_gpu(lib):
     with pytest.raises(dd.DD4DVError) as e:
         dd.Context(2, 1, 10.0, 4)
     assert e.value.status == -1
+
+
+def test_package_refuses_to_import_without_the_library(tmp_path):
+    """There is no CPU fallback: a copy of the package without the built
+    library raises ImportError at import."""
+    import shutil
+    import subprocess
+    import sys
+    src = os.path.join(ROOT, "paper_2205_06649_gb300")
+    dst = tmp_path / "paper_2205_06649_gb300"
+    shutil.copytree(src, dst, ignore=shutil.ignore_patterns("*.so", "csrc", "__pycache__"))
+    r = subprocess.run([sys.executable, "-c", "import paper_2205_06649_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "libdd4dvar.so" in r.stderr
