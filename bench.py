@@ -392,6 +392,42 @@ def scaleup_mode(args, torch):
     return 0
 
 
+def tta_mode(args, torch):
+    """Time to analysis on one workload: the full outer loop (Algorithm 1)
+    with the FP64 path and with the FP32-state path from the same start,
+    analysis RMSE(h) at t0 after each outer iteration, and the time each path
+    needs to reach 1.01 x the FP64 path's final RMSE."""
+    wl = workloads.preset(args.workload)
+    inp = workloads.generate(wl)
+    solver = solver_for(wl)
+    hist = {}
+    shapes = {}
+    for prec, shape in ((0, args.shape), (1, args.shape32)):
+        stream = torch.cuda.Stream()
+        ctx, _, truth, _ = build_problem(wl, prec, stream.cuda_stream, inputs=inp, shape=shape)
+        zeros = torch.zeros(ctx.ctrl_total, dtype=torch.float64, device="cuda")
+        hist[prec] = time_to_analysis(ctx, solver, truth[0], args.outer, torch, stream, zeros)
+        shapes[prec] = ctx.sweep_config()
+        log(f"precision {prec}: " + " ".join(f"{t:.2f}s:{r:.4f}" for t, r, _ in hist[prec]))
+        ctx.destroy()
+        del zeros
+        torch.cuda.empty_cache()
+    target = 1.01 * hist[0][-1][1]
+    t64 = next(t for t, r, _ in hist[0] if r <= target)
+    t32 = next((t for t, r, _ in hist[1] if r <= target), None)
+    print(json.dumps({
+        "metric": "time to analysis at fixed RMSE, FP32-state path vs FP64 path", "unit": "s",
+        "higher_is_better": False, "n_gpus": 1, "dtype": "f64 and f32 state", "data": "synthetic",
+        "config": {"workload": wl_desc(wl), "outer_iterations": args.outer,
+                   "local_solver": "L-BFGS m=%d, %d iterations" % (wl.lbfgs_m, wl.local_iters),
+                   "sweep_launch": {"fp64": shapes[0], "fp32": shapes[1]}},
+        "rmse_h_background": rmse_h(inp["x_b0"], inp["x_t0"]),
+        "history_fp64": [[t, r] for t, r, _ in hist[0]], "history_fp32": [[t, r] for t, r, _ in hist[1]],
+        "target_rmse_h": target, "fp64_s": t64, "fp32_s": t32,
+        "speedup": (t64 / t32) if t32 else None}), flush=True)
+    return 0
+
+
 def wl_desc(wl):
     return (f"{wl.name}: {wl.nlon}x{wl.nlat} grid, {wl.nsteps} steps, {wl.P1}x{wl.P2}x{wl.Q} "
             f"subdomains ({'uneven' if wl.uneven else 'equal'}), overlap {wl.o_lon} pts / {wl.o_t} steps, "
@@ -411,11 +447,14 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip FP32 and time-to-analysis legs")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="only run this many evaluations (for an ncu launch list) and exit")
-    ap.add_argument("--mode", default="outer", choices=["outer", "eval", "scaleup"],
+    ap.add_argument("--mode", default="outer", choices=["outer", "eval", "scaleup", "tta"],
                     help="outer: a step is one outer iteration (default); eval: a step is one batched "
                          "J and grad J evaluation of all subdomains (for workloads too large for the "
                          "outer-iteration bench); scaleup: the weak-scaling experiment of Table 3 "
-                         "(measured scale-up of one outer iteration, QP = 2..64)")
+                         "(measured scale-up of one outer iteration, QP = 2..64); tta: time to analysis "
+                         "of the FP64 and FP32-state paths over --outer outer iterations")
+    ap.add_argument("--outer", type=int, default=10, help="outer iterations of --mode tta")
+    ap.add_argument("--shape32", default="", help="as --shape, for the FP32-state context of --mode tta")
     ap.add_argument("--ckpt", type=int, default=0, help="ckpt_k of the decomposition (0, -1 or k > 0)")
     ap.add_argument("--shape", default="",
                     help="fwd_cluster,fwd_threads,adj_cluster,adj_threads,stored_stages: force the "
@@ -439,6 +478,8 @@ def main():
 
     if args.mode == "scaleup":
         return scaleup_mode(args, torch) if rank == 0 else 0
+    if args.mode == "tta":
+        return tta_mode(args, torch) if rank == 0 else 0
 
     wl = workloads.preset(args.workload)
     prec = 0 if args.precision == "f64" else 1
