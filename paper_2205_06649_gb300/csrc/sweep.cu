@@ -72,26 +72,62 @@ __device__ __forceinline__ int off(const Geo<T>& g, int v, int rr, int k) {
   return (v * g.R2 + rr + 1) * g.W + k + 1;
 }
 
-// Per-row constants staged in shared memory for rows rr = -1 .. Rn (index rr+1).
+// Per-row constants staged in shared memory for rows rr = -1 .. Rn (index
+// i = rr + 1), as two 8-value records per row so that a point reads its row's
+// constants with two (FP32) or four (FP64) 16-byte loads:
+//   fw[8 i ..]: A, f, tau, B/c, g A, c of row i+1, c of row i-1, 0
+//               (tendencies and tangent-linear tendencies)
+//   bw[8 i ..]: A, f, tau, g A, B c, 1/c of row i+1, 1/c of row i-1, 0
+//               (adjoint tendencies)
+// Wall ghost rows take the edge row's cos (mirror).
 template <typename T>
 struct RowSmem {
-  T *A, *f, *tau, *BinvC, *gA, *c, *ic, *BcC;
+  T *fw, *bw;
 };
+
+template <typename T>
+__device__ __forceinline__ void load_rec8(const T* p, T (&r)[8]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 x = *reinterpret_cast<const float4*>(p);
+    const float4 y = *reinterpret_cast<const float4*>(p + 4);
+    r[0] = x.x; r[1] = x.y; r[2] = x.z; r[3] = x.w;
+    r[4] = y.x; r[5] = y.y; r[6] = y.z; r[7] = y.w;
+  } else {
+    for (int q = 0; q < 4; ++q) {
+      const double2 x = *reinterpret_cast<const double2*>(p + 2 * q);
+      r[2 * q] = x.x;
+      r[2 * q + 1] = x.y;
+    }
+  }
+}
 
 template <typename T>
 __device__ void load_rows(const SweepArgs<T>& a, const Geo<T>& g, RowSmem<T>& rs) {
   for (int i = threadIdx.x; i < g.Rn + 2; i += blockDim.x) {
     const int j = g.d.j0 + g.R0 + i - 1;
     const int jc = min(max(j, 0), a.nlat - 1);       // wall ghost rows mirror cos
+    const int jn = min(max(j + 1, 0), a.nlat - 1);
+    const int js = min(max(j - 1, 0), a.nlat - 1);
     const RowConst rc = a.rows[jc];
-    rs.A[i] = (T)rc.A;
-    rs.f[i] = (T)rc.f;
-    rs.tau[i] = (T)rc.tau;
-    rs.BinvC[i] = (T)rc.BinvC;
-    rs.gA[i] = (T)rc.gA;
-    rs.c[i] = (T)rc.c;
-    rs.ic[i] = (T)(1.0 / rc.c);
-    rs.BcC[i] = (T)(a.Bth * rc.c);
+    const double cn = a.rows[jn].c, cs = a.rows[js].c;
+    T* f = rs.fw + 8 * i;
+    f[0] = (T)rc.A;
+    f[1] = (T)rc.f;
+    f[2] = (T)rc.tau;
+    f[3] = (T)rc.BinvC;
+    f[4] = (T)rc.gA;
+    f[5] = (T)cn;
+    f[6] = (T)cs;
+    f[7] = (T)0;
+    T* b = rs.bw + 8 * i;
+    b[0] = (T)rc.A;
+    b[1] = (T)rc.f;
+    b[2] = (T)rc.tau;
+    b[3] = (T)rc.gA;
+    b[4] = (T)(a.Bth * rc.c);
+    b[5] = (T)(1.0 / cn);
+    b[6] = (T)(1.0 / cs);
+    b[7] = (T)0;
   }
 }
 
@@ -692,8 +728,9 @@ __device__ __forceinline__ void stage_point(const SweepArgs<T>& a, const Geo<T>&
   const int o = (rr + 1) * g.W + k + 1;
   const int ri = rr + 1;
   T Fh, Fu, Fv;
-  rhs_pt<T, DEV>(Y, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.BinvC[ri], rs.gA[ri], rs.c[ri + 1],
-                 rs.c[ri - 1], Bth, gBth, href, Fh, Fu, Fv);
+  T rc[8];
+  load_rec8(rs.fw + 8 * ri, rc);
+  rhs_pt<T, DEV>(Y, o, P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, Fh, Fu, Fv);
   if (cx == (T)0) {
     o0 = cy * (Y[o] + dt * Fh);
     o1 = cy * (Y[o + P] + dt * Fu);
@@ -918,15 +955,12 @@ __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs
     p += 3 * g.P;
   }
   const int nr = a.R + 2;
-  rs.A = p; p += nr;
-  rs.f = p; p += nr;
-  rs.tau = p; p += nr;
-  rs.BinvC = p; p += nr;
-  rs.gA = p; p += nr;
-  rs.c = p; p += nr;
-  rs.ic = p; p += nr;
-  rs.BcC = p; p += nr;
   uintptr_t q = reinterpret_cast<uintptr_t>(p);
+  q = (q + 15) & ~uintptr_t(15);   // 16-byte records
+  rs.fw = reinterpret_cast<T*>(q);
+  rs.bw = rs.fw + 8 * nr;
+  p = rs.bw + 8 * nr;
+  q = reinterpret_cast<uintptr_t>(p);
   q = (q + 15) & ~uintptr_t(15);
   *scratch = reinterpret_cast<double*>(q);
   q += 64 * sizeof(double);
@@ -941,7 +975,7 @@ __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs
 
 template <typename T>
 size_t smem_bytes(int nbuf, int R, int W, bool cache) {
-  return (size_t)nbuf * 3 * (R + 2) * W * sizeof(T) + 8 * (size_t)(R + 2) * sizeof(T) + 16 +
+  return (size_t)nbuf * 3 * (R + 2) * W * sizeof(T) + 16 + 16 * (size_t)(R + 2) * sizeof(T) + 16 +
          64 * sizeof(double) + 3 * (size_t)ghost_len<T>(cache, R, W) * sizeof(T) + 3 * sizeof(int) + 16;
 }
 
@@ -1131,8 +1165,10 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
-      rhs_adj_pt<T, DEV>(X2, Lp, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
-                         rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
+      T rc[8];
+      load_rec8(rs.bw + 8 * ri, rc);
+      rhs_adj_pt<T, DEV>(X2, Lp, o, P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth,
+                         href, wall, Gh, Gu, Gv);
       v0 = c23 * (Lp[o] + dt * Gh);
       v1 = c23 * (Lp[o + P] + dt * Gu);
       v2 = c23 * (Lp[o + 2 * P] + dt * Gv);
@@ -1146,8 +1182,10 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
-      rhs_adj_pt<T, DEV>(X1, L2, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
-                         rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
+      T rc[8];
+      load_rec8(rs.bw + 8 * ri, rc);
+      rhs_adj_pt<T, DEV>(X1, L2, o, P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth,
+                         href, wall, Gh, Gu, Gv);
       v0 = (T)0.25 * (L2[o] + dt * Gh);
       v1 = (T)0.25 * (L2[o + P] + dt * Gu);
       v2 = (T)0.25 * (L2[o + 2 * P] + dt * Gv);
@@ -1161,8 +1199,10 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
-      rhs_adj_pt<T, DEV>(X, L1, o, P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.gA[ri],
-                         rs.BcC[ri], rs.ic[ri + 1], rs.ic[ri - 1], Bth, gBth, href, wall, Gh, Gu, Gv);
+      T rc[8];
+      load_rec8(rs.bw + 8 * ri, rc);
+      rhs_adj_pt<T, DEV>(X, L1, o, P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth,
+                         href, wall, Gh, Gu, Gv);
       Lp[o] = c13 * Lp[o] + (T)0.75 * L2[o] + L1[o] + dt * Gh;
       Lp[o + P] = c13 * Lp[o + P] + (T)0.75 * L2[o + P] + L1[o + P] + dt * Gu;
       Lp[o + 2 * P] = c13 * Lp[o + 2 * P] + (T)0.75 * L2[o + 2 * P] + L1[o + 2 * P] + dt * Gv;
@@ -1240,8 +1280,10 @@ __device__ void stage_tl(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T
     const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
     const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
     T Fh, Fu, Fv;
-    rhs_tl_pt<T, DEV>(Y, DY, o, g.P, g.W, rs.A[ri], rs.f[ri], rs.tau[ri], rs.BinvC[ri], rs.gA[ri],
-                      rs.c[ri + 1], rs.c[ri - 1], Bth, gBth, href, Fh, Fu, Fv);
+    T rc[8];
+    load_rec8(rs.fw + 8 * ri, rc);
+    rhs_tl_pt<T, DEV>(Y, DY, o, g.P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, Fh,
+                      Fu, Fv);
     dout[o] = cx * DX[o] + cy * (DY[o] + dt * Fh);
     dout[o + g.P] = cx * DX[o + g.P] + cy * (DY[o + g.P] + dt * Fu);
     dout[o + 2 * g.P] = cx * DX[o + 2 * g.P] + cy * (DY[o + 2 * g.P] + dt * Fv);
