@@ -34,9 +34,26 @@ namespace dd4dv {
 
 namespace {
 
+// Shared-memory layout of one state buffer (R2 = R + 2 rows of W points,
+// including the halo rows and ghost columns):
+//   FP64: three planes [v][R2][W]; plane stride P = R2 W, column stride 1.
+//   FP32: one 16-byte slot (h, u, v, 0) per point, [R2][W][4]; plane stride
+//         P = 1, column stride 4, so a point's three values are one 128-bit
+//         shared-memory access and a 5-point stencil is five of them.
+// The FP64 sweeps are bound by the FP64 pipe, not by instruction issue, so
+// they keep the denser planar layout.
+template <typename T>
+struct Lay {
+  static constexpr bool kVec = sizeof(T) == 4;
+  static constexpr int CS = kVec ? 4 : 1;   // column stride (elements)
+  static constexpr int NS = kVec ? 4 : 3;   // elements per point in a buffer
+};
+
 template <typename T>
 struct Geo {
   int s, rank, CL, R0, Rn, nx, ny, L, a, R2, W, P, flags;
+  int RS;             // row stride (elements) = W * column stride
+  int BUF;            // elements of one state buffer
   int Rprev, Rnext;   // own-row counts of the south / north neighbour CTA
   SubDesc d;
   T* gh;              // ghost cache: 3 slots of [6 R columns | 6 W rows] values
@@ -61,15 +78,58 @@ __device__ __forceinline__ int mdiv(int a, unsigned m) {
   return m ? (int)__umulhi((unsigned)a, m) : a;
 }
 
+// Arithmetic with explicit rounding: the compiler neither contracts nor
+// reorders these, so every inlined copy of the forward step (forward sweep,
+// stage recomputation in the adjoint, checkpoint-segment recomputation,
+// tangent-linear sweep) rounds identically and the copies agree bit for bit.
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float xsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float xfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 __device__ __forceinline__ void split_rows(int ny, int CL, int rank, int& R0, int& Rn) {
   const int base = ny / CL, rem = ny % CL;
   R0 = rank * base + min(rank, rem);
   Rn = base + (rank < rem ? 1 : 0);
 }
 
+// Element index of point (rr, k) (own rows rr = 0 .. Rn-1, halo rows -1 and
+// Rn; columns k = 0 .. nx-1, ghost columns -1 and nx), first variable; the
+// variable v sits at + v P.
+template <typename T>
+__device__ __forceinline__ int pidx(const Geo<T>& g, int rr, int k) {
+  return ((rr + 1) * g.W + k + 1) * Lay<T>::CS;
+}
 template <typename T>
 __device__ __forceinline__ int off(const Geo<T>& g, int v, int rr, int k) {
-  return (v * g.R2 + rr + 1) * g.W + k + 1;
+  return pidx(g, rr, k) + v * g.P;
+}
+
+// The three values (h, u, v) of the point at element index o.
+template <typename T>
+__device__ __forceinline__ void ld3(const T* Z, int o, int P, T& h, T& u, T& v) {
+  if constexpr (Lay<T>::kVec) {
+    const float4 x = *reinterpret_cast<const float4*>(Z + o);
+    h = x.x;
+    u = x.y;
+    v = x.z;
+  } else {
+    h = Z[o];
+    u = Z[o + P];
+    v = Z[o + 2 * P];
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st3(T* Z, int o, int P, T h, T u, T v) {
+  if constexpr (Lay<T>::kVec) {
+    *reinterpret_cast<float4*>(Z + o) = make_float4(h, u, v, 0.0f);
+  } else {
+    Z[o] = h;
+    Z[o + P] = u;
+    Z[o + 2 * P] = v;
+  }
 }
 
 // Per-row constants staged in shared memory for rows rr = -1 .. Rn (index
@@ -144,7 +204,7 @@ __device__ __forceinline__ T bnd_val(const SweepArgs<T>& a, int nA, int nB, T wA
   const T xa = a.bnd[(size_t)nA * 3 * plane + o];
   if (wB == (T)0) return xa;
   const T xb = a.bnd[(size_t)nB * 3 * plane + o];
-  return wA * xa + wB * xb;
+  return xfma(wA, xa, xmul(wB, xb));
 }
 
 // ---- ghost cache --------------------------------------------------------
@@ -219,7 +279,7 @@ __device__ __forceinline__ T gh_col(const SweepArgs<T>& a, const Geo<T>& g, int 
     const int o = (side * 3 + v) * R + rr;
     const T xa = g.gh[(size_t)sA * g.gh_len + o];
     if (wB == (T)0) return xa;
-    return wA * xa + wB * g.gh[(size_t)sB * g.gh_len + o];
+    return xfma(wA, xa, xmul(wB, g.gh[(size_t)sB * g.gh_len + o]));
   }
   const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + g.nx) % a.nlon;
   return bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.R0 + rr, i);
@@ -236,9 +296,51 @@ __device__ __forceinline__ T gh_row(const SweepArgs<T>& a, const Geo<T>& g, int 
     const int o = 6 * R + (side * 3 + v) * g.W + k;
     const T xa = g.gh[(size_t)sA * g.gh_len + o];
     if (wB == (T)0) return xa;
-    return wA * xa + wB * g.gh[(size_t)sB * g.gh_len + o];
+    return xfma(wA, xa, xmul(wB, g.gh[(size_t)sB * g.gh_len + o]));
   }
   return bnd_val(a, nA, nB, wA, wB, v, side ? g.d.j0 + g.ny : g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
+}
+
+// Value of halo row `side` (0 south, 1 north) at column k of a stripe that
+// has no neighbour CTA on that side: the wall mirror (h, u, -v) of the edge
+// row, the frozen boundary trajectory blended between levels nA and nB, or
+// zero (adjoint buffers at walls; adjoint and tangent-linear buffers at frozen
+// edges).
+template <typename T>
+__device__ __forceinline__ void edge_row_val(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int kind,
+                                             int side, int k, int nA, int nB, T wA, T wB, T& h, T& u, T& v) {
+  const bool wall = side ? (g.flags & F_NWALL) : (g.flags & F_SWALL);
+  if (wall) {
+    if (kind == K_ADJ) {
+      h = u = v = (T)0;
+      return;
+    }
+    ld3(X, pidx(g, side ? g.Rn - 1 : 0, k), g.P, h, u, v);
+    v = -v;
+  } else if (kind == K_STATE) {
+    h = gh_row(a, g, nA, nB, wA, wB, side, 0, k);
+    u = gh_row(a, g, nA, nB, wA, wB, side, 1, k);
+    v = gh_row(a, g, nA, nB, wA, wB, side, 2, k);
+  } else {
+    h = u = v = (T)0;
+  }
+}
+
+// Value of ghost column `side` (0 west, 1 east) of own row rr: the periodic
+// wrap, the frozen boundary trajectory, or zero.
+template <typename T>
+__device__ __forceinline__ void ghost_col_val(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int kind,
+                                              int side, int rr, int nA, int nB, T wA, T wB, T& h, T& u,
+                                              T& v) {
+  if (g.flags & F_PERIODIC) {
+    ld3(X, pidx(g, rr, side ? 0 : g.nx - 1), g.P, h, u, v);
+  } else if (kind == K_STATE) {
+    h = gh_col(a, g, nA, nB, wA, wB, side, 0, rr);
+    u = gh_col(a, g, nA, nB, wA, wB, side, 1, rr);
+    v = gh_col(a, g, nA, nB, wA, wB, side, 2, rr);
+  } else {
+    h = u = v = (T)0;
+  }
 }
 
 // Complete a buffer whose own rows were just written by this CTA: cluster
@@ -251,58 +353,53 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
   if constexpr (sizeof(T) == 4) cp_async_wait_all();   // this thread's ghost copies land first
   cl.sync();
   const int nx = g.nx;
-  const bool periodic = g.flags & F_PERIODIC;
-  // halo rows
   const T* south_nb = (g.rank > 0) ? cl.map_shared_rank(X, g.rank - 1) : nullptr;
   const T* north_nb = (g.rank < g.CL - 1) ? cl.map_shared_rank(X, g.rank + 1) : nullptr;
-  for (int idx = threadIdx.x; idx < 2 * 3 * nx; idx += blockDim.x) {
-    const int q = mdiv(idx, g.mnx);   // side * 3 + v
-    const int side = q / 3;
-    const int v = q - 3 * side;
-    const int k = idx - q * nx;
-    T val;
-    if (side == 0) {   // south halo rr = -1
-      if (south_nb) {
-        val = south_nb[off(g, v, g.Rprev - 1, k)];
-      } else if (g.flags & F_SWALL) {
-        val = (kind == K_ADJ) ? (T)0 : ((v == 2) ? -X[off(g, v, 0, k)] : X[off(g, v, 0, k)]);
-      } else {
-        val = (kind == K_STATE)
-                  ? gh_row(a, g, nA, nB, wA, wB, 0, v, k)
-                  : (T)0;
-      }
-      X[off(g, v, -1, k)] = val;
-    } else {           // north halo rr = Rn
-      if (north_nb) {
-        val = north_nb[off(g, v, 0, k)];
-      } else if (g.flags & F_NWALL) {
-        val = (kind == K_ADJ) ? (T)0
-                              : ((v == 2) ? -X[off(g, v, g.Rn - 1, k)] : X[off(g, v, g.Rn - 1, k)]);
-      } else {
-        val = (kind == K_STATE)
-                  ? gh_row(a, g, nA, nB, wA, wB, 1, v, k)
-                  : (T)0;
-      }
-      X[off(g, v, g.Rn, k)] = val;
+  // halo rows
+  for (int idx = threadIdx.x; idx < 2 * nx; idx += blockDim.x) {
+    const int side = idx >= nx ? 1 : 0;
+    const int k = idx - side * nx;
+    const T* nb = side ? north_nb : south_nb;
+    T h, u, v;
+    if (nb) {
+      ld3(nb, pidx(g, side ? 0 : g.Rprev - 1, k), g.P, h, u, v);
+    } else {
+      edge_row_val(a, g, X, kind, side, k, nA, nB, wA, wB, h, u, v);
     }
+    st3(X, pidx(g, side ? g.Rn : -1, k), g.P, h, u, v);
   }
   // ghost columns of own rows
-  for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
-    const int q = mdiv(idx, g.mRn);   // side * 3 + v
-    const int side = q / 3;
-    const int v = q - 3 * side;
-    const int rr = idx - q * g.Rn;
-    T val;
-    if (periodic) {
-      val = side == 0 ? X[off(g, v, rr, nx - 1)] : X[off(g, v, rr, 0)];
-    } else if (kind == K_STATE) {
-      val = gh_col(a, g, nA, nB, wA, wB, side, v, rr);
-    } else {
-      val = (T)0;
-    }
-    X[off(g, v, rr, side == 0 ? -1 : nx)] = val;
+  for (int idx = threadIdx.x; idx < 2 * g.Rn; idx += blockDim.x) {
+    const int side = idx >= g.Rn ? 1 : 0;
+    const int rr = idx - side * g.Rn;
+    T h, u, v;
+    ghost_col_val(a, g, X, kind, side, rr, nA, nB, wA, wB, h, u, v);
+    st3(X, pidx(g, rr, side ? nx : -1), g.P, h, u, v);
   }
   __syncthreads();
+}
+
+// Box-edge halo rows (stripes at the box edges only) and ghost columns of a
+// state buffer X whose own rows are in place; ghosts from the boundary
+// trajectory blended between levels nA and nB.
+template <typename T>
+__device__ __forceinline__ void state_edges(const SweepArgs<T>& a, const Geo<T>& g, T* X, int j, int nA,
+                                            int nB, T wA, T wB) {
+  const int nx = g.nx;
+  T h, u, v;
+  if (j < 2 * nx) {
+    const int side = j >= nx ? 1 : 0;
+    const int k = j - side * nx;
+    if (side ? g.rank != g.CL - 1 : g.rank != 0) return;   // interior halo: loaded
+    edge_row_val(a, g, X, K_STATE, side, k, nA, nB, wA, wB, h, u, v);
+    st3(X, pidx(g, side ? g.Rn : -1, k), g.P, h, u, v);
+  } else {
+    j -= 2 * nx;
+    const int side = j >= g.Rn ? 1 : 0;
+    const int rr = j - side * g.Rn;
+    ghost_col_val(a, g, X, K_STATE, side, rr, nA, nB, wA, wB, h, u, v);
+    st3(X, pidx(g, rr, side ? nx : -1), g.P, h, u, v);
+  }
 }
 
 // Load one stored state (own rows and interior halo rows straight from HBM,
@@ -316,50 +413,20 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
   const int r_lo = (g.rank > 0) ? -1 : 0;
   const int r_hi = (g.rank < g.CL - 1) ? g.Rn + 1 : g.Rn;
   const int nr = r_hi - r_lo;
-  for (int idx = threadIdx.x; idx < 3 * nr * nx; idx += blockDim.x) {
-    const int q = mdiv(idx, g.mnx);   // v * nr + (rr - r_lo)
-    const int v = mdiv(q, g.mnr);
-    const int rr = q - v * nr + r_lo;
-    const int k = idx - q * nx;
-    X[off(g, v, rr, k)] = src[((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k];
+  const size_t pl = (size_t)g.ny * g.d.nxp;
+  for (int idx = threadIdx.x; idx < nr * nx; idx += blockDim.x) {
+    const int q = mdiv(idx, g.mnx);
+    const int rr = q + r_lo, k = idx - q * nx;
+    const T* s = src + (size_t)(g.R0 + rr) * g.d.nxp + k;
+    st3(X, pidx(g, rr, k), g.P, s[0], s[pl], s[2 * pl]);
   }
   if constexpr (sizeof(T) == 4) cp_async_wait_all();
   __syncthreads();
-  const bool periodic = g.flags & F_PERIODIC;
-  if (g.rank == 0) {
-    for (int idx = threadIdx.x; idx < 3 * nx; idx += blockDim.x) {
-      const int v = mdiv(idx, g.mnx), k = idx - v * nx;
-      X[off(g, v, -1, k)] = (g.flags & F_SWALL)
-                                ? ((v == 2) ? -X[off(g, v, 0, k)] : X[off(g, v, 0, k)])
-                                : gh_row(a, g, nA, nB, wA, wB, 0, v, k);
-    }
-  }
-  if (g.rank == g.CL - 1) {
-    for (int idx = threadIdx.x; idx < 3 * nx; idx += blockDim.x) {
-      const int v = mdiv(idx, g.mnx), k = idx - v * nx;
-      X[off(g, v, g.Rn, k)] =
-          (g.flags & F_NWALL)
-              ? ((v == 2) ? -X[off(g, v, g.Rn - 1, k)] : X[off(g, v, g.Rn - 1, k)])
-              : gh_row(a, g, nA, nB, wA, wB, 1, v, k);
-    }
-  }
-  for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
-    const int q = mdiv(idx, g.mRn);   // side * 3 + v
-    const int side = q / 3;
-    const int v = q - 3 * side;
-    const int rr = idx - q * g.Rn;
-    T val;
-    if (periodic) {
-      val = side == 0 ? X[off(g, v, rr, nx - 1)] : X[off(g, v, rr, 0)];
-    } else {
-      val = gh_col(a, g, nA, nB, wA, wB, side, v, rr);
-    }
-    X[off(g, v, rr, side == 0 ? -1 : nx)] = val;
-  }
+  for (int j = threadIdx.x; j < 2 * nx + 2 * g.Rn; j += blockDim.x) state_edges(a, g, X, j, nA, nB, wA, wB);
   __syncthreads();
 }
 
-// Load up to three stored states at once (one pass, one barrier pair) so that
+// Load three stored states at once (one pass, one barrier pair) so that
 // their global-load latencies overlap.  Same rules as load_state.
 template <typename T>
 __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X, const T* const* src,
@@ -368,53 +435,23 @@ __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X
   const int r_lo = (g.rank > 0) ? -1 : 0;
   const int r_hi = (g.rank < g.CL - 1) ? g.Rn + 1 : g.Rn;
   const int nr = r_hi - r_lo;
-  const int per = 3 * nr * nx;
-  for (int idx = threadIdx.x; idx < 3 * per; idx += blockDim.x) {
-    const int q = mdiv(idx, g.mnx);   // (b * 3 + v) * nr + (rr - r_lo)
-    const int bv = mdiv(q, g.mnr);
-    const int b = bv / 3, v = bv - 3 * b;
-    const int rr = q - bv * nr + r_lo;
-    const int k = idx - q * nx;
-    X[b][off(g, v, rr, k)] = src[b][((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k];
+  const size_t pl = (size_t)g.ny * g.d.nxp;
+  for (int idx = threadIdx.x; idx < nr * nx; idx += blockDim.x) {
+    const int q = mdiv(idx, g.mnx);
+    const int rr = q + r_lo, k = idx - q * nx;
+    const size_t go = (size_t)(g.R0 + rr) * g.d.nxp + k;
+    const int o = pidx(g, rr, k);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const T* s = src[b] + go;
+      st3(X[b], o, g.P, s[0], s[pl], s[2 * pl]);
+    }
   }
   if constexpr (sizeof(T) == 4) cp_async_wait_all();
   __syncthreads();
-  const bool periodic = g.flags & F_PERIODIC;
-  const int ne = 2 * 3 * nx;      // box-edge halo rows (both sides, all vars)
-  const int nc = 2 * 3 * g.Rn;    // ghost columns of own rows
-  const unsigned mb = magic_of(ne + nc);
-  for (int idx = threadIdx.x; idx < 3 * (ne + nc); idx += blockDim.x) {
-    const int b = mdiv(idx, mb);
-    int j = idx - b * (ne + nc);
-    T* Y = X[b];
-    if (j < ne) {
-      const int q = mdiv(j, g.mnx);   // side * 3 + v
-      const int side = q / 3;
-      const int v = q - 3 * side, k = j - q * nx;
-      if (side == 0 && g.rank == 0) {
-        Y[off(g, v, -1, k)] = (g.flags & F_SWALL)
-                                  ? ((v == 2) ? -Y[off(g, v, 0, k)] : Y[off(g, v, 0, k)])
-                                  : gh_row(a, g, nA[b], nB[b], wA[b], wB[b], 0, v, k);
-      } else if (side == 1 && g.rank == g.CL - 1) {
-        Y[off(g, v, g.Rn, k)] =
-            (g.flags & F_NWALL)
-                ? ((v == 2) ? -Y[off(g, v, g.Rn - 1, k)] : Y[off(g, v, g.Rn - 1, k)])
-                : gh_row(a, g, nA[b], nB[b], wA[b], wB[b], 1, v, k);
-      }
-    } else {
-      j -= ne;
-      const int q = mdiv(j, g.mRn);   // side * 3 + v
-      const int side = q / 3;
-      const int v = q - 3 * side;
-      const int rr = j - q * g.Rn;
-      T val;
-      if (periodic) {
-        val = side == 0 ? Y[off(g, v, rr, nx - 1)] : Y[off(g, v, rr, 0)];
-      } else {
-        val = gh_col(a, g, nA[b], nB[b], wA[b], wB[b], side, v, rr);
-      }
-      Y[off(g, v, rr, side == 0 ? -1 : nx)] = val;
-    }
+  for (int j = threadIdx.x; j < 2 * nx + 2 * g.Rn; j += blockDim.x) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) state_edges(a, g, X[b], j, nA[b], nB[b], wA[b], wB[b]);
   }
   __syncthreads();
 }
@@ -430,6 +467,21 @@ __device__ __forceinline__ T* stage_ptr(const SweepArgs<T>& a, const Geo<T>& g, 
   return a.stg + g.d.stg_off + ((size_t)l * 2 + which) * 3 * g.ny * g.d.nxp;
 }
 
+// The five stencil points of element index o in a buffer with plane stride
+// P, column stride CS and row stride RS: centre, east, west, north, south.
+template <typename T>
+struct Pt5 {
+  T h, u, v, hE, uE, vE, hW, uW, vW, hN, uN, vN, hS, uS, vS;
+};
+template <typename T>
+__device__ __forceinline__ void load5(const T* Z, int o, int P, int CS, int RS, Pt5<T>& p) {
+  ld3(Z, o, P, p.h, p.u, p.v);
+  ld3(Z, o + CS, P, p.hE, p.uE, p.vE);
+  ld3(Z, o - CS, P, p.hW, p.uW, p.vW);
+  ld3(Z, o + RS, P, p.hN, p.uN, p.vN);
+  ld3(Z, o - RS, P, p.hS, p.uS, p.vS);
+}
+
 // Tendencies F(Z) at one point (Sec. 7, centred differences):
 //   F_u = -A u (uE-uW) - Bth v (uN-uS) + (f + tau u) v - gA (hE-hW)
 //   F_v = -A u (vE-vW) - Bth v (vN-vS) - (f + tau u) u - gBth (hN-hS)
@@ -437,50 +489,41 @@ __device__ __forceinline__ T* stage_ptr(const SweepArgs<T>& a, const Geo<T>& g, 
 // On the FP32 path h = h_ref + h' and the h_ref parts of the fluxes are
 // formed from velocity differences.
 template <typename T, bool DEV>
-__device__ __forceinline__ void rhs_pt(const T* Z, int o, int P, int W, T A, T f, T tau, T BinvC,
-                                       T gA, T cN, T cS, T Bth, T gBth, T href, T& Fh, T& Fu,
-                                       T& Fv) {
-  const T* H = Z;
-  const T* U = Z + P;
-  const T* V = Z + 2 * P;
-  const T u = U[o], v = V[o];
-  const T uE = U[o + 1], uW = U[o - 1], uN = U[o + W], uS = U[o - W];
-  const T vE = V[o + 1], vW = V[o - 1], vN = V[o + W], vS = V[o - W];
-  const T hE = H[o + 1], hW = H[o - 1], hN = H[o + W], hS = H[o - W];
-  const T fu = f + tau * u;
-  Fu = -A * u * (uE - uW) - Bth * v * (uN - uS) + fu * v - gA * (hE - hW);
-  Fv = -A * u * (vE - vW) - Bth * v * (vN - vS) - fu * u - gBth * (hN - hS);
-  T flx = hE * uE - hW * uW;
-  T fly = hN * vN * cN - hS * vS * cS;
+__device__ __forceinline__ void rhs_pt(const Pt5<T>& z, T A, T f, T tau, T BinvC, T gA, T cN, T cS, T Bth,
+                                       T gBth, T href, T& Fh, T& Fu, T& Fv) {
+  const T u = z.u, v = z.v;
+  const T dUx = xsub(z.uE, z.uW), dUy = xsub(z.uN, z.uS);
+  const T dVx = xsub(z.vE, z.vW), dVy = xsub(z.vN, z.vS);
+  const T dHx = xsub(z.hE, z.hW), dHy = xsub(z.hN, z.hS);
+  const T fu = xfma(tau, u, f);
+  const T Au = xmul(A, u), Bv = xmul(Bth, v);
+  Fu = xfma(fu, v, -xfma(Au, dUx, xfma(Bv, dUy, xmul(gA, dHx))));
+  Fv = -xfma(Au, dVx, xfma(Bv, dVy, xfma(fu, u, xmul(gBth, dHy))));
+  T flx = xfma(z.hE, z.uE, -xmul(z.hW, z.uW));
+  T fly = xfma(xmul(z.hN, z.vN), cN, -xmul(xmul(z.hS, z.vS), cS));
   if (DEV) {
-    flx += href * (uE - uW);
-    fly += href * (vN * cN - vS * cS);
+    flx = xfma(href, dUx, flx);
+    fly = xfma(href, xfma(z.vN, cN, -xmul(z.vS, cS)), fly);
   }
-  Fh = -A * flx - BinvC * fly;
+  Fh = -xfma(A, flx, xmul(BinvC, fly));
 }
 
 // Adjoint of the tendencies: G = F'(Z)^T M at one point (derived by hand from
 // rhs_pt; M holds zero at ghost points that carry no tendency).  Wall rows add
 // the transposed ghost mirror (h, u, -v) of the edge row.
 template <typename T, bool DEV>
-__device__ __forceinline__ void rhs_adj_pt(const T* Z, const T* M, int o, int P, int W, T A, T f,
-                                           T tau, T gA, T BcC, T icN, T icS, T Bth, T gBth, T href,
-                                           int wall, T& Gh, T& Gu, T& Gv) {
-  const T* H = Z;
-  const T* U = Z + P;
-  const T* V = Z + 2 * P;
-  const T* mH = M;
-  const T* mU = M + P;
-  const T* mV = M + 2 * P;
-  T h = H[o];
+__device__ __forceinline__ void rhs_adj_pt(const Pt5<T>& z, const Pt5<T>& m, T A, T f, T tau, T gA, T BcC,
+                                           T icN, T icS, T Bth, T gBth, T href, int wall, T& Gh, T& Gu,
+                                           T& Gv) {
+  T h = z.h;
   if (DEV) h += href;
-  const T u = U[o], v = V[o];
-  const T uE = U[o + 1], uW = U[o - 1], uN = U[o + W], uS = U[o - W];
-  const T vE = V[o + 1], vW = V[o - 1], vN = V[o + W], vS = V[o - W];
-  const T mu = mU[o], mv = mV[o], mh = mH[o];
-  const T muE = mU[o + 1], muW = mU[o - 1], muN = mU[o + W], muS = mU[o - W];
-  const T mvE = mV[o + 1], mvW = mV[o - 1], mvN = mV[o + W], mvS = mV[o - W];
-  const T mhE = mH[o + 1], mhW = mH[o - 1], mhN = mH[o + W], mhS = mH[o - W];
+  const T u = z.u, v = z.v;
+  const T uE = z.uE, uW = z.uW, uN = z.uN, uS = z.uS;
+  const T vE = z.vE, vW = z.vW, vN = z.vN, vS = z.vS;
+  const T mu = m.u, mv = m.v, mh = m.h;
+  const T muE = m.uE, muW = m.uW, muN = m.uN, muS = m.uS;
+  const T mvE = m.vE, mvW = m.vW, mvN = m.vN, mvS = m.vS;
+  const T mhE = m.hE, mhW = m.hW, mhN = m.hN, mhS = m.hS;
   const T dmhEW = mhE - mhW;
   const T dmhNS = mhN * icN - mhS * icS;
   Gu = mu * (tau * v - A * (uE - uW)) - mv * (A * (vE - vW) + f + (T)2 * tau * u) +
@@ -501,26 +544,19 @@ __device__ __forceinline__ void rhs_adj_pt(const T* Z, const T* M, int o, int P,
 
 // Tangent-linear tendencies dF = F'(Z) dZ at one point.
 template <typename T, bool DEV>
-__device__ __forceinline__ void rhs_tl_pt(const T* Z, const T* D, int o, int P, int W, T A, T f,
-                                          T tau, T BinvC, T gA, T cN, T cS, T Bth, T gBth, T href,
-                                          T& dFh, T& dFu, T& dFv) {
-  const T* H = Z;
-  const T* U = Z + P;
-  const T* V = Z + 2 * P;
-  const T* dH = D;
-  const T* dU = D + P;
-  const T* dV = D + 2 * P;
-  const T u = U[o], v = V[o];
-  const T du = dU[o], dv = dV[o];
-  const T uE = U[o + 1], uW = U[o - 1], uN = U[o + W], uS = U[o - W];
-  const T vE = V[o + 1], vW = V[o - 1], vN = V[o + W], vS = V[o - W];
-  T hE = H[o + 1], hW = H[o - 1], hN = H[o + W], hS = H[o - W];
+__device__ __forceinline__ void rhs_tl_pt(const Pt5<T>& z, const Pt5<T>& d, T A, T f, T tau, T BinvC, T gA,
+                                          T cN, T cS, T Bth, T gBth, T href, T& dFh, T& dFu, T& dFv) {
+  const T u = z.u, v = z.v;
+  const T du = d.u, dv = d.v;
+  const T uE = z.uE, uW = z.uW, uN = z.uN, uS = z.uS;
+  const T vE = z.vE, vW = z.vW, vN = z.vN, vS = z.vS;
+  T hE = z.hE, hW = z.hW, hN = z.hN, hS = z.hS;
   if (DEV) {
     hE += href; hW += href; hN += href; hS += href;
   }
-  const T duE = dU[o + 1], duW = dU[o - 1], duN = dU[o + W], duS = dU[o - W];
-  const T dvE = dV[o + 1], dvW = dV[o - 1], dvN = dV[o + W], dvS = dV[o - W];
-  const T dhE = dH[o + 1], dhW = dH[o - 1], dhN = dH[o + W], dhS = dH[o - W];
+  const T duE = d.uE, duW = d.uW, duN = d.uN, duS = d.uS;
+  const T dvE = d.vE, dvW = d.vW, dvN = d.vN, dvS = d.vS;
+  const T dhE = d.hE, dhW = d.hW, dhN = d.hN, dhS = d.hS;
   dFu = -A * (du * (uE - uW) + u * (duE - duW)) - Bth * (dv * (uN - uS) + v * (duN - duS)) +
         (f + tau * u) * dv + tau * du * v - gA * (dhE - dhW);
   dFv = -A * (du * (vE - vW) + u * (dvE - dvW)) - Bth * (dv * (vN - vS) + v * (dvN - dvS)) -
@@ -572,14 +608,13 @@ __device__ void obs_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, in
     const ObsRec ob = a.obs[o];
     const int rr = ob.r0 - g.R0;
     if (rr < 0 || rr >= g.Rn) continue;
-    const T* P = X + ob.var * g.P;
     double acc = 0.0;
     const double wj0 = 1.0 - ob.dj, wi0 = 1.0 - ob.di;
-    acc += (wj0 * wi0) * (double)P[(rr + 1) * g.W + ob.k0 + 1];
-    if (ob.di != 0.0) acc += (wj0 * ob.di) * (double)P[(rr + 1) * g.W + ob.k1 + 1];
+    acc += (wj0 * wi0) * (double)X[off(g, ob.var, rr, ob.k0)];
+    if (ob.di != 0.0) acc += (wj0 * ob.di) * (double)X[off(g, ob.var, rr, ob.k1)];
     if (ob.dj != 0.0) {
-      acc += (ob.dj * wi0) * (double)P[(rr + 2) * g.W + ob.k0 + 1];
-      if (ob.di != 0.0) acc += (ob.dj * ob.di) * (double)P[(rr + 2) * g.W + ob.k1 + 1];
+      acc += (ob.dj * wi0) * (double)X[off(g, ob.var, rr + 1, ob.k0)];
+      if (ob.di != 0.0) acc += (ob.dj * ob.di) * (double)X[off(g, ob.var, rr + 1, ob.k1)];
     }
     const double d = acc - ob.y;
     Jo += 0.5 * ob.w * d * d;
@@ -597,14 +632,13 @@ __device__ void obs_level_lin(const SweepArgs<T>& a, const Geo<T>& g, const T* D
     const ObsRec ob = a.obs[o];
     const int rr = ob.r0 - g.R0;
     if (rr < 0 || rr >= g.Rn) continue;
-    const T* P = D + ob.var * g.P;
     double acc = 0.0;
     const double wj0 = 1.0 - ob.dj, wi0 = 1.0 - ob.di;
-    acc += (wj0 * wi0) * (double)P[(rr + 1) * g.W + ob.k0 + 1];
-    if (ob.di != 0.0) acc += (wj0 * ob.di) * (double)P[(rr + 1) * g.W + ob.k1 + 1];
+    acc += (wj0 * wi0) * (double)D[off(g, ob.var, rr, ob.k0)];
+    if (ob.di != 0.0) acc += (wj0 * ob.di) * (double)D[off(g, ob.var, rr, ob.k1)];
     if (ob.dj != 0.0) {
-      acc += (ob.dj * wi0) * (double)P[(rr + 2) * g.W + ob.k0 + 1];
-      if (ob.di != 0.0) acc += (ob.dj * ob.di) * (double)P[(rr + 2) * g.W + ob.k1 + 1];
+      acc += (ob.dj * wi0) * (double)D[off(g, ob.var, rr + 1, ob.k0)];
+      if (ob.di != 0.0) acc += (ob.dj * ob.di) * (double)D[off(g, ob.var, rr + 1, ob.k1)];
     }
     a.obs_force[o] = a.lam * ob.w * acc;
   }
@@ -675,9 +709,11 @@ __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X
   T part = (T)0;
   for_overlap_points(g, l, [&](int rr, int k, int c) {
     const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
-    const T e0 = X[off(g, 0, rr, k)] - tg[go];
-    const T e1 = X[off(g, 1, rr, k)] - tg[go + pl];
-    const T e2 = X[off(g, 2, rr, k)] - tg[go + 2 * pl];
+    T x0, x1, x2;
+    ld3(X, pidx(g, rr, k), g.P, x0, x1, x2);
+    const T e0 = x0 - tg[go];
+    const T e1 = x1 - tg[go + pl];
+    const T e2 = x2 - tg[go + 2 * pl];
     part += (T)c * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
   });
   Jm += (double)part;
@@ -707,7 +743,9 @@ __device__ __forceinline__ bool setup_geo(const SweepArgs<T>& a, cg::cluster_gro
   if (g.rank < g.CL - 1) split_rows(g.ny, g.CL, g.rank + 1, t, g.Rnext); else g.Rnext = 0;
   g.R2 = a.R + 2;
   g.W = a.W;
-  g.P = g.R2 * g.W;
+  g.P = Lay<T>::kVec ? 1 : g.R2 * g.W;
+  g.RS = g.W * Lay<T>::CS;
+  g.BUF = Lay<T>::NS * g.R2 * g.W;
   if (g.rank != 0) g.flags &= ~F_SWALL;           // only the edge CTAs see the walls
   if (g.rank != g.CL - 1) g.flags &= ~F_NWALL;
   g.mnx = magic_of(g.nx);
@@ -725,24 +763,25 @@ __device__ __forceinline__ void stage_point(const SweepArgs<T>& a, const Geo<T>&
                                             T& o0, T& o1, T& o2) {
   const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
   const int P = g.P;
-  const int o = (rr + 1) * g.W + k + 1;
+  const int o = pidx(g, rr, k);
   const int ri = rr + 1;
   T Fh, Fu, Fv;
   T rc[8];
   load_rec8(rs.fw + 8 * ri, rc);
-  rhs_pt<T, DEV>(Y, o, P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, Fh, Fu, Fv);
-  if (cx == (T)0) {
-    o0 = cy * (Y[o] + dt * Fh);
-    o1 = cy * (Y[o + P] + dt * Fu);
-    o2 = cy * (Y[o + 2 * P] + dt * Fv);
-  } else {
-    o0 = cx * X[o] + cy * (Y[o] + dt * Fh);
-    o1 = cx * X[o + P] + cy * (Y[o + P] + dt * Fu);
-    o2 = cx * X[o + 2 * P] + cy * (Y[o + 2 * P] + dt * Fv);
+  Pt5<T> y;
+  load5(Y, o, P, Lay<T>::CS, g.RS, y);
+  rhs_pt<T, DEV>(y, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, Fh, Fu, Fv);
+  o0 = xmul(cy, xfma(dt, Fh, y.h));
+  o1 = xmul(cy, xfma(dt, Fu, y.u));
+  o2 = xmul(cy, xfma(dt, Fv, y.v));
+  if (cx != (T)0) {
+    T xh, xu, xv;
+    ld3(X, o, P, xh, xu, xv);
+    o0 = xfma(cx, xh, o0);
+    o1 = xfma(cx, xu, o1);
+    o2 = xfma(cx, xv, o2);
   }
-  out[o] = o0;
-  out[o + P] = o1;
-  out[o + 2 * P] = o2;
+  st3(out, o, P, o0, o1, o2);
 }
 
 // One RK3 stage on own rows (halos completed afterwards by complete_buf).
@@ -792,22 +831,22 @@ __device__ void fill_fixed(const SweepArgs<T>& a, const Geo<T>& g, T* X, int kin
   const bool s_fixed = g.rank == 0 && (!(g.flags & F_SWALL) || kind == K_ADJ);
   const bool n_fixed = g.rank == g.CL - 1 && (!(g.flags & F_NWALL) || kind == K_ADJ);
   if (s_fixed || n_fixed) {
-    for (int idx = threadIdx.x; idx < 2 * 3 * nx; idx += blockDim.x) {
-      const int q = mdiv(idx, g.mnx);   // side * 3 + v
-      const int side = q / 3;
-      if (side == 0 ? !s_fixed : !n_fixed) continue;
-      const int v = q - 3 * side, k = idx - q * nx;
-      const bool wall = (side == 0) ? (g.flags & F_SWALL) : (g.flags & F_NWALL);
-      X[off(g, v, side == 0 ? -1 : g.Rn, k)] =
-          (kind == K_STATE && !wall) ? gh_row(a, g, nA, nB, wA, wB, side, v, k) : (T)0;
+    for (int idx = threadIdx.x; idx < 2 * nx; idx += blockDim.x) {
+      const int side = idx >= nx ? 1 : 0;
+      if (side ? !n_fixed : !s_fixed) continue;
+      const int k = idx - side * nx;
+      T h, u, v;
+      edge_row_val(a, g, X, kind, side, k, nA, nB, wA, wB, h, u, v);
+      st3(X, pidx(g, side ? g.Rn : -1, k), g.P, h, u, v);
     }
   }
   if (!(g.flags & F_PERIODIC)) {
-    for (int idx = threadIdx.x; idx < 2 * 3 * g.Rn; idx += blockDim.x) {
-      const int q = mdiv(idx, g.mRn);   // side * 3 + v
-      const int side = q / 3;
-      const int v = q - 3 * side, rr = idx - q * g.Rn;
-      X[off(g, v, rr, side == 0 ? -1 : nx)] = (kind == K_STATE) ? gh_col(a, g, nA, nB, wA, wB, side, v, rr) : (T)0;
+    for (int idx = threadIdx.x; idx < 2 * g.Rn; idx += blockDim.x) {
+      const int side = idx >= g.Rn ? 1 : 0;
+      const int rr = idx - side * g.Rn;
+      T h, u, v;
+      ghost_col_val(a, g, X, kind, side, rr, nA, nB, wA, wB, h, u, v);
+      st3(X, pidx(g, rr, side ? nx : -1), g.P, h, u, v);
     }
   }
 }
@@ -819,37 +858,21 @@ __device__ __forceinline__ void publish(const Geo<T>& g, T* X, T* snb, T* nnb, i
                                         T v1, T v2) {
   if (rr == 0) {
     if (snb) {
-      snb[off(g, 0, g.Rprev, k)] = v0;
-      snb[off(g, 1, g.Rprev, k)] = v1;
-      snb[off(g, 2, g.Rprev, k)] = v2;
+      st3(snb, pidx(g, g.Rprev, k), g.P, v0, v1, v2);
     } else if ((g.flags & F_SWALL) && kind != K_ADJ) {
-      X[off(g, 0, -1, k)] = v0;
-      X[off(g, 1, -1, k)] = v1;
-      X[off(g, 2, -1, k)] = -v2;
+      st3(X, pidx(g, -1, k), g.P, v0, v1, -v2);
     }
   }
   if (rr == g.Rn - 1) {
     if (nnb) {
-      nnb[off(g, 0, -1, k)] = v0;
-      nnb[off(g, 1, -1, k)] = v1;
-      nnb[off(g, 2, -1, k)] = v2;
+      st3(nnb, pidx(g, -1, k), g.P, v0, v1, v2);
     } else if ((g.flags & F_NWALL) && kind != K_ADJ) {
-      X[off(g, 0, g.Rn, k)] = v0;
-      X[off(g, 1, g.Rn, k)] = v1;
-      X[off(g, 2, g.Rn, k)] = -v2;
+      st3(X, pidx(g, g.Rn, k), g.P, v0, v1, -v2);
     }
   }
   if (g.flags & F_PERIODIC) {
-    if (k == 0) {
-      X[off(g, 0, rr, g.nx)] = v0;
-      X[off(g, 1, rr, g.nx)] = v1;
-      X[off(g, 2, rr, g.nx)] = v2;
-    }
-    if (k == g.nx - 1) {
-      X[off(g, 0, rr, -1)] = v0;
-      X[off(g, 1, rr, -1)] = v1;
-      X[off(g, 2, rr, -1)] = v2;
-    }
+    if (k == 0) st3(X, pidx(g, rr, g.nx), g.P, v0, v1, v2);
+    if (k == g.nx - 1) st3(X, pidx(g, rr, -1), g.P, v0, v1, v2);
   }
 }
 
@@ -918,7 +941,9 @@ __device__ void push_halos(cg::cluster_group& cl, const SweepArgs<T>& a, const G
       k = (j & 1) ? nx - 1 : 0;
       if (rr == 0 || rr == g.Rn - 1) continue;   // done with the edge rows
     }
-    publish(g, X, snb, nnb, kind, rr, k, X[off(g, 0, rr, k)], X[off(g, 1, rr, k)], X[off(g, 2, rr, k)]);
+    T h, u, v;
+    ld3(X, pidx(g, rr, k), g.P, h, u, v);
+    publish(g, X, snb, nnb, kind, rr, k, h, u, v);
   }
   if constexpr (sizeof(T) == 4) cp_async_wait_all();
   cl.sync();
@@ -926,11 +951,15 @@ __device__ void push_halos(cg::cluster_group& cl, const SweepArgs<T>& a, const G
 
 template <typename T>
 __device__ void store_block(const Geo<T>& g, const T* X, T* dst) {
-  for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
-    const int q = mdiv(idx, g.mnx);   // v * Rn + rr
-    const int v = mdiv(q, g.mRn);
-    const int rr = q - v * g.Rn, k = idx - q * g.nx;
-    dst[((size_t)v * g.ny + g.R0 + rr) * g.d.nxp + k] = X[off(g, v, rr, k)];
+  const size_t pl = (size_t)g.ny * g.d.nxp;
+  for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+    const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+    T h, u, v;
+    ld3(X, pidx(g, rr, k), g.P, h, u, v);
+    T* d = dst + (size_t)(g.R0 + rr) * g.d.nxp + k;
+    d[0] = h;
+    d[pl] = u;
+    d[2 * pl] = v;
   }
 }
 
@@ -952,7 +981,7 @@ __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs
   T* p = reinterpret_cast<T*>(smem_raw);
   for (int b = 0; b < nbuf; ++b) {
     bufs[b] = p;
-    p += 3 * g.P;
+    p += g.BUF;
   }
   const int nr = a.R + 2;
   uintptr_t q = reinterpret_cast<uintptr_t>(p);
@@ -975,7 +1004,7 @@ __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs
 
 template <typename T>
 size_t smem_bytes(int nbuf, int R, int W, bool cache) {
-  return (size_t)nbuf * 3 * (R + 2) * W * sizeof(T) + 16 + 16 * (size_t)(R + 2) * sizeof(T) + 16 +
+  return (size_t)nbuf * Lay<T>::NS * (R + 2) * W * sizeof(T) + 16 + 16 * (size_t)(R + 2) * sizeof(T) + 16 +
          64 * sizeof(double) + 3 * (size_t)ghost_len<T>(cache, R, W) * sizeof(T) + 3 * sizeof(int) + 16;
 }
 
@@ -1050,9 +1079,10 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
     for_overlap_points(g, l, [&](int rr, int k, int c) {
       const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
       const T cc = (T)c;
-      Lb[off(g, 0, rr, k)] += cc * m0 * dx[go];
-      Lb[off(g, 1, rr, k)] += cc * m1 * dx[go + pl];
-      Lb[off(g, 2, rr, k)] += cc * m2 * dx[go + 2 * pl];
+      const int o = pidx(g, rr, k);
+      T l0, l1, l2;
+      ld3(Lb, o, g.P, l0, l1, l2);
+      st3(Lb, o, g.P, l0 + cc * m0 * dx[go], l1 + cc * m1 * dx[go + pl], l2 + cc * m2 * dx[go + 2 * pl]);
     });
   } else if ((any_t || any_s) && a.mu != 0.0) {
     const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
@@ -1061,9 +1091,12 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
     for_overlap_points(g, l, [&](int rr, int k, int c) {
       const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
       const T cc = (T)c;
-      Lb[off(g, 0, rr, k)] += cc * m0 * (X[off(g, 0, rr, k)] - tg[go]);
-      Lb[off(g, 1, rr, k)] += cc * m1 * (X[off(g, 1, rr, k)] - tg[go + pl]);
-      Lb[off(g, 2, rr, k)] += cc * m2 * (X[off(g, 2, rr, k)] - tg[go + 2 * pl]);
+      const int o = pidx(g, rr, k);
+      T l0, l1, l2, x0, x1, x2;
+      ld3(Lb, o, g.P, l0, l1, l2);
+      ld3(X, o, g.P, x0, x1, x2);
+      st3(Lb, o, g.P, l0 + cc * m0 * (x0 - tg[go]), l1 + cc * m1 * (x1 - tg[go + pl]),
+          l2 + cc * m2 * (x2 - tg[go + 2 * pl]));
     });
   }
   __syncthreads();
@@ -1103,7 +1136,7 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   load_rows(a, g, rs);
   ghost_prefetch(a, g, g.a + g.L);
   if (g.L > 0) ghost_prefetch(a, g, g.a + g.L - 1);
-  for (int i = threadIdx.x; i < 3 * g.P; i += blockDim.x) Lp[i] = (T)0;
+  for (int i = threadIdx.x; i < g.BUF; i += blockDim.x) Lp[i] = (T)0;
   const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
   const T c23 = (T)(2.0 / 3.0), c13 = (T)(1.0 / 3.0);
   const int wall_s = (g.flags & F_SWALL) ? 1 : 0;
@@ -1160,52 +1193,60 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       stage_push<T, DEV>(cl, a, g, rs, X2, X, X1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5);
     }
     const int P = g.P;
+    constexpr int CS = Lay<T>::CS;
     // lambda_x2 = 2/3 lambda' + 2/3 dt F'(x2)^T lambda'
     phase_push(cl, a, g, L2, K_ADJ, 0, 0, (T)1, (T)0, [&](int rr, int k, T& v0, T& v1, T& v2) {
-      const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
+      const int o = pidx(g, rr, k), ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
       T rc[8];
       load_rec8(rs.bw + 8 * ri, rc);
-      rhs_adj_pt<T, DEV>(X2, Lp, o, P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth,
-                         href, wall, Gh, Gu, Gv);
-      v0 = c23 * (Lp[o] + dt * Gh);
-      v1 = c23 * (Lp[o + P] + dt * Gu);
-      v2 = c23 * (Lp[o + 2 * P] + dt * Gv);
-      L2[o] = v0;
-      L2[o + P] = v1;
-      L2[o + 2 * P] = v2;
+      Pt5<T> z, m;
+      load5(X2, o, P, CS, g.RS, z);
+      load5(Lp, o, P, CS, g.RS, m);
+      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, wall, Gh, Gu,
+                         Gv);
+      v0 = c23 * (m.h + dt * Gh);
+      v1 = c23 * (m.u + dt * Gu);
+      v2 = c23 * (m.v + dt * Gv);
+      st3(L2, o, P, v0, v1, v2);
     });
     // lambda_x1 = 1/4 lambda_x2 + 1/4 dt F'(x1)^T lambda_x2   (into X2's buffer)
     T* L1 = X2;
     phase_push(cl, a, g, L1, K_ADJ, 0, 0, (T)1, (T)0, [&](int rr, int k, T& v0, T& v1, T& v2) {
-      const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
+      const int o = pidx(g, rr, k), ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
       T rc[8];
       load_rec8(rs.bw + 8 * ri, rc);
-      rhs_adj_pt<T, DEV>(X1, L2, o, P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth,
-                         href, wall, Gh, Gu, Gv);
-      v0 = (T)0.25 * (L2[o] + dt * Gh);
-      v1 = (T)0.25 * (L2[o + P] + dt * Gu);
-      v2 = (T)0.25 * (L2[o + 2 * P] + dt * Gv);
-      L1[o] = v0;
-      L1[o + P] = v1;
-      L1[o + 2 * P] = v2;
+      Pt5<T> z, m;
+      load5(X1, o, P, CS, g.RS, z);
+      load5(L2, o, P, CS, g.RS, m);
+      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, wall, Gh, Gu,
+                         Gv);
+      v0 = (T)0.25 * (m.h + dt * Gh);
+      v1 = (T)0.25 * (m.u + dt * Gu);
+      v2 = (T)0.25 * (m.v + dt * Gv);
+      st3(L1, o, P, v0, v1, v2);
     });
     // lambda(n) = 1/3 lambda' + 3/4 lambda_x2 + lambda_x1 + dt F'(x)^T lambda_x1
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
       const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
-      const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
+      const int o = pidx(g, rr, k), ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
       T rc[8];
       load_rec8(rs.bw + 8 * ri, rc);
-      rhs_adj_pt<T, DEV>(X, L1, o, P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth,
-                         href, wall, Gh, Gu, Gv);
-      Lp[o] = c13 * Lp[o] + (T)0.75 * L2[o] + L1[o] + dt * Gh;
-      Lp[o + P] = c13 * Lp[o + P] + (T)0.75 * L2[o + P] + L1[o + P] + dt * Gu;
-      Lp[o + 2 * P] = c13 * Lp[o + 2 * P] + (T)0.75 * L2[o + 2 * P] + L1[o + 2 * P] + dt * Gv;
+      Pt5<T> z, m;
+      load5(X, o, P, CS, g.RS, z);
+      load5(L1, o, P, CS, g.RS, m);
+      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, wall, Gh, Gu,
+                         Gv);
+      T ph, pu, pv, qh, qu, qv;
+      ld3(Lp, o, P, ph, pu, pv);
+      ld3(L2, o, P, qh, qu, qv);
+      st3(Lp, o, P, c13 * ph + (T)0.75 * qh + m.h + dt * Gh, c13 * pu + (T)0.75 * qu + m.u + dt * Gu,
+          c13 * pv + (T)0.75 * qv + m.v + dt * Gv);
     }
     __syncthreads();
     add_forcing(a, g, Lp, X, l);
@@ -1232,7 +1273,7 @@ __device__ void load_delta0(const SweepArgs<T>& a, const Geo<T>& g, T* D) {
   const int r_lo = (g.rank > 0) ? -1 : 0;
   const int r_hi = (g.rank < g.CL - 1) ? g.Rn + 1 : g.Rn;
   const int nr = r_hi - r_lo;
-  for (int i = threadIdx.x; i < 3 * g.P; i += blockDim.x) D[i] = (T)0;
+  for (int i = threadIdx.x; i < g.BUF; i += blockDim.x) D[i] = (T)0;
   __syncthreads();
   for (int idx = threadIdx.x; idx < 3 * nr * g.nx; idx += blockDim.x) {
     const int q = mdiv(idx, g.mnx);   // v * nr + (rr - r_lo)
@@ -1278,15 +1319,18 @@ __device__ void stage_tl(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T
   const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
   for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
     const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
-    const int o = (rr + 1) * g.W + k + 1, ri = rr + 1;
+    const int o = pidx(g, rr, k), ri = rr + 1;
     T Fh, Fu, Fv;
     T rc[8];
     load_rec8(rs.fw + 8 * ri, rc);
-    rhs_tl_pt<T, DEV>(Y, DY, o, g.P, g.W, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, Fh,
-                      Fu, Fv);
-    dout[o] = cx * DX[o] + cy * (DY[o] + dt * Fh);
-    dout[o + g.P] = cx * DX[o + g.P] + cy * (DY[o + g.P] + dt * Fu);
-    dout[o + 2 * g.P] = cx * DX[o + 2 * g.P] + cy * (DY[o + 2 * g.P] + dt * Fv);
+    Pt5<T> z, d;
+    load5(Y, o, g.P, Lay<T>::CS, g.RS, z);
+    load5(DY, o, g.P, Lay<T>::CS, g.RS, d);
+    rhs_tl_pt<T, DEV>(z, d, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, Fh, Fu, Fv);
+    T xh, xu, xv;
+    ld3(DX, o, g.P, xh, xu, xv);
+    st3(dout, o, g.P, cx * xh + cy * (d.h + dt * Fh), cx * xu + cy * (d.u + dt * Fu),
+        cx * xv + cy * (d.v + dt * Fv));
   }
 }
 
