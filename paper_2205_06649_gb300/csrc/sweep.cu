@@ -264,41 +264,60 @@ __device__ void ghost_prefetch(const SweepArgs<T>& a, const Geo<T>& g, int n) {
   if (threadIdx.x == 0) g.gh_tag[slot] = n;
 }
 
-// Ghost column of own row rr (side 0 = west, 1 = east) and ghost row value at
-// column k (side 0 = south, 1 = north), blended between levels nA and nB.
+// Source of the ghost values of one phase: the boundary trajectory blended
+// between levels nA and nB (wA x(nA) + wB x(nB)).  Resolved once per phase:
+// when both levels sit in the ghost cache, ca / cb point at their slots and
+// every lookup is one or two shared-memory loads; otherwise (FP64 path, or a
+// level not cached) the values are read from HBM.  Both give identical
+// values.
 template <typename T>
-__device__ __forceinline__ T gh_col(const SweepArgs<T>& a, const Geo<T>& g, int nA, int nB, T wA, T wB,
-                                    int side, int v, int rr) {
-  if constexpr (sizeof(T) == 8) {
-    const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + g.nx) % a.nlon;
-    return bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.R0 + rr, i);
+struct GhostSrc {
+  const T* ca;
+  const T* cb;   // nullptr when wB = 0
+  int nA, nB;
+  T wA, wB;
+  bool cached;
+};
+
+template <typename T>
+__device__ __forceinline__ GhostSrc<T> ghost_src(const Geo<T>& g, int nA, int nB, T wA, T wB) {
+  GhostSrc<T> s{nullptr, nullptr, nA, nB, wA, wB, false};
+  if constexpr (sizeof(T) == 4) {
+    if (g.gh_len > 0 && nA >= 0 && nB >= 0) {
+      const int sA = nA % 3, sB = nB % 3;
+      if (g.gh_tag[sA] == nA && (wB == (T)0 || g.gh_tag[sB] == nB)) {
+        s.cached = true;
+        s.ca = g.gh + (size_t)sA * g.gh_len;
+        s.cb = (wB == (T)0) ? nullptr : g.gh + (size_t)sB * g.gh_len;
+      }
+    }
   }
-  const int R = g.R2 - 2;
-  const int sA = nA % 3, sB = nB % 3;
-  if (g.gh_tag[sA] == nA && (wB == (T)0 || g.gh_tag[sB] == nB)) {
-    const int o = (side * 3 + v) * R + rr;
-    const T xa = g.gh[(size_t)sA * g.gh_len + o];
-    if (wB == (T)0) return xa;
-    return xfma(wA, xa, xmul(wB, g.gh[(size_t)sB * g.gh_len + o]));
+  return s;
+}
+
+// Ghost column of own row rr (side 0 = west, 1 = east) and ghost row value at
+// column k (side 0 = south, 1 = north).
+template <typename T>
+__device__ __forceinline__ T gh_col(const SweepArgs<T>& a, const Geo<T>& g, const GhostSrc<T>& s, int side,
+                                    int v, int rr) {
+  if (s.cached) {
+    const int o = (side * 3 + v) * (g.R2 - 2) + rr;
+    const T xa = s.ca[o];
+    return s.cb ? xfma(s.wA, xa, xmul(s.wB, s.cb[o])) : xa;
   }
   const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + g.nx) % a.nlon;
-  return bnd_val(a, nA, nB, wA, wB, v, g.d.j0 + g.R0 + rr, i);
+  return bnd_val(a, s.nA, s.nB, s.wA, s.wB, v, g.d.j0 + g.R0 + rr, i);
 }
 
 template <typename T>
-__device__ __forceinline__ T gh_row(const SweepArgs<T>& a, const Geo<T>& g, int nA, int nB, T wA, T wB,
-                                    int side, int v, int k) {
-  if constexpr (sizeof(T) == 8)
-    return bnd_val(a, nA, nB, wA, wB, v, side ? g.d.j0 + g.ny : g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
-  const int R = g.R2 - 2;
-  const int sA = nA % 3, sB = nB % 3;
-  if (g.gh_tag[sA] == nA && (wB == (T)0 || g.gh_tag[sB] == nB)) {
-    const int o = 6 * R + (side * 3 + v) * g.W + k;
-    const T xa = g.gh[(size_t)sA * g.gh_len + o];
-    if (wB == (T)0) return xa;
-    return xfma(wA, xa, xmul(wB, g.gh[(size_t)sB * g.gh_len + o]));
+__device__ __forceinline__ T gh_row(const SweepArgs<T>& a, const Geo<T>& g, const GhostSrc<T>& s, int side,
+                                    int v, int k) {
+  if (s.cached) {
+    const int o = 6 * (g.R2 - 2) + (side * 3 + v) * g.W + k;
+    const T xa = s.ca[o];
+    return s.cb ? xfma(s.wA, xa, xmul(s.wB, s.cb[o])) : xa;
   }
-  return bnd_val(a, nA, nB, wA, wB, v, side ? g.d.j0 + g.ny : g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
+  return bnd_val(a, s.nA, s.nB, s.wA, s.wB, v, side ? g.d.j0 + g.ny : g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
 }
 
 // Value of halo row `side` (0 south, 1 north) at column k of a stripe that
@@ -308,7 +327,7 @@ __device__ __forceinline__ T gh_row(const SweepArgs<T>& a, const Geo<T>& g, int 
 // edges).
 template <typename T>
 __device__ __forceinline__ void edge_row_val(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int kind,
-                                             int side, int k, int nA, int nB, T wA, T wB, T& h, T& u, T& v) {
+                                             int side, int k, const GhostSrc<T>& gs, T& h, T& u, T& v) {
   const bool wall = side ? (g.flags & F_NWALL) : (g.flags & F_SWALL);
   if (wall) {
     if (kind == K_ADJ) {
@@ -318,9 +337,9 @@ __device__ __forceinline__ void edge_row_val(const SweepArgs<T>& a, const Geo<T>
     ld3(X, pidx(g, side ? g.Rn - 1 : 0, k), g.P, h, u, v);
     v = -v;
   } else if (kind == K_STATE) {
-    h = gh_row(a, g, nA, nB, wA, wB, side, 0, k);
-    u = gh_row(a, g, nA, nB, wA, wB, side, 1, k);
-    v = gh_row(a, g, nA, nB, wA, wB, side, 2, k);
+    h = gh_row(a, g, gs, side, 0, k);
+    u = gh_row(a, g, gs, side, 1, k);
+    v = gh_row(a, g, gs, side, 2, k);
   } else {
     h = u = v = (T)0;
   }
@@ -330,14 +349,13 @@ __device__ __forceinline__ void edge_row_val(const SweepArgs<T>& a, const Geo<T>
 // wrap, the frozen boundary trajectory, or zero.
 template <typename T>
 __device__ __forceinline__ void ghost_col_val(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int kind,
-                                              int side, int rr, int nA, int nB, T wA, T wB, T& h, T& u,
-                                              T& v) {
+                                              int side, int rr, const GhostSrc<T>& gs, T& h, T& u, T& v) {
   if (g.flags & F_PERIODIC) {
     ld3(X, pidx(g, rr, side ? 0 : g.nx - 1), g.P, h, u, v);
   } else if (kind == K_STATE) {
-    h = gh_col(a, g, nA, nB, wA, wB, side, 0, rr);
-    u = gh_col(a, g, nA, nB, wA, wB, side, 1, rr);
-    v = gh_col(a, g, nA, nB, wA, wB, side, 2, rr);
+    h = gh_col(a, g, gs, side, 0, rr);
+    u = gh_col(a, g, gs, side, 1, rr);
+    v = gh_col(a, g, gs, side, 2, rr);
   } else {
     h = u = v = (T)0;
   }
@@ -355,6 +373,7 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
   const int nx = g.nx;
   const T* south_nb = (g.rank > 0) ? cl.map_shared_rank(X, g.rank - 1) : nullptr;
   const T* north_nb = (g.rank < g.CL - 1) ? cl.map_shared_rank(X, g.rank + 1) : nullptr;
+  const GhostSrc<T> gs = ghost_src(g, nA, nB, wA, wB);
   // halo rows
   for (int idx = threadIdx.x; idx < 2 * nx; idx += blockDim.x) {
     const int side = idx >= nx ? 1 : 0;
@@ -364,7 +383,7 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
     if (nb) {
       ld3(nb, pidx(g, side ? 0 : g.Rprev - 1, k), g.P, h, u, v);
     } else {
-      edge_row_val(a, g, X, kind, side, k, nA, nB, wA, wB, h, u, v);
+      edge_row_val(a, g, X, kind, side, k, gs, h, u, v);
     }
     st3(X, pidx(g, side ? g.Rn : -1, k), g.P, h, u, v);
   }
@@ -373,7 +392,7 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
     const int side = idx >= g.Rn ? 1 : 0;
     const int rr = idx - side * g.Rn;
     T h, u, v;
-    ghost_col_val(a, g, X, kind, side, rr, nA, nB, wA, wB, h, u, v);
+    ghost_col_val(a, g, X, kind, side, rr, gs, h, u, v);
     st3(X, pidx(g, rr, side ? nx : -1), g.P, h, u, v);
   }
   __syncthreads();
@@ -383,21 +402,21 @@ __device__ void complete_buf(cg::cluster_group& cl, const SweepArgs<T>& a, const
 // state buffer X whose own rows are in place; ghosts from the boundary
 // trajectory blended between levels nA and nB.
 template <typename T>
-__device__ __forceinline__ void state_edges(const SweepArgs<T>& a, const Geo<T>& g, T* X, int j, int nA,
-                                            int nB, T wA, T wB) {
+__device__ __forceinline__ void state_edges(const SweepArgs<T>& a, const Geo<T>& g, T* X, int j,
+                                            const GhostSrc<T>& gs) {
   const int nx = g.nx;
   T h, u, v;
   if (j < 2 * nx) {
     const int side = j >= nx ? 1 : 0;
     const int k = j - side * nx;
     if (side ? g.rank != g.CL - 1 : g.rank != 0) return;   // interior halo: loaded
-    edge_row_val(a, g, X, K_STATE, side, k, nA, nB, wA, wB, h, u, v);
+    edge_row_val(a, g, X, K_STATE, side, k, gs, h, u, v);
     st3(X, pidx(g, side ? g.Rn : -1, k), g.P, h, u, v);
   } else {
     j -= 2 * nx;
     const int side = j >= g.Rn ? 1 : 0;
     const int rr = j - side * g.Rn;
-    ghost_col_val(a, g, X, K_STATE, side, rr, nA, nB, wA, wB, h, u, v);
+    ghost_col_val(a, g, X, K_STATE, side, rr, gs, h, u, v);
     st3(X, pidx(g, rr, side ? nx : -1), g.P, h, u, v);
   }
 }
@@ -422,7 +441,8 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
   }
   if constexpr (sizeof(T) == 4) cp_async_wait_all();
   __syncthreads();
-  for (int j = threadIdx.x; j < 2 * nx + 2 * g.Rn; j += blockDim.x) state_edges(a, g, X, j, nA, nB, wA, wB);
+  const GhostSrc<T> gs = ghost_src(g, nA, nB, wA, wB);
+  for (int j = threadIdx.x; j < 2 * nx + 2 * g.Rn; j += blockDim.x) state_edges(a, g, X, j, gs);
   __syncthreads();
 }
 
@@ -449,9 +469,12 @@ __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X
   }
   if constexpr (sizeof(T) == 4) cp_async_wait_all();
   __syncthreads();
+  GhostSrc<T> gs[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) gs[b] = ghost_src(g, nA[b], nB[b], wA[b], wB[b]);
   for (int j = threadIdx.x; j < 2 * nx + 2 * g.Rn; j += blockDim.x) {
 #pragma unroll
-    for (int b = 0; b < 3; ++b) state_edges(a, g, X[b], j, nA[b], nB[b], wA[b], wB[b]);
+    for (int b = 0; b < 3; ++b) state_edges(a, g, X[b], j, gs[b]);
   }
   __syncthreads();
 }
@@ -604,7 +627,9 @@ __device__ __forceinline__ int overlap_count(const Geo<T>& g, int l, int r, int 
 template <typename T>
 __device__ void obs_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int l, double& Jo) {
   const int o0 = a.lvl_obs[g.d.obs_lvl + l], o1 = a.lvl_obs[g.d.obs_lvl + l + 1];
-  for (int o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
+  // highest-numbered threads first (the low threads start the next phase's
+  // edge rows)
+  for (int o = o0 + (blockDim.x - 1 - threadIdx.x); o < o1; o += blockDim.x) {
     const ObsRec ob = a.obs[o];
     const int rr = ob.r0 - g.R0;
     if (rr < 0 || rr >= g.Rn) continue;
@@ -645,7 +670,8 @@ __device__ void obs_level_lin(const SweepArgs<T>& a, const Geo<T>& g, const T* D
 }
 
 // Calls f(rr, k, c) for every own point (rr, k) of level l with overlap count
-// c > 0, spread over the CTA's threads.  At a level outside the time overlaps
+// c > 0, spread over the CTA's threads from the highest-numbered one down (the
+// low threads start the next phase's edge rows).  At a level outside the time overlaps
 // only the spatial bands have c > 0: rows r < wS and r >= ny - wN in full,
 // and the columns k < wL and k >= nx - wR of the rows between; those points
 // alone are visited.
@@ -655,7 +681,7 @@ __device__ __forceinline__ void for_overlap_points(const Geo<T>& g, int l, F&& f
   const int nx = g.nx;
   const bool any_t = (l < d.tA) || (l > g.L - d.tB);
   if (any_t || d.wL + d.wR >= nx) {
-    for (int idx = threadIdx.x; idx < g.Rn * nx; idx += blockDim.x) {
+    for (int idx = blockDim.x - 1 - threadIdx.x; idx < g.Rn * nx; idx += blockDim.x) {
       const int rr = mdiv(idx, g.mnx), k = idx - rr * nx;
       const int c = overlap_count(g, l, g.R0 + rr, k);
       if (c) f(rr, k, c);
@@ -670,7 +696,7 @@ __device__ __forceinline__ void for_overlap_points(const Geo<T>& g, int l, F&& f
   const int wc = d.wL + d.wR;
   const int nA = A * nx, nC = C * nx, nB = B * wc;
   const unsigned mwc = magic_of(wc);
-  for (int idx = threadIdx.x; idx < nA + nC + nB; idx += blockDim.x) {
+  for (int idx = blockDim.x - 1 - threadIdx.x; idx < nA + nC + nB; idx += blockDim.x) {
     int rr, k;
     if (idx < nA) {
       rr = mdiv(idx, g.mnx);
@@ -830,22 +856,27 @@ __device__ void fill_fixed(const SweepArgs<T>& a, const Geo<T>& g, T* X, int kin
   const int nx = g.nx;
   const bool s_fixed = g.rank == 0 && (!(g.flags & F_SWALL) || kind == K_ADJ);
   const bool n_fixed = g.rank == g.CL - 1 && (!(g.flags & F_NWALL) || kind == K_ADJ);
-  if (s_fixed || n_fixed) {
-    for (int idx = threadIdx.x; idx < 2 * nx; idx += blockDim.x) {
-      const int side = idx >= nx ? 1 : 0;
+  const bool cols = !(g.flags & F_PERIODIC);
+  if (!s_fixed && !n_fixed && !cols) return;
+  const GhostSrc<T> gs = ghost_src(g, nA, nB, wA, wB);
+  // Edge-row points [0, 2 nx) then ghost-column points [2 nx, 2 nx + 2 Rn),
+  // on the highest-numbered threads: the low threads compute the edge rows
+  // and the most interior points of the phase.
+  const int n = 2 * nx + 2 * g.Rn;
+  for (int r = blockDim.x - 1 - threadIdx.x; r < n; r += blockDim.x) {
+    T h, u, v;
+    if (r < 2 * nx) {
+      const int side = r >= nx ? 1 : 0;
       if (side ? !n_fixed : !s_fixed) continue;
-      const int k = idx - side * nx;
-      T h, u, v;
-      edge_row_val(a, g, X, kind, side, k, nA, nB, wA, wB, h, u, v);
+      const int k = r - side * nx;
+      edge_row_val(a, g, X, kind, side, k, gs, h, u, v);
       st3(X, pidx(g, side ? g.Rn : -1, k), g.P, h, u, v);
-    }
-  }
-  if (!(g.flags & F_PERIODIC)) {
-    for (int idx = threadIdx.x; idx < 2 * g.Rn; idx += blockDim.x) {
-      const int side = idx >= g.Rn ? 1 : 0;
-      const int rr = idx - side * g.Rn;
-      T h, u, v;
-      ghost_col_val(a, g, X, kind, side, rr, nA, nB, wA, wB, h, u, v);
+    } else {
+      if (!cols) continue;
+      const int j = r - 2 * nx;
+      const int side = j >= g.Rn ? 1 : 0;
+      const int rr = j - side * g.Rn;
+      ghost_col_val(a, g, X, kind, side, rr, gs, h, u, v);
       st3(X, pidx(g, rr, side ? nx : -1), g.P, h, u, v);
     }
   }
