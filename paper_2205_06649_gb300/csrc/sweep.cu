@@ -58,6 +58,7 @@ struct Geo {
   SubDesc d;
   T* gh;              // ghost cache: 3 slots of [6 R columns | 6 W rows] values
   int* gh_tag;        // level held by each slot (-1: none)
+  T* tgb;             // shared buffer of prefetched overlap targets (FP32 sweeps), or nullptr
   int gh_len;         // values per slot
   // multipliers for division by nx, Rn, ny and the loaded row count nr
   // (mdiv below) in the per-point index mappings
@@ -214,7 +215,8 @@ __device__ __forceinline__ T bnd_val(const SweepArgs<T>& a, int nA, int nB, T wA
 // shared-memory ring with cp.async one step before they are used, so that the
 // completion after each stage reads shared memory instead of waiting on HBM.
 // Slot of level n: n mod 3; a lookup whose level is not in its slot falls back
-// to HBM (results never depend on the cache).
+// to HBM (results never depend on the cache).  The copies join the caller's
+// next cp.async commit group.
 // Slot layout: columns [side][var][R], then rows [side][var][W].
 
 __device__ __forceinline__ void cp_async_4or8(void* dst, const void* src, int bytes) {
@@ -226,6 +228,8 @@ __device__ __forceinline__ void cp_async_4or8(void* dst, const void* src, int by
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+// All but the most recently committed group complete.
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 template <typename T>
 __device__ void ghost_prefetch(const SweepArgs<T>& a, const Geo<T>& g, int n) {
@@ -260,7 +264,6 @@ __device__ void ghost_prefetch(const SweepArgs<T>& a, const Geo<T>& g, int n) {
                     src + ((size_t)v * a.nlat + j) * a.nlon + (g.d.i0 + k) % a.nlon, (int)sizeof(T));
     }
   }
-  cp_async_commit();
   if (threadIdx.x == 0) g.gh_tag[slot] = n;
 }
 
@@ -732,17 +735,50 @@ __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X
   const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
   const T i0 = a.isb2_s[0], i1 = a.isb2_s[1], i2 = a.isb2_s[2];
   const size_t pl = (size_t)g.ny * d.nxp;
+  if (g.tgb) cp_async_wait_all();   // this thread's prefetched targets
   T part = (T)0;
   for_overlap_points(g, l, [&](int rr, int k, int c) {
-    const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
-    T x0, x1, x2;
-    ld3(X, pidx(g, rr, k), g.P, x0, x1, x2);
-    const T e0 = x0 - tg[go];
-    const T e1 = x1 - tg[go + pl];
-    const T e2 = x2 - tg[go + 2 * pl];
+    const int o = pidx(g, rr, k);
+    T x0, x1, x2, t0, t1, t2;
+    ld3(X, o, g.P, x0, x1, x2);
+    if (g.tgb) {
+      ld3(g.tgb, o, g.P, t0, t1, t2);
+    } else {
+      const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
+      t0 = tg[go];
+      t1 = tg[go + pl];
+      t2 = tg[go + 2 * pl];
+    }
+    const T e0 = x0 - t0;
+    const T e1 = x1 - t1;
+    const T e2 = x2 - t2;
     part += (T)c * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
   });
   Jm += (double)part;
+}
+
+// Copies the overlap targets of level l at this CTA's overlap points into the
+// shared target buffer (FP32 sweeps) with cp.async, a few phases before
+// overlap_level or add_forcing read them.  Each point is copied and later
+// read by the same thread (the same for_overlap_points mapping), so that
+// thread's own cp.async wait is all the synchronisation the read needs.  The
+// copies join the caller's next commit group.
+template <typename T>
+__device__ void prefetch_targets(const SweepArgs<T>& a, const Geo<T>& g, int l) {
+  if (!g.tgb) return;
+  const SubDesc& d = g.d;
+  const bool any_t = (l < d.tA) || (l > g.L - d.tB);
+  const bool any_s = d.wL || d.wR || d.wS || d.wN;
+  if (!any_t && !any_s) return;
+  const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
+  const size_t pl = (size_t)g.ny * d.nxp;
+  for_overlap_points(g, l, [&](int rr, int k, int c) {
+    const T* s = tg + (size_t)(g.R0 + rr) * d.nxp + k;
+    T* dst = g.tgb + pidx(g, rr, k);
+    cp_async_4or8(dst, s, (int)sizeof(T));
+    cp_async_4or8(dst + g.P, s + pl, (int)sizeof(T));
+    cp_async_4or8(dst + 2 * g.P, s + 2 * pl, (int)sizeof(T));
+  });
 }
 
 template <typename T>
@@ -909,9 +945,11 @@ __device__ __forceinline__ void publish(const Geo<T>& g, T* X, T* snb, T* nnb, i
 
 // Steps 1-5 with fn(rr, k, v0, v1, v2) computing and storing point (rr, k)
 // of X and returning its values.
+// pend = 1 leaves the most recent cp.async commit group in flight at the end
+// of the phase (prefetches consumed in a later phase).
 template <typename T, typename Fn>
 __device__ void phase_push(cg::cluster_group& cl, const SweepArgs<T>& a, const Geo<T>& g, T* X, int kind,
-                           int nA, int nB, T wA, T wB, Fn&& fn) {
+                           int nA, int nB, T wA, T wB, Fn&& fn, int pend = 0) {
   fill_fixed(a, g, X, kind, nA, nB, wA, wB);
   T* snb = g.rank > 0 ? cl.map_shared_rank(X, g.rank - 1) : nullptr;
   T* nnb = g.rank < g.CL - 1 ? cl.map_shared_rank(X, g.rank + 1) : nullptr;
@@ -933,7 +971,12 @@ __device__ void phase_push(cg::cluster_group& cl, const SweepArgs<T>& a, const G
     fn(rr, k, v0, v1, v2);
     if ((g.flags & F_PERIODIC) && (k == 0 || k == nx - 1)) publish(g, X, snb, nnb, kind, rr, k, v0, v1, v2);
   }
-  if constexpr (sizeof(T) == 4) cp_async_wait_all();   // this thread's ghost copies land first
+  if constexpr (sizeof(T) == 4) {   // this thread's ghost copies land first
+    if (pend)
+      cp_async_wait_prev();
+    else
+      cp_async_wait_all();
+  }
   __syncthreads();
   cluster_wait_acquire();
 }
@@ -942,10 +985,13 @@ __device__ void phase_push(cg::cluster_group& cl, const SweepArgs<T>& a, const G
 template <typename T, bool DEV>
 __device__ __forceinline__ void stage_push(cg::cluster_group& cl, const SweepArgs<T>& a, const Geo<T>& g,
                                            const RowSmem<T>& rs, T* out, const T* X, const T* Y, T cx, T cy,
-                                           int nA, int nB, T wA, T wB) {
-  phase_push(cl, a, g, out, K_STATE, nA, nB, wA, wB, [&](int rr, int k, T& v0, T& v1, T& v2) {
-    stage_point<T, DEV>(a, g, rs, out, X, Y, cx, cy, rr, k, v0, v1, v2);
-  });
+                                           int nA, int nB, T wA, T wB, int pend = 0) {
+  phase_push(
+      cl, a, g, out, K_STATE, nA, nB, wA, wB,
+      [&](int rr, int k, T& v0, T& v1, T& v2) {
+        stage_point<T, DEV>(a, g, rs, out, X, Y, cx, cy, rr, k, v0, v1, v2);
+      },
+      pend);
 }
 
 // Halo data of a buffer whose own rows are final (after forcing terms were
@@ -999,6 +1045,13 @@ __device__ __forceinline__ void store_level(const SweepArgs<T>& a, const Geo<T>&
   store_block(g, X, a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp);
 }
 
+// The FP32 forward and adjoint sweeps (the ones with a ghost cache) also
+// prefetch overlap targets into one more state-sized buffer.
+template <typename T>
+__host__ __device__ constexpr bool target_buffer(bool cache) {
+  return cache && sizeof(T) == 4;
+}
+
 // Ghost-cache length per slot (FP32 forward / adjoint sweeps only).
 template <typename T>
 __host__ __device__ constexpr int ghost_len(bool cache, int R, int W) {
@@ -1012,6 +1065,12 @@ __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs
   T* p = reinterpret_cast<T*>(smem_raw);
   for (int b = 0; b < nbuf; ++b) {
     bufs[b] = p;
+    p += g.BUF;
+  }
+  Geo<T>& gt = const_cast<Geo<T>&>(g);
+  gt.tgb = nullptr;
+  if (target_buffer<T>(cache)) {
+    gt.tgb = p;
     p += g.BUF;
   }
   const int nr = a.R + 2;
@@ -1035,6 +1094,7 @@ __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs
 
 template <typename T>
 size_t smem_bytes(int nbuf, int R, int W, bool cache) {
+  nbuf += target_buffer<T>(cache) ? 1 : 0;
   return (size_t)nbuf * Lay<T>::NS * (R + 2) * W * sizeof(T) + 16 + 16 * (size_t)(R + 2) * sizeof(T) + 16 +
          64 * sizeof(double) + 3 * (size_t)ghost_len<T>(cache, R, W) * sizeof(T) + 3 * sizeof(int) + 16;
 }
@@ -1058,17 +1118,25 @@ __global__ void __launch_bounds__(512, 2) fwd_kernel(SweepArgs<T> a) {
   load_rows(a, g, rs);
   ghost_prefetch(a, g, g.a);
   if (g.L > 0) ghost_prefetch(a, g, g.a + 1);
+  cp_async_commit();
   load_level(a, g, X, 0, g.a);   // includes a CTA barrier
+  prefetch_targets(a, g, 0);
+  cp_async_commit();
   double Jo = 0.0, Jm = 0.0;
   obs_level(a, g, X, 0, Jo);
   overlap_level(a, g, X, 0, Jm);
   for (int l = 0; l < g.L; ++l) {
     const int n = g.a + l;
-    if (n + 2 <= g.d.b) ghost_prefetch(a, g, n + 2);   // used by the next step
     stage_push<T, DEV>(cl, a, g, rs, S1, X, X, (T)0, (T)1, n + 1, n + 1, (T)1, (T)0);
     // stores read the buffer with another thread mapping: after the barrier
     if (a.stg) store_block(g, S1, stage_ptr(a, g, l, 0));
-    stage_push<T, DEV>(cl, a, g, rs, S2, X, S1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5);
+    // after that barrier, level l's targets have been read and the ghost slot
+    // of level n - 1 is free: prefetch the ghosts of the next step and the
+    // targets of level l + 1, consumed after the third stage
+    if (n + 2 <= g.d.b) ghost_prefetch(a, g, n + 2);
+    prefetch_targets(a, g, l + 1);
+    cp_async_commit();
+    stage_push<T, DEV>(cl, a, g, rs, S2, X, S1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5, 1);
     if (a.stg) store_block(g, S2, stage_ptr(a, g, l, 1));
     stage_push<T, DEV>(cl, a, g, rs, X, X, S2, (T)(1.0 / 3.0), (T)(2.0 / 3.0), n + 1, n + 1, (T)1, (T)0);
     if (a.ckpt == 0 || (l + 1) % a.ckpt == 0) store_level(a, g, X, l + 1);
@@ -1119,15 +1187,22 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
     const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
     const T m0 = a.musb2_s[0], m1 = a.musb2_s[1], m2 = a.musb2_s[2];
     const size_t pl = (size_t)g.ny * d.nxp;
+    if (g.tgb) cp_async_wait_all();   // this thread's prefetched targets
     for_overlap_points(g, l, [&](int rr, int k, int c) {
-      const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
       const T cc = (T)c;
       const int o = pidx(g, rr, k);
-      T l0, l1, l2, x0, x1, x2;
+      T l0, l1, l2, x0, x1, x2, t0, t1, t2;
       ld3(Lb, o, g.P, l0, l1, l2);
       ld3(X, o, g.P, x0, x1, x2);
-      st3(Lb, o, g.P, l0 + cc * m0 * (x0 - tg[go]), l1 + cc * m1 * (x1 - tg[go + pl]),
-          l2 + cc * m2 * (x2 - tg[go + 2 * pl]));
+      if (g.tgb) {
+        ld3(g.tgb, o, g.P, t0, t1, t2);
+      } else {
+        const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
+        t0 = tg[go];
+        t1 = tg[go + pl];
+        t2 = tg[go + 2 * pl];
+      }
+      st3(Lb, o, g.P, l0 + cc * m0 * (x0 - t0), l1 + cc * m1 * (x1 - t1), l2 + cc * m2 * (x2 - t2));
     });
   }
   __syncthreads();
@@ -1167,6 +1242,10 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   load_rows(a, g, rs);
   ghost_prefetch(a, g, g.a + g.L);
   if (g.L > 0) ghost_prefetch(a, g, g.a + g.L - 1);
+  cp_async_commit();
+  // overlap targets prefetched for add_forcing (not for external forcing or
+  // Gauss-Newton products, which take no targets)
+  const bool pre_tg = g.tgb && a.mu != 0.0 && !a.gn_dx && !a.yforce;
   for (int i = threadIdx.x; i < g.BUF; i += blockDim.x) Lp[i] = (T)0;
   const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
   const T c23 = (T)(2.0 / 3.0), c13 = (T)(1.0 / 3.0);
@@ -1203,12 +1282,13 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   if (sgi == nseg - 1) {
     // lambda(b) = forcing(b)
     load_state(a, g, X, level_src(g.L), g.a + g.L, g.a + g.L, (T)1, (T)0);
+    if (pre_tg) prefetch_targets(a, g, g.L);
+    cp_async_commit();
     add_forcing(a, g, Lp, X, g.L);
     complete_buf(cl, a, g, Lp, K_ADJ, 0, 0, (T)1, (T)0);
   }
   for (int l = l1 - 1; l >= l0; --l) {
     const int n = g.a + l;
-    if (l > 0) ghost_prefetch(a, g, n - 1);   // used by the next (earlier) step
     if (a.stg && !K) {   // x(n) and the stage states stored by the forward sweep
       T* bufs[3] = {X, X1, X2};
       const T* srcs[3] = {a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp,
@@ -1223,10 +1303,18 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       stage_push<T, DEV>(cl, a, g, rs, X1, X, X, (T)0, (T)1, n + 1, n + 1, (T)1, (T)0);
       stage_push<T, DEV>(cl, a, g, rs, X2, X, X1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5);
     }
+    // after those barriers, the ghost slot of level n + 2 and the target
+    // buffer are free: prefetch the ghosts of the next (earlier) step and the
+    // targets of this level, consumed by add_forcing at the end of the step
+    if (l > 0) ghost_prefetch(a, g, n - 1);
+    if (pre_tg) prefetch_targets(a, g, l);
+    cp_async_commit();
     const int P = g.P;
     constexpr int CS = Lay<T>::CS;
     // lambda_x2 = 2/3 lambda' + 2/3 dt F'(x2)^T lambda'
-    phase_push(cl, a, g, L2, K_ADJ, 0, 0, (T)1, (T)0, [&](int rr, int k, T& v0, T& v1, T& v2) {
+    phase_push(
+        cl, a, g, L2, K_ADJ, 0, 0, (T)1, (T)0,
+        [&](int rr, int k, T& v0, T& v1, T& v2) {
       const int o = pidx(g, rr, k), ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
@@ -1241,10 +1329,13 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       v1 = c23 * (m.u + dt * Gu);
       v2 = c23 * (m.v + dt * Gv);
       st3(L2, o, P, v0, v1, v2);
-    });
+        },
+        1);
     // lambda_x1 = 1/4 lambda_x2 + 1/4 dt F'(x1)^T lambda_x2   (into X2's buffer)
     T* L1 = X2;
-    phase_push(cl, a, g, L1, K_ADJ, 0, 0, (T)1, (T)0, [&](int rr, int k, T& v0, T& v1, T& v2) {
+    phase_push(
+        cl, a, g, L1, K_ADJ, 0, 0, (T)1, (T)0,
+        [&](int rr, int k, T& v0, T& v1, T& v2) {
       const int o = pidx(g, rr, k), ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
@@ -1259,7 +1350,8 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       v1 = (T)0.25 * (m.u + dt * Gu);
       v2 = (T)0.25 * (m.v + dt * Gv);
       st3(L1, o, P, v0, v1, v2);
-    });
+        },
+        1);
     // lambda(n) = 1/3 lambda' + 3/4 lambda_x2 + lambda_x1 + dt F'(x)^T lambda_x1
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
       const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
