@@ -330,9 +330,10 @@ dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* ctx, int* shape, double* eval_m
 
 /* Force launch shapes (e.g. ones an earlier autotuning run reported), same
  * layout as dd4dv_sweep_config: cluster sizes 1..16 (<= smallest box height),
- * threads a multiple of 32 in 64..512, stored stages 1 only with ckpt_k = 0
- * and the stage buffer present.  Results are the same for every shape up to
- * the order of the per-CTA partial sums of J. */
+ * threads a multiple of 32 in 64..512 (forward sweep of the FP32-state path:
+ * at most 384), stored stages 1 only with ckpt_k = 0 and the stage buffer
+ * present; DD4DV_EINVAL otherwise.  Results are the same for every shape up
+ * to the order of the per-CTA partial sums of J. */
 dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape);
 
 /* The cluster size (CTAs per subdomain) the sweeps use. */

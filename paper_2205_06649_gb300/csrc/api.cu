@@ -569,7 +569,8 @@ void autotune(dd4dv_ctx* ctx) {
     const int R = (ctx->max_ny + c - 1) / c;
     ctx->cl_f = ctx->cl = c;
     ctx->R_f = ctx->R = R;
-    ctx->nt_f = ctx->nthreads = nt;
+    ctx->nthreads = nt;
+    ctx->nt_f = std::min(nt, f32 ? max_threads_forward<float>() : max_threads_forward<double>());
     try {
       by_precision(ctx, [&](auto tt) {
         using T = decltype(tt);
@@ -619,7 +620,7 @@ void autotune(dd4dv_ctx* ctx) {
         spent += tf + ta + tf2 + ta2;
         tf = std::min(tf, tf2);
         ta = std::min(ta, ta2);
-        if (smem_f((ctx->max_ny + c - 1) / c) <= (size_t)cap && tf < best_f[use].t) best_f[use] = {tf, c, nt};
+        if (smem_f((ctx->max_ny + c - 1) / c) <= (size_t)cap && tf < best_f[use].t) best_f[use] = {tf, c, ctx->nt_f};
         if (ta < best_a[use].t) best_a[use] = {ta, c, nt};
       }
   }
@@ -2050,6 +2051,8 @@ dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape) {
         fail(ctx, DD4DV_EINVAL, "cluster sizes must be 1..16 and <= the smallest box height %d", ctx->min_ny);
     for (int t : {tf, ta})
       if (t < 64 || t > 512 || t % 32) fail(ctx, DD4DV_EINVAL, "threads must be a multiple of 32 in 64..512");
+    const int tf_max = ctx->m.precision == 1 ? max_threads_forward<float>() : max_threads_forward<double>();
+    if (tf > tf_max) fail(ctx, DD4DV_EINVAL, "forward sweep threads must be <= %d at this precision", tf_max);
     if (sg && !ctx->stg) fail(ctx, DD4DV_EINVAL, "no stage buffer (ckpt_k != 0 or freed by the autotuner)");
     const int Rf = (ctx->max_ny + cf - 1) / cf, Ra = (ctx->max_ny + ca - 1) / ca;
     const bool f32 = ctx->m.precision == 1;

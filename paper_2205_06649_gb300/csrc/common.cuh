@@ -102,6 +102,11 @@ struct SweepArgs {
   int* err;                   // device error word (0 = ok)
 };
 
+// Largest CTA of the forward sweep: 384 threads on the FP32 path, whose
+// forward kernel is compiled for up to 80 registers (2 CTAs of 384 threads
+// per SM), 512 on the FP64 path (64 registers).
+template <typename T> constexpr int max_threads_forward() { return sizeof(T) == 4 ? 384 : 512; }
+
 // ---- launchers (sweep.cu) ----
 template <typename T> cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);
 template <typename T> cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);

@@ -1103,7 +1103,7 @@ size_t smem_bytes(int nbuf, int R, int W, bool cache) {
 // Forward sweep: x(a) (stored at level 0 by the init kernel) -> x(a+1..b),
 // trajectory stored at every level, J_o and J_mu partial sums per CTA.
 template <typename T>
-__global__ void __launch_bounds__(512, 2) fwd_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(max_threads_forward<T>(), 2) fwd_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;

@@ -115,3 +115,23 @@ def test_gpu_outer_loop_reaches_blue_closed_form():
         j, i = int(ob.fj[k]), int(ob.fi[k])
         expect[0, j, i] = xb[0, j, i] + sb ** 2 * (ob.value[k] - xb[0, j, i]) / (sb ** 2 + so ** 2)
     assert rel(xa - xb, expect - xb) <= 1e-8
+
+
+def test_sweep_shape_limits():
+    """Launch shapes outside the documented limits are refused with EINVAL
+    (FP32-state forward sweep: at most 384 threads per CTA), and a shape at
+    the limit gives the autotuned result up to the order of J's partial sums."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("ragged")
+    st, inp, _ = oracle.build_setup(wl)
+    w = np.concatenate([rand_w(lp.nctrl, seed=700 + s).numpy() for s, lp in enumerate(st.locals)])
+    ctx = make_context(wl, st, inp, precision=1, cluster=2)
+    J0, g0 = ctx.eval(w)
+    for fwd, adj in (((2, 416), (2, 256)), ((2, 256), (2, 544)), ((17, 256), (2, 256)), ((2, 100), (2, 256))):
+        with pytest.raises(dd.DD4DVError) as e:
+            ctx.set_sweep_config(fwd, adj, False)
+        assert e.value.status == -1, (fwd, adj)
+    ctx.set_sweep_config((2, 384), (2, 512), False)
+    J, g = ctx.eval(w)
+    assert rel(J, J0) <= 1e-6 and np.array_equal(g, g0)
+    ctx.destroy()
