@@ -100,6 +100,8 @@ struct SweepArgs {
   int R;                      // max rows per CTA
   int W;                      // shared-memory row pitch (>= max nx + 2)
   int* err;                   // device error word (0 = ok)
+  int tgb_on;                 // set by the launcher: the FP32 sweep's shared memory holds a
+                              // buffer of prefetched overlap targets (only if it still fits)
 };
 
 // Largest CTA of the forward sweep: 384 threads on the FP32 path, whose

@@ -1046,11 +1046,15 @@ __device__ __forceinline__ void store_level(const SweepArgs<T>& a, const Geo<T>&
 }
 
 // The FP32 forward and adjoint sweeps (the ones with a ghost cache) also
-// prefetch overlap targets into one more state-sized buffer.
+// prefetch overlap targets into one more state-sized buffer, when the CTA's
+// shared memory still fits the device's opt-in maximum with it (large boxes
+// in few-CTA clusters read the targets from HBM instead, as the FP64 sweeps
+// do).
 template <typename T>
 __host__ __device__ constexpr bool target_buffer(bool cache) {
   return cache && sizeof(T) == 4;
 }
+constexpr size_t kSmemOptinMax = 232448;   // 227 KB per CTA on sm_100 / sm_103
 
 // Ghost-cache length per slot (FP32 forward / adjoint sweeps only).
 template <typename T>
@@ -1069,7 +1073,7 @@ __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs
   }
   Geo<T>& gt = const_cast<Geo<T>&>(g);
   gt.tgb = nullptr;
-  if (target_buffer<T>(cache)) {
+  if (target_buffer<T>(cache) && a.tgb_on) {
     gt.tgb = p;
     p += g.BUF;
   }
@@ -1093,10 +1097,19 @@ __device__ void carve(const SweepArgs<T>& a, const Geo<T>& g, int nbuf, T** bufs
 }
 
 template <typename T>
-size_t smem_bytes(int nbuf, int R, int W, bool cache) {
-  nbuf += target_buffer<T>(cache) ? 1 : 0;
+size_t smem_bytes_tg(int nbuf, int R, int W, bool cache, bool tg) {
+  nbuf += tg ? 1 : 0;
   return (size_t)nbuf * Lay<T>::NS * (R + 2) * W * sizeof(T) + 16 + 16 * (size_t)(R + 2) * sizeof(T) + 16 +
          64 * sizeof(double) + 3 * (size_t)ghost_len<T>(cache, R, W) * sizeof(T) + 3 * sizeof(int) + 16;
+}
+// whether the sweep with nbuf state buffers carries the target buffer
+template <typename T>
+bool use_target_buffer(int nbuf, int R, int W, bool cache) {
+  return target_buffer<T>(cache) && smem_bytes_tg<T>(nbuf, R, W, cache, true) <= kSmemOptinMax;
+}
+template <typename T>
+size_t smem_bytes(int nbuf, int R, int W, bool cache) {
+  return smem_bytes_tg<T>(nbuf, R, W, cache, use_target_buffer<T>(nbuf, R, W, cache));
 }
 
 // ---------------------------------------------------------------------------
@@ -1590,11 +1603,15 @@ int occupancy_adjoint(int R, int W, int nthreads) {
 
 template <typename T>
 cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
-  return launch_cluster(fwd_kernel<T>, a, cl, nthreads, smem_forward<T>(a.R, a.W), st);
+  SweepArgs<T> b = a;
+  b.tgb_on = use_target_buffer<T>(3, a.R, a.W, true) ? 1 : 0;
+  return launch_cluster(fwd_kernel<T>, b, cl, nthreads, smem_forward<T>(a.R, a.W), st);
 }
 template <typename T>
 cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
-  return launch_cluster(adj_kernel<T>, a, cl, nthreads, smem_adjoint<T>(a.R, a.W), st);
+  SweepArgs<T> b = a;
+  b.tgb_on = use_target_buffer<T>(5, a.R, a.W, true) ? 1 : 0;
+  return launch_cluster(adj_kernel<T>, b, cl, nthreads, smem_adjoint<T>(a.R, a.W), st);
 }
 template <typename T>
 cudaError_t launch_tlm(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
