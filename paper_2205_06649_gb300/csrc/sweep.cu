@@ -138,7 +138,7 @@ __device__ __forceinline__ void st3(T* Z, int o, int P, T h, T u, T v) {
 // constants with two (FP32) or four (FP64) 16-byte loads:
 //   fw[8 i ..]: A, f, tau, B/c, g A, c of row i+1, c of row i-1, 0
 //               (tendencies and tangent-linear tendencies)
-//   bw[8 i ..]: A, f, tau, g A, B c, 1/c of row i+1, 1/c of row i-1, 0
+//   bw[8 i ..]: A, f, tau, g A, B c, 1/c of row i+1, 1/c of row i-1, 2 tau
 //               (adjoint tendencies)
 // Wall ghost rows take the edge row's cos (mirror).
 template <typename T>
@@ -188,7 +188,7 @@ __device__ void load_rows(const SweepArgs<T>& a, const Geo<T>& g, RowSmem<T>& rs
     b[4] = (T)(a.Bth * rc.c);
     b[5] = (T)(1.0 / cn);
     b[6] = (T)(1.0 / cs);
-    b[7] = (T)0;
+    b[7] = (T)(2.0 * rc.tau);
   }
 }
 
@@ -537,34 +537,45 @@ __device__ __forceinline__ void rhs_pt(const Pt5<T>& z, T A, T f, T tau, T BinvC
 // Adjoint of the tendencies: G = F'(Z)^T M at one point (derived by hand from
 // rhs_pt; M holds zero at ghost points that carry no tendency).  Wall rows add
 // the transposed ghost mirror (h, u, -v) of the edge row.
+//   G_u = mu (tau v - A dU_x) - mv (A dV_x + f + 2 tau u) + A (muE uE - muW uW)
+//         + A h (mhE - mhW) + Bth (muN vN - muS vS)
+//   G_v = mu (f + tau u - Bth dU_y) - mv Bth dV_y + A (mvE uE - mvW uW)
+//         + Bth (mvN vN - mvS vS) + (B c) h (mhN / cN - mhS / cS)
+//   G_h = gA (muE - muW) + gBth (mvN - mvS) + A u (mhE - mhW)
+//         + (B c) v (mhN / cN - mhS / cS)
+// evaluated as 42 explicitly rounded operations, 21 of them fused
+// multiply-adds.
 template <typename T, bool DEV>
 __device__ __forceinline__ void rhs_adj_pt(const Pt5<T>& z, const Pt5<T>& m, T A, T f, T tau, T gA, T BcC,
-                                           T icN, T icS, T Bth, T gBth, T href, int wall, T& Gh, T& Gu,
-                                           T& Gv) {
+                                           T icN, T icS, T tau2, T Bth, T gBth, T href, int wall, T& Gh,
+                                           T& Gu, T& Gv) {
   T h = z.h;
   if (DEV) h += href;
   const T u = z.u, v = z.v;
-  const T uE = z.uE, uW = z.uW, uN = z.uN, uS = z.uS;
-  const T vE = z.vE, vW = z.vW, vN = z.vN, vS = z.vS;
   const T mu = m.u, mv = m.v, mh = m.h;
-  const T muE = m.uE, muW = m.uW, muN = m.uN, muS = m.uS;
-  const T mvE = m.vE, mvW = m.vW, mvN = m.vN, mvS = m.vS;
-  const T mhE = m.hE, mhW = m.hW, mhN = m.hN, mhS = m.hS;
-  const T dmhEW = mhE - mhW;
-  const T dmhNS = mhN * icN - mhS * icS;
-  Gu = mu * (tau * v - A * (uE - uW)) - mv * (A * (vE - vW) + f + (T)2 * tau * u) +
-       A * (muE * uE - muW * uW) + A * h * dmhEW + Bth * (muN * vN - muS * vS);
-  Gv = mu * (f + tau * u - Bth * (uN - uS)) - mv * (Bth * (vN - vS)) + A * (mvE * uE - mvW * uW) +
-       Bth * (mvN * vN - mvS * vS) + BcC * h * dmhNS;
-  Gh = gA * (muE - muW) + gBth * (mvN - mvS) + A * u * dmhEW + BcC * v * dmhNS;
+  const T dUx = xsub(z.uE, z.uW), dVx = xsub(z.vE, z.vW);
+  const T dUy = xsub(z.uN, z.uS), dVy = xsub(z.vN, z.vS);
+  const T dmhEW = xsub(m.hE, m.hW);
+  const T dmhNS = xfma(m.hN, icN, -xmul(m.hS, icS));
+  Gh = xfma(xmul(BcC, v), dmhNS,
+            xfma(xmul(A, u), dmhEW, xfma(gBth, xsub(m.vN, m.vS), xmul(gA, xsub(m.uE, m.uW)))));
+  const T a1 = xfma(-A, dUx, xmul(tau, v));
+  const T a2 = xfma(A, dVx, xfma(tau2, u, f));
+  const T p1 = xfma(m.uE, z.uE, -xmul(m.uW, z.uW));
+  const T p2 = xfma(m.uN, z.vN, -xmul(m.uS, z.vS));
+  Gu = xfma(Bth, p2, xfma(xmul(A, h), dmhEW, xfma(A, p1, xfma(-mv, a2, xmul(mu, a1)))));
+  const T b1 = xfma(-Bth, dUy, xfma(tau, u, f));
+  const T q1 = xfma(m.vE, z.uE, -xmul(m.vW, z.uW));
+  const T q2 = xfma(m.vN, z.vN, -xmul(m.vS, z.vS));
+  Gv = xfma(xmul(BcC, h), dmhNS, xfma(Bth, q2, xfma(A, q1, xfma(-mv, xmul(Bth, dVy), xmul(mu, b1)))));
   if (wall == 1) {         // south wall: ghost row = (h, u, -v) of this row
-    Gu += Bth * mu * v;
-    Gv -= Bth * (mv * v + h * mh);
-    Gh += gBth * mv - Bth * v * mh;
+    Gu = xfma(xmul(Bth, mu), v, Gu);
+    Gv = xfma(-Bth, xfma(mv, v, xmul(h, mh)), Gv);
+    Gh = xfma(gBth, mv, xfma(-Bth, xmul(v, mh), Gh));
   } else if (wall == 2) {  // north wall
-    Gu -= Bth * mu * v;
-    Gv += Bth * (mv * v + h * mh);
-    Gh += Bth * v * mh - gBth * mv;
+    Gu = xfma(-xmul(Bth, mu), v, Gu);
+    Gv = xfma(Bth, xfma(mv, v, xmul(h, mh)), Gv);
+    Gh = xfma(Bth, xmul(v, mh), xfma(-gBth, mv, Gh));
   }
 }
 
@@ -833,9 +844,14 @@ __device__ __forceinline__ void stage_point(const SweepArgs<T>& a, const Geo<T>&
   Pt5<T> y;
   load5(Y, o, P, Lay<T>::CS, g.RS, y);
   rhs_pt<T, DEV>(y, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, Fh, Fu, Fv);
-  o0 = xmul(cy, xfma(dt, Fh, y.h));
-  o1 = xmul(cy, xfma(dt, Fu, y.u));
-  o2 = xmul(cy, xfma(dt, Fv, y.v));
+  o0 = xfma(dt, Fh, y.h);
+  o1 = xfma(dt, Fu, y.u);
+  o2 = xfma(dt, Fv, y.v);
+  if (cy != (T)1) {
+    o0 = xmul(cy, o0);
+    o1 = xmul(cy, o1);
+    o2 = xmul(cy, o2);
+  }
   if (cx != (T)0) {
     T xh, xu, xv;
     ld3(X, o, P, xh, xu, xv);
@@ -1261,7 +1277,7 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   const bool pre_tg = g.tgb && a.mu != 0.0 && !a.gn_dx && !a.yforce;
   for (int i = threadIdx.x; i < g.BUF; i += blockDim.x) Lp[i] = (T)0;
   const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
-  const T c23 = (T)(2.0 / 3.0), c13 = (T)(1.0 / 3.0);
+  const T c13 = (T)(1.0 / 3.0), c16 = (T)(1.0 / 6.0);
   const int wall_s = (g.flags & F_SWALL) ? 1 : 0;
   const int wall_n = (g.flags & F_NWALL) ? 2 : 0;
   const size_t lvl_sz = (size_t)3 * g.ny * g.d.nxp;
@@ -1324,7 +1340,13 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
     cp_async_commit();
     const int P = g.P;
     constexpr int CS = Lay<T>::CS;
-    // lambda_x2 = 2/3 lambda' + 2/3 dt F'(x2)^T lambda'
+    // The transposed RK3 step with the stage adjoints scaled so that no stage
+    // needs its own multiplication (G_k is linear in its argument):
+    //   lambda_x2 = 2/3 mu2,  mu2 = lambda' + dt F'(x2)^T lambda'
+    //   lambda_x1 = 1/6 mu1,  mu1 = mu2 + dt F'(x1)^T mu2
+    //   lambda(n) = 1/3 lambda' + 3/4 lambda_x2 + lambda_x1 + dt F'(x)^T lambda_x1
+    //             = 1/3 lambda' + 1/2 mu2 + 1/6 (mu1 + dt F'(x)^T mu1)
+    // mu2 (into L2)
     phase_push(
         cl, a, g, L2, K_ADJ, 0, 0, (T)1, (T)0,
         [&](int rr, int k, T& v0, T& v1, T& v2) {
@@ -1336,15 +1358,15 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       Pt5<T> z, m;
       load5(X2, o, P, CS, g.RS, z);
       load5(Lp, o, P, CS, g.RS, m);
-      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, wall, Gh, Gu,
+      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], rc[7], Bth, gBth, href, wall, Gh, Gu,
                          Gv);
-      v0 = c23 * (m.h + dt * Gh);
-      v1 = c23 * (m.u + dt * Gu);
-      v2 = c23 * (m.v + dt * Gv);
+      v0 = xfma(dt, Gh, m.h);
+      v1 = xfma(dt, Gu, m.u);
+      v2 = xfma(dt, Gv, m.v);
       st3(L2, o, P, v0, v1, v2);
         },
         1);
-    // lambda_x1 = 1/4 lambda_x2 + 1/4 dt F'(x1)^T lambda_x2   (into X2's buffer)
+    // mu1 (into X2's buffer)
     T* L1 = X2;
     phase_push(
         cl, a, g, L1, K_ADJ, 0, 0, (T)1, (T)0,
@@ -1357,15 +1379,15 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       Pt5<T> z, m;
       load5(X1, o, P, CS, g.RS, z);
       load5(L2, o, P, CS, g.RS, m);
-      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, wall, Gh, Gu,
+      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], rc[7], Bth, gBth, href, wall, Gh, Gu,
                          Gv);
-      v0 = (T)0.25 * (m.h + dt * Gh);
-      v1 = (T)0.25 * (m.u + dt * Gu);
-      v2 = (T)0.25 * (m.v + dt * Gv);
+      v0 = xfma(dt, Gh, m.h);
+      v1 = xfma(dt, Gu, m.u);
+      v2 = xfma(dt, Gv, m.v);
       st3(L1, o, P, v0, v1, v2);
         },
         1);
-    // lambda(n) = 1/3 lambda' + 3/4 lambda_x2 + lambda_x1 + dt F'(x)^T lambda_x1
+    // lambda(n)
     for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
       const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
       const int o = pidx(g, rr, k), ri = rr + 1;
@@ -1376,13 +1398,14 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       Pt5<T> z, m;
       load5(X, o, P, CS, g.RS, z);
       load5(L1, o, P, CS, g.RS, m);
-      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, wall, Gh, Gu,
+      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], rc[7], Bth, gBth, href, wall, Gh, Gu,
                          Gv);
       T ph, pu, pv, qh, qu, qv;
       ld3(Lp, o, P, ph, pu, pv);
       ld3(L2, o, P, qh, qu, qv);
-      st3(Lp, o, P, c13 * ph + (T)0.75 * qh + m.h + dt * Gh, c13 * pu + (T)0.75 * qu + m.u + dt * Gu,
-          c13 * pv + (T)0.75 * qv + m.v + dt * Gv);
+      st3(Lp, o, P, xfma(c16, xfma(dt, Gh, m.h), xfma((T)0.5, qh, xmul(c13, ph))),
+          xfma(c16, xfma(dt, Gu, m.u), xfma((T)0.5, qu, xmul(c13, pu))),
+          xfma(c16, xfma(dt, Gv, m.v), xfma((T)0.5, qv, xmul(c13, pv))));
     }
     __syncthreads();
     add_forcing(a, g, Lp, X, l);
