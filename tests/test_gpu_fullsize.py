@@ -97,6 +97,30 @@ def test_batching_workload_properties_at_full_size():
     assert worst <= 1e-12, worst
 
 
+def test_fp32_target_buffer_paths_agree_at_batching_size():
+    """FP32 state on the batching workload (512 uneven subdomains, boxes of
+    about 176 x 91 points): in 8-CTA clusters the adjoint sweep's shared
+    memory has no room for the prefetched overlap targets, so it reads them
+    from HBM; in 16-CTA clusters it reads them from the shared buffer.  The
+    gradients agree bit for bit, J up to the order of its FP32 partial sums."""
+    wl = workloads.preset("batching")
+    inp = workloads.generate(wl)
+    so = np.asarray(wl.sigma_o)[inp["obs_var"]]
+    y = np.where(inp["obs_var"] == 0, workloads.H_REF, 0.0) + so * inp["obs_noise"]
+    ctx = _lib_ctx(wl, inp, y, so, 1, cluster=0)
+    assert ctx.n_sub == 512
+    w = 0.3 * np.random.default_rng(11).standard_normal(ctx.ctrl_total)
+    res = []
+    for shape in ((8, 384), (16, 384)):
+        ctx.set_sweep_config(shape, shape, False)
+        res.append(ctx.eval(w))
+    (J8, g8), (J16, g16) = res
+    assert np.all(np.isfinite(J8)) and np.all(J8 > 0)
+    assert rel(J8, J16) <= 1e-6
+    assert np.array_equal(g8, g16)
+    ctx.destroy()
+
+
 def test_large_workload_fits_and_satisfies_properties_at_full_size():
     """2048 uneven subdomains of the 2048 x 1024 / 1024-step workload (3.3e9
     pt-steps per evaluation) in one launch per sweep, FP64: the context fits
