@@ -1181,6 +1181,32 @@ __global__ void __launch_bounds__(max_threads_forward<T>(), 2) fwd_kernel(SweepA
   cl.sync();   // keep shared memory alive until every neighbour is done with it
 }
 
+// Overlap forcing mu c (x - m) / sb^2 of own point (rr, k) with overlap count
+// c, added to (l0, l1, l2) with explicit rounding: the same arithmetic in
+// add_forcing and in the fused lambda(n) phase of the adjoint sweep.  The
+// targets m come from the shared target buffer when there is one (its
+// copies have landed), else from HBM.
+template <typename T>
+__device__ __forceinline__ void overlap_force(const SweepArgs<T>& a, const Geo<T>& g, const T* X, const T* tg,
+                                              int rr, int k, int c, T& l0, T& l1, T& l2) {
+  const int o = pidx(g, rr, k);
+  T x0, x1, x2, t0, t1, t2;
+  ld3(X, o, g.P, x0, x1, x2);
+  if (g.tgb) {
+    ld3(g.tgb, o, g.P, t0, t1, t2);
+  } else {
+    const size_t pl = (size_t)g.ny * g.d.nxp;
+    const size_t go = (size_t)(g.R0 + rr) * g.d.nxp + k;
+    t0 = tg[go];
+    t1 = tg[go + pl];
+    t2 = tg[go + 2 * pl];
+  }
+  const T cc = (T)c;
+  l0 = xfma(xmul(cc, a.musb2_s[0]), xsub(x0, t0), l0);
+  l1 = xfma(xmul(cc, a.musb2_s[1]), xsub(x1, t1), l1);
+  l2 = xfma(xmul(cc, a.musb2_s[2]), xsub(x2, t2), l2);
+}
+
 // Forcing of the adjoint at level l on own rows: observation scatter (H^T of
 // lambda w d, fixed order per target) and overlap term mu c (x - m)/sb^2, or an
 // external forcing y.  L holds the adjoint state, X the state at that level.
@@ -1214,24 +1240,13 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
     });
   } else if ((any_t || any_s) && a.mu != 0.0) {
     const T* tg = a.tgt + d.traj_off + (size_t)l * 3 * g.ny * d.nxp;
-    const T m0 = a.musb2_s[0], m1 = a.musb2_s[1], m2 = a.musb2_s[2];
-    const size_t pl = (size_t)g.ny * d.nxp;
     if (g.tgb) cp_async_wait_all();   // this thread's prefetched targets
     for_overlap_points(g, l, [&](int rr, int k, int c) {
-      const T cc = (T)c;
       const int o = pidx(g, rr, k);
-      T l0, l1, l2, x0, x1, x2, t0, t1, t2;
+      T l0, l1, l2;
       ld3(Lb, o, g.P, l0, l1, l2);
-      ld3(X, o, g.P, x0, x1, x2);
-      if (g.tgb) {
-        ld3(g.tgb, o, g.P, t0, t1, t2);
-      } else {
-        const size_t go = (size_t)(g.R0 + rr) * d.nxp + k;
-        t0 = tg[go];
-        t1 = tg[go + pl];
-        t2 = tg[go + 2 * pl];
-      }
-      st3(Lb, o, g.P, l0 + cc * m0 * (x0 - t0), l1 + cc * m1 * (x1 - t1), l2 + cc * m2 * (x2 - t2));
+      overlap_force(a, g, X, tg, rr, k, c, l0, l1, l2);
+      st3(Lb, o, g.P, l0, l1, l2);
     });
   }
   __syncthreads();
@@ -1386,10 +1401,9 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       v2 = xfma(dt, Gv, m.v);
       st3(L1, o, P, v0, v1, v2);
         },
-        1);
+        0);   // the prefetched targets land before the next phase reads them
     // lambda(n)
-    for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
-      const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+    const auto lam_n = [&](int rr, int k, T& v0, T& v1, T& v2) {
       const int o = pidx(g, rr, k), ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
       T Gh, Gu, Gv;
@@ -1403,13 +1417,39 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       T ph, pu, pv, qh, qu, qv;
       ld3(Lp, o, P, ph, pu, pv);
       ld3(L2, o, P, qh, qu, qv);
-      st3(Lp, o, P, xfma(c16, xfma(dt, Gh, m.h), xfma((T)0.5, qh, xmul(c13, ph))),
-          xfma(c16, xfma(dt, Gu, m.u), xfma((T)0.5, qu, xmul(c13, pu))),
-          xfma(c16, xfma(dt, Gv, m.v), xfma((T)0.5, qv, xmul(c13, pv))));
+      v0 = xfma(c16, xfma(dt, Gh, m.h), xfma((T)0.5, qh, xmul(c13, ph)));
+      v1 = xfma(c16, xfma(dt, Gu, m.u), xfma((T)0.5, qu, xmul(c13, pu)));
+      v2 = xfma(c16, xfma(dt, Gv, m.v), xfma((T)0.5, qv, xmul(c13, pv)));
+    };
+    // With no external forcing, no Gauss-Newton product and no observation
+    // at this level, lambda(n) takes its overlap forcing point by point and
+    // pushes its halo in the same phase (the arithmetic of add_forcing,
+    // without its passes and barriers).  Every CTA of the cluster takes the
+    // same branch: the conditions belong to the subdomain.
+    const SubDesc& d = g.d;
+    const bool fuse = !a.yforce && !a.gn_dx && a.lvl_sc[d.sc_lvl + l] == a.lvl_sc[d.sc_lvl + l + 1];
+    if (fuse) {
+      const bool ovl = a.mu != 0.0 && ((l < d.tA) || (l > g.L - d.tB) || d.wL || d.wR || d.wS || d.wN);
+      const T* tg = a.tgt + d.traj_off + (size_t)l * lvl_sz;
+      phase_push(cl, a, g, Lp, K_ADJ, 0, 0, (T)1, (T)0, [&](int rr, int k, T& v0, T& v1, T& v2) {
+        lam_n(rr, k, v0, v1, v2);
+        if (ovl) {
+          const int c = overlap_count(g, l, g.R0 + rr, k);
+          if (c) overlap_force(a, g, X, tg, rr, k, c, v0, v1, v2);
+        }
+        st3(Lp, pidx(g, rr, k), P, v0, v1, v2);
+      });
+    } else {
+      for (int idx = threadIdx.x; idx < g.Rn * g.nx; idx += blockDim.x) {
+        const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+        T v0, v1, v2;
+        lam_n(rr, k, v0, v1, v2);
+        st3(Lp, pidx(g, rr, k), P, v0, v1, v2);
+      }
+      __syncthreads();
+      add_forcing(a, g, Lp, X, l);
+      push_halos(cl, a, g, Lp, K_ADJ);
     }
-    __syncthreads();
-    add_forcing(a, g, Lp, X, l);
-    push_halos(cl, a, g, Lp, K_ADJ);
   }
   }
   // lambda(a) -> packed control layout (FP64)
