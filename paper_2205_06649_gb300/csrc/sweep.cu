@@ -5,13 +5,16 @@
 // cluster's CTAs split the subdomain's box into horizontal stripes of rows;
 // each CTA keeps its stripe of the state (plus one halo row on each side and
 // a ghost column on each side) resident in shared memory for the whole time
-// window.  After every RK3 stage the CTAs barrier on the cluster and read
-// their neighbours' edge rows through distributed shared memory
-// (ld.shared::cluster via cooperative_groups::cluster_group::map_shared_rank),
-// so the only HBM traffic of a step is the trajectory store (forward), the
-// trajectory load (adjoint), ghost values of the frozen boundary trajectory
-// and the sparse observation / overlap data.  Clusters are ordered longest
-// subdomain first (uneven sizes in one launch).
+// window.  Each RK3 stage is one cluster barrier phase: a CTA computes its
+// edge rows first and stores them straight into its neighbours' halo rows
+// through distributed shared memory, arrives at the cluster barrier, computes
+// its interior rows while the barrier completes, and waits (the pushed halo
+// exchange of phase_push).  The only HBM traffic of a step is the trajectory
+// (and stage-state) store in the forward sweep and load in the adjoint sweep,
+// ghost values of the frozen boundary trajectory (prefetched with cp.async on
+// the FP32 path) and the sparse observation / overlap data.  FP32 buffers
+// hold one 16-byte (h, u, v, 0) slot per point, FP64 buffers three planes.
+// Clusters are ordered longest subdomain first (uneven sizes in one launch).
 //
 // Mathematics (paper arXiv 2205.06649):
 //   model      Sec. 7 Eqs. EquU-EquH, centred differences, flux-form
