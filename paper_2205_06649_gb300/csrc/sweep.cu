@@ -772,11 +772,13 @@ __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X
 }
 
 // Copies the overlap targets of level l at this CTA's overlap points into the
-// shared target buffer (FP32 sweeps) with cp.async, a few phases before
-// overlap_level or add_forcing read them.  Each point is copied and later
-// read by the same thread (the same for_overlap_points mapping), so that
-// thread's own cp.async wait is all the synchronisation the read needs.  The
-// copies join the caller's next commit group.
+// shared target buffer (FP32 sweeps) with cp.async, a few phases before they
+// are read.  overlap_level and add_forcing read each point on the thread that
+// copied it (the same for_overlap_points mapping), so that thread's own
+// cp.async wait is all the synchronisation they need; the adjoint's fused
+// lambda(n) phase reads them on any thread, after a phase that waited for all
+// copies and ended with a barrier.  The copies join the caller's next commit
+// group.
 template <typename T>
 __device__ void prefetch_targets(const SweepArgs<T>& a, const Geo<T>& g, int l) {
   if (!g.tgb) return;
