@@ -140,6 +140,12 @@ PRESETS: Dict[str, Workload] = {
     "large": Workload("large", 2048, 1024, 1024, 16, 16, 8, 8, 8, 8, uneven=True,
                       obs_kind="random", obs_vars=(0, 1, 2), obs_count=1000000,
                       obs_every=4, corr_len=3.0),
+    # One 64-step window of the batching decomposition (8x8 uneven boxes of
+    # up to 179 x 85 points, 1/8 of its observations): a case of a few GB for
+    # ncu captures of the sweeps in the batching workload's launch shapes.
+    "batching_window": Workload("batching_window", 1024, 512, 64, 8, 8, 1, 4, 4, 8, uneven=True,
+                                obs_kind="random", obs_vars=(0, 1, 2), obs_count=12500,
+                                obs_every=8),
     # A mid-size parity case: several tiles, ragged (non-power-of-two) boxes,
     # uneven cuts, random fractional observations and a recursive-filter B.
     "ragged": Workload("ragged", 70, 38, 30, 3, 2, 3, 3, 2, 3, uneven=True,
