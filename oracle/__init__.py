@@ -9,6 +9,8 @@ from the separate ``workloads`` module, which holds no method arithmetic.
 
 Plain, slow, FP64 PyTorch-CPU code written from the paper:
   swe.py            shallow-water model and SSP-RK3 step (Sec. 7)
+  tz.py             the Turkel-Zwas stencil of Sec. 7 (p, q strides, alpha
+                    averaging), global domain only; no GPU counterpart yet
   decomposition.py  space-time decomposition, restriction weights (Sec. 3.1-3.2)
   bcov.py           B = V V^T, diagonal or recursive filter (Sec. 4, Eq. EqV)
   local.py          local functional J_s, gradient, TLM (Sec. 3.3, Alg. 6)
@@ -32,3 +34,4 @@ from .lbfgs import lbfgs, LbfgsResult  # noqa: F401
 from .gauss_newton import residuals, gn_operator, gn_hessvec, cg, gauss_newton, CgResult, GnResult  # noqa: F401
 from .dd4dvar import dd4dvar, global_J, rmse, DDResult  # noqa: F401
 from .problem import build_setup  # noqa: F401
+from .tz import tz_rhs, tz_forward  # noqa: F401
