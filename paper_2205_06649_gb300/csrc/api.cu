@@ -322,8 +322,13 @@ void apply_VT(dd4dv_ctx* ctx, const double* y, const double* w, const double* sc
               const int* active, int av) {
   if (fused_v(ctx)) {
     RFArgs ra{ctx->subs_d, ctx->n_sub, ctx->rf_alpha, ctx->rf_c, ctx->rf_passes, active, av};
-    KL(launch_vgrad(ctx->subs_d, ctx->n_sub, w, y, ctx->sigma_d, ra, ctx->corr_len > 0.0 ? 1 : 0, scale, out,
-                    active, av, max_plane(ctx), ctx->st));
+    const int rf = ctx->corr_len > 0.0 ? 1 : 0;
+    if (ctx->m.precision == 1)
+      KL(launch_vgrad<float>(ctx->subs_d, ctx->n_sub, w, y, ctx->sigma_d, ra, rf, scale, out, active, av,
+                             max_plane(ctx), ctx->st));
+    else
+      KL(launch_vgrad<double>(ctx->subs_d, ctx->n_sub, w, y, ctx->sigma_d, ra, rf, scale, out, active, av,
+                              max_plane(ctx), ctx->st));
     return;
   }
   KL(launch_scale_copy(ctx->subs_d, ctx->n_sub, y, ctx->sigma_d, ctx->vw2, active, av, ctx->max_pts, ctx->st));

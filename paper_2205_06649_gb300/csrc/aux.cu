@@ -616,16 +616,21 @@ __global__ void finite_check_kernel(const double* a, long long n, int* flag) {
 //   forward (V):   x(a) = x_b(a) + sigma_v L_lat L_lon w  -> trajectory level 0
 //   adjoint (V^T): grad = scale_s (w + L_lon L_lat (sigma_v y))
 // Rows (lon lines) are filtered by one thread per row, columns by one thread
-// per column, in the same operation order as the separate kernels.
-__device__ void rf_line_smem(double* x, int n, int stride, double alpha, double c, int npass) {
-  const double b = 1.0 - alpha;
+// per column, in the same operation order as the separate kernels.  The
+// filter runs in the state precision R: FP64 on the FP64 path; on the
+// FP32-state path in FP32, since L w only feeds an initial state that is
+// stored in FP32 and L^T acts on an adjoint state computed in FP32 (the
+// control, x_b, w and the gradient stay FP64).
+template <typename R>
+__device__ void rf_line_smem(R* x, int n, int stride, R alpha, R c, int npass) {
+  const R b = (R)1 - alpha;
   for (int p = 0; p < npass; ++p) {
-    double q = 0.0;
+    R q = (R)0;
     for (int i = 0; i < n; ++i) {
       q = alpha * q + b * x[i * stride];
       x[i * stride] = q;
     }
-    q = 0.0;
+    q = (R)0;
     for (int i = n - 1; i >= 0; --i) {
       q = alpha * q + b * x[i * stride];
       x[i * stride] = q;
@@ -634,11 +639,13 @@ __device__ void rf_line_smem(double* x, int n, int stride, double alpha, double 
   for (int i = 0; i < n; ++i) x[i * stride] *= c;
 }
 
+extern __shared__ __align__(16) unsigned char smem_plane[];
+
 template <typename T>
 __global__ void vinit_kernel(const SubDesc* subs, const double* xb_a, const double* w, const double* sigma,
                              RFArgs rf, int use_rf, double h_ref, T* traj, const int* active,
                              int active_value) {
-  extern __shared__ double pl[];
+  T* pl = reinterpret_cast<T*>(smem_plane);
   const int s = blockIdx.x, v = blockIdx.y;
   if (!is_active(active, active_value, s)) return;
   const SubDesc d = subs[s];
@@ -647,13 +654,14 @@ __global__ void vinit_kernel(const SubDesc* subs, const double* xb_a, const doub
   const double* src = w + d.ctrl_off + (size_t)v * n;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int r = i / d.nx, k = i - r * d.nx;
-    pl[r * pitch + k] = src[i];
+    pl[r * pitch + k] = (T)src[i];
   }
   __syncthreads();
   if (use_rf) {
-    for (int r = threadIdx.x; r < d.ny; r += blockDim.x) rf_line_smem(pl + r * pitch, d.nx, 1, rf.alpha, rf.c, rf.npass);
+    const T al = (T)rf.alpha, c = (T)rf.c;
+    for (int r = threadIdx.x; r < d.ny; r += blockDim.x) rf_line_smem(pl + r * pitch, d.nx, 1, al, c, rf.npass);
     __syncthreads();
-    for (int k = threadIdx.x; k < d.nx; k += blockDim.x) rf_line_smem(pl + k, d.ny, pitch, rf.alpha, rf.c, rf.npass);
+    for (int k = threadIdx.x; k < d.nx; k += blockDim.x) rf_line_smem(pl + k, d.ny, pitch, al, c, rf.npass);
     __syncthreads();
   }
   const double sg = sigma[v];
@@ -661,16 +669,17 @@ __global__ void vinit_kernel(const SubDesc* subs, const double* xb_a, const doub
   T* dst = traj + d.traj_off + (size_t)v * d.ny * d.nxp;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int r = i / d.nx, k = i - r * d.nx;
-    double x = xb[i] + sg * pl[r * pitch + k];
+    double x = xb[i] + sg * (double)pl[r * pitch + k];
     if (v == 0) x -= h_ref;
     dst[(size_t)r * d.nxp + k] = (T)x;
   }
 }
 
+template <typename R>
 __global__ void vgrad_kernel(const SubDesc* subs, const double* w, const double* y, const double* sigma,
                              RFArgs rf, int use_rf, const double* scale, double* grad, const int* active,
                              int active_value) {
-  extern __shared__ double pl[];
+  R* pl = reinterpret_cast<R*>(smem_plane);
   const int s = blockIdx.x, v = blockIdx.y;
   if (!is_active(active, active_value, s)) return;
   const SubDesc d = subs[s];
@@ -680,19 +689,20 @@ __global__ void vgrad_kernel(const SubDesc* subs, const double* w, const double*
   const double sg = sigma[v];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int r = i / d.nx, k = i - r * d.nx;
-    pl[r * pitch + k] = sg * y[o + i];
+    pl[r * pitch + k] = (R)(sg * y[o + i]);
   }
   __syncthreads();
   if (use_rf) {
-    for (int k = threadIdx.x; k < d.nx; k += blockDim.x) rf_line_smem(pl + k, d.ny, pitch, rf.alpha, rf.c, rf.npass);
+    const R al = (R)rf.alpha, c = (R)rf.c;
+    for (int k = threadIdx.x; k < d.nx; k += blockDim.x) rf_line_smem(pl + k, d.ny, pitch, al, c, rf.npass);
     __syncthreads();
-    for (int r = threadIdx.x; r < d.ny; r += blockDim.x) rf_line_smem(pl + r * pitch, d.nx, 1, rf.alpha, rf.c, rf.npass);
+    for (int r = threadIdx.x; r < d.ny; r += blockDim.x) rf_line_smem(pl + r * pitch, d.nx, 1, al, c, rf.npass);
     __syncthreads();
   }
   const double sc = scale ? scale[s] : 1.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int r = i / d.nx, k = i - r * d.nx;
-    const double gv = (w ? w[o + i] : 0.0) + pl[r * pitch + k];
+    const double gv = (w ? w[o + i] : 0.0) + (double)pl[r * pitch + k];
     grad[o + i] = scale ? sc * gv : gv;
   }
 }
@@ -710,7 +720,7 @@ template <typename T>
 cudaError_t launch_vinit(const SubDesc* subs, int n_sub, const double* xb_a, const double* w,
                          const double* sigma, const RFArgs& rf, int use_rf, double h_ref, T* traj,
                          const int* active, int active_value, int max_plane, cudaStream_t st) {
-  const size_t smem = (size_t)max_plane * sizeof(double);
+  const size_t smem = (size_t)max_plane * sizeof(T);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(vinit_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
@@ -722,18 +732,19 @@ cudaError_t launch_vinit(const SubDesc* subs, int n_sub, const double* xb_a, con
   return cudaGetLastError();
 }
 
+template <typename R>
 cudaError_t launch_vgrad(const SubDesc* subs, int n_sub, const double* w, const double* y, const double* sigma,
                          const RFArgs& rf, int use_rf, const double* scale, double* grad, const int* active,
                          int active_value, int max_plane, cudaStream_t st) {
-  const size_t smem = (size_t)max_plane * sizeof(double);
+  const size_t smem = (size_t)max_plane * sizeof(R);
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(vgrad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+    cudaError_t e = cudaFuncSetAttribute(vgrad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  vgrad_kernel<<<dim3(n_sub, 3), 256, smem, st>>>(subs, w, y, sigma, rf, use_rf, scale, grad, active,
-                                                  active_value);
+  vgrad_kernel<R><<<dim3(n_sub, 3), 256, smem, st>>>(subs, w, y, sigma, rf, use_rf, scale, grad, active,
+                                                     active_value);
   return cudaGetLastError();
 }
 
@@ -993,6 +1004,9 @@ cudaError_t launch_finite_check(const double* a, long long n, int* flag, cudaStr
 }
 
 #define DD4DV_INST(T)                                                                              \
+  template cudaError_t launch_vgrad<T>(const SubDesc*, int, const double*, const double*,           \
+                                       const double*, const RFArgs&, int, const double*, double*,  \
+                                       const int*, int, int, cudaStream_t);                        \
   template cudaError_t launch_vinit<T>(const SubDesc*, int, const double*, const double*,           \
                                        const double*, const RFArgs&, int, double, T*, const int*,  \
                                        int, int, cudaStream_t);                                    \

@@ -134,6 +134,8 @@ template <typename T>
 cudaError_t launch_vinit(const SubDesc* subs, int n_sub, const double* xb_a, const double* w,
                          const double* sigma, const RFArgs& rf, int use_rf, double h_ref, T* traj,
                          const int* active, int active_value, int max_plane, cudaStream_t st);
+// R = precision of the recursive filter (the state precision)
+template <typename R>
 cudaError_t launch_vgrad(const SubDesc* subs, int n_sub, const double* w, const double* y, const double* sigma,
                          const RFArgs& rf, int use_rf, const double* scale, double* grad, const int* active,
                          int active_value, int max_plane, cudaStream_t st);
