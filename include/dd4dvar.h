@@ -52,7 +52,10 @@ typedef enum {
   DD4DV_ENOMEM = -2,       /* device or pinned host allocation failed      */
   DD4DV_ECUDA = -3,        /* CUDA runtime error (message has the details) */
   DD4DV_ESTATE = -4,       /* call made before its prerequisites           */
-  DD4DV_ETIMEOUT = -5,     /* a bounded device wait ran out                */
+  DD4DV_ETIMEOUT = -5,     /* reserved, never returned: no kernel of this
+                              library spin-waits (the sweeps synchronise
+                              only through hardware cluster barriers), so
+                              there is no bounded wait that could run out  */
   DD4DV_ENONFINITE = -6,   /* NaN or Inf in an input                       */
   DD4DV_NOTCONV = 1        /* warning: stopping test not met, outputs valid */
 } dd4dv_status;
@@ -351,19 +354,20 @@ dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* ctx, int* n);
  *   x0: device pointer, [3][nlat][nlon] initial state.
  *   traj: device pointer, [nsteps+1][3][nlat][nlon] output (caller-owned).
  *   cuda_stream: cudaStream_t to order the work on (NULL = legacy stream).
- *     The call waits once for the work already queued on that stream (it
- *     copies the grid constants from the host), then enqueues the model run
- *     and returns without waiting for it.
+ *     The call enqueues the whole run on that stream (a kernel that computes
+ *     the grid constants, then the RK3 stages) and returns without waiting:
+ *     it makes no host copy and no stream or device synchronisation.
  * Limit: 3*nlat*nlon <= 393216 doubles (e.g. 512 x 256 points) and
  * nlat <= 1024; larger grids return DD4DV_EINVAL.  Errors: EINVAL, ECUDA;
  * the message is dd4dv_last_error(NULL).
- * Scratch: the two RK3 stage states live in a fixed 6.3 MB __device__
- * array of the library that every GPU which loads the library keeps until
- * the process exits.  The first call on a device (with that device current)
- * looks up the array's device address; make that first call before any
- * stream capture.  All calls on a device share the array, so calls whose
- * work overlaps on the GPU (other streams, other threads) race and must be
- * ordered by the caller. */
+ * Scratch: the two RK3 stage states and the grid constants live in a fixed
+ * 6.3 MB __device__ array of the library that every GPU which loads the
+ * library keeps until the process exits.  The first call on a device (with
+ * that device current) looks up the array's device address and keeps it for
+ * the life of the process; make that first call before any stream capture.
+ * A device reset (cudaDeviceReset) after it is not supported.  All calls on
+ * a device share the array, so calls whose work overlaps on the GPU (other
+ * streams, other threads) race and must be ordered by the caller. */
 dd4dv_status dd4dv_forward_noalloc(const dd4dv_model* model, const double* x0, double* traj,
                                    void* cuda_stream);
 

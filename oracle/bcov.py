@@ -100,9 +100,3 @@ class BOp:
         if self.ell <= 0.0:
             return self.sigma * w
         return self.sigma * (self.Llat @ (w @ self.Llon.T))
-
-    def apply_T(self, y: torch.Tensor) -> torch.Tensor:
-        """V^T y."""
-        if self.ell <= 0.0:
-            return self.sigma * y
-        return self.Llat.T @ ((self.sigma * y) @ self.Llon)

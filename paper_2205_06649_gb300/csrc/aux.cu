@@ -6,6 +6,9 @@
 #include "common.cuh"
 
 #include <cfloat>
+#include <mutex>
+#include <set>
+#include <utility>
 
 namespace dd4dv {
 
@@ -707,6 +710,25 @@ __global__ void vgrad_kernel(const SubDesc* subs, const double* w, const double*
   }
 }
 
+// Raises a kernel's dynamic shared-memory cap to the 227 KB opt-in maximum,
+// once per (kernel, device): the attribute belongs to the device current at
+// the call, so a context on another device sets it again.
+template <typename K>
+cudaError_t raise_smem_cap(K kernel) {
+  static std::mutex mu;
+  static std::set<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  const std::pair<const void*, int> key{reinterpret_cast<const void*>(kernel), dev};
+  if (done.count(key)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
+  if (e != cudaSuccess) return e;
+  done.insert(key);
+  return cudaSuccess;
+}
+
 inline unsigned blocks_for(long long n, int t, int cap = 152 * 16) {
   long long b = (n + t - 1) / t;
   if (b < 1) b = 1;
@@ -721,12 +743,8 @@ cudaError_t launch_vinit(const SubDesc* subs, int n_sub, const double* xb_a, con
                          const double* sigma, const RFArgs& rf, int use_rf, double h_ref, T* traj,
                          const int* active, int active_value, int max_plane, cudaStream_t st) {
   const size_t smem = (size_t)max_plane * sizeof(T);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(vinit_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = raise_smem_cap(vinit_kernel<T>);
+  if (e != cudaSuccess) return e;
   vinit_kernel<T><<<dim3(n_sub, 3), 256, smem, st>>>(subs, xb_a, w, sigma, rf, use_rf, h_ref, traj, active,
                                                       active_value);
   return cudaGetLastError();
@@ -737,12 +755,8 @@ cudaError_t launch_vgrad(const SubDesc* subs, int n_sub, const double* w, const 
                          const RFArgs& rf, int use_rf, const double* scale, double* grad, const int* active,
                          int active_value, int max_plane, cudaStream_t st) {
   const size_t smem = (size_t)max_plane * sizeof(R);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(vgrad_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  cudaError_t e = raise_smem_cap(vgrad_kernel<R>);
+  if (e != cudaSuccess) return e;
   vgrad_kernel<R><<<dim3(n_sub, 3), 256, smem, st>>>(subs, w, y, sigma, rf, use_rf, scale, grad, active,
                                                      active_value);
   return cudaGetLastError();

@@ -15,7 +15,11 @@
 // every GPU which loads this library keeps until the process exits.  The
 // device address of that array is looked up once per device with
 // cudaGetSymbolAddress on the first call made with that device current; that
-// first call should therefore come before any stream capture.  All calls on a
+// first call should therefore come before any stream capture.  The address is
+// kept for the life of the process, so a device reset (cudaDeviceReset)
+// after that first call is not supported.  The grid constants are computed
+// by a kernel on the caller's stream, so a call only enqueues work: it makes
+// no host copy and no stream or device synchronisation.  All calls on a
 // device share the array: two calls whose work overlaps on the GPU (different
 // streams, or different host threads) race on it and must be ordered by the
 // caller.  Every scratch word a call reads was written earlier by the same
@@ -59,6 +63,32 @@ cudaError_t scratch_address(double** out) {
   return cudaSuccess;
 }
 
+// Per-row constants of the global grid (Sec. 7), one thread per latitude
+// row: cell-centre latitude theta_j = lat_min + (j + 1/2) dtheta and
+// A = 1/(2 a cos dlambda), f = 2 Omega sin, tau = tan / a, Bth / cos, g A.
+// The products and sums are rounded one by one (no contraction), as the
+// host computes them for dd4dv_create.
+__global__ void noalloc_rows_kernel(RowConst* rows, int nlon, int nlat, double lat_min_deg,
+                                    double lat_max_deg, double radius, double gravity, double omega) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nlat) return;
+  const double pi = 3.14159265358979323846;
+  const double dlam = __ddiv_rn(__dmul_rn(2.0, pi), (double)nlon);
+  const double dth = __ddiv_rn(__ddiv_rn(__dmul_rn(__dsub_rn(lat_max_deg, lat_min_deg), pi), 180.0),
+                               (double)nlat);
+  const double th0 = __ddiv_rn(__dmul_rn(lat_min_deg, pi), 180.0);
+  const double Bth = __ddiv_rn(1.0, __dmul_rn(__dmul_rn(2.0, radius), dth));
+  const double th = __dadd_rn(th0, __dmul_rn(__dadd_rn((double)j, 0.5), dth));
+  RowConst r;
+  r.c = cos(th);
+  r.A = __ddiv_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(2.0, radius), r.c), dlam));
+  r.f = __dmul_rn(__dmul_rn(2.0, omega), sin(th));
+  r.tau = __ddiv_rn(tan(th), radius);
+  r.BinvC = __ddiv_rn(Bth, r.c);
+  r.gA = __dmul_rn(gravity, r.A);
+  rows[j] = r;
+}
+
 }  // namespace
 }  // namespace dd4dv
 
@@ -93,27 +123,15 @@ extern "C" dd4dv_status dd4dv_forward_noalloc(const dd4dv_model* model, const do
   double* s2 = scratch + kMaxStateDoubles;
   RowConst* rows_d = reinterpret_cast<RowConst*>(scratch + 2 * kMaxStateDoubles);
 
-  // per-row constants of the grid (Sec. 7), computed on the host
-  RowConst rows[kMaxRows];
+  // per-row constants of the grid (Sec. 7), computed on the device into the
+  // scratch array; the two scalars the stages take are formed here
   const double pi = 3.14159265358979323846;
-  const double dlam = 2.0 * pi / m.nlon;
   const double dth = (m.lat_max_deg - m.lat_min_deg) * pi / 180.0 / m.nlat;
-  const double th0 = m.lat_min_deg * pi / 180.0;
   const double Bth = 1.0 / (2.0 * m.radius * dth);
   const double gBth = m.gravity * Bth;
-  for (int j = 0; j < m.nlat; ++j) {
-    const double th = th0 + (j + 0.5) * dth;
-    RowConst r;
-    r.c = std::cos(th);
-    r.A = 1.0 / (2.0 * m.radius * r.c * dlam);
-    r.f = 2.0 * m.omega * std::sin(th);
-    r.tau = std::tan(th) / m.radius;
-    r.BinvC = Bth / r.c;
-    r.gA = m.gravity * r.A;
-    rows[j] = r;
-  }
-  e = cudaMemcpyAsync(rows_d, rows, m.nlat * sizeof(RowConst), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);   // rows[] lives on this stack frame
+  noalloc_rows_kernel<<<(m.nlat + 127) / 128, 128, 0, st>>>(rows_d, m.nlon, m.nlat, m.lat_min_deg,
+                                                           m.lat_max_deg, m.radius, m.gravity, m.omega);
+  e = cudaGetLastError();
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(traj, x0, G * sizeof(double), cudaMemcpyDeviceToDevice, st);
   for (int n = 0; n < m.nsteps && e == cudaSuccess; ++n) {

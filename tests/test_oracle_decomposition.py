@@ -156,3 +156,79 @@ def test_scaleup_workloads_reproduce_table3_problem_sizes():
         size = sum(3 * s.nx * s.ny for s in dec.subs)
         assert size == 3 * 32 * 32 * int(qp)
         assert abs(size - printed) <= 0.05 * printed
+
+
+def _bilinear_field(nlon, nlat, coef, shift):
+    """f(i, j) = a + b u + c j + d u j with u = (i - shift) mod nlon, so that
+    f is bilinear in (u, j) on every cell whose columns do not straddle
+    u = nlon - 1 -> 0."""
+    a, b, c, d = coef
+    u = ((np.arange(nlon) - shift) % nlon)[None, :].astype(np.float64)
+    j = np.arange(nlat)[:, None].astype(np.float64)
+    return a + b * u + c * j + d * u * j
+
+
+def test_bilinear_operator_is_exact_on_bilinear_fields():
+    """Pin of H (bilinear interpolation in index space, lon periodic): it
+    reproduces exactly the fields in span{1, i, j, i j} at any fractional
+    (fi, fj), and it is the only 4-corner rule that does (four corners,
+    four coefficients).  Each observation gets a field whose lon origin puts
+    its cell away from the field's seam, so cells across the periodic edge
+    i = nlon - 1 -> 0 are covered.  A swapped lon/lat fraction, a dropped
+    corner or a wrong wrap fails."""
+    nlon, nlat = 16, 9
+    rng = np.random.default_rng(7)
+    n = 400
+    fi = rng.uniform(0.0, nlon, n)
+    fj = rng.uniform(0.0, nlat - 1, n)
+    fi[:40] = nlon - 1 + rng.uniform(0.0, 1.0, 40)   # across the periodic edge
+    fi[40:60] = np.floor(fi[40:60])                   # on grid columns
+    fj[60:80] = np.floor(fj[60:80])                   # on grid rows
+    fj[80:90] = nlat - 1                              # on the last row
+    var = rng.integers(0, 3, n)
+    coefs = [(3.0, 0.7, -1.3, 0.11), (-2.0, -0.4, 0.9, -0.07), (0.5, 1.9, 0.3, 0.05)]
+    for k in range(n):
+        shift = (int(np.floor(fi[k])) - nlon // 2) % nlon
+        traj = torch.zeros(1, 3, nlat, nlon, dtype=F64)
+        for v in range(3):
+            traj[0, v] = torch.as_tensor(_bilinear_field(nlon, nlat, coefs[v], shift))
+        got = oracle.observe(nlon, traj, [0], [int(var[k])], [fi[k]], [fj[k]])[0]
+        u = fi[k] - np.floor(fi[k]) + nlon // 2
+        a, b, c, d = coefs[var[k]]
+        want = a + b * u + c * fj[k] + d * u * fj[k]
+        assert abs(got - want) <= 1e-13 * max(1.0, abs(want)), (k, fi[k], fj[k], got, want)
+
+
+def test_local_observation_term_vanishes_on_exact_bilinear_data():
+    """The same pin through a subdomain's own index mapping (local rows and
+    columns of the bilinear corners, boxes that wrap around i = 0): with
+    every observation value equal to the bilinear field at (fi, fj), the
+    local misfit term of Eq. funrestr is zero at the field's restriction."""
+    w = tiny_workload(obs_count=120)
+    inp = workloads.generate(w)
+    nlon, nlat = w.nlon, w.nlat
+    shift = nlon // 2            # field seam between columns nlon/2 - 1 and nlon/2
+    coefs = [(3.0, 0.7, -1.3, 0.11), (-2.0, -0.4, 0.9, -0.07), (0.5, 1.9, 0.3, 0.05)]
+    F = np.stack([_bilinear_field(nlon, nlat, c, shift) for c in coefs])
+    fi, fj = np.asarray(inp["obs_fi"]), np.asarray(inp["obs_fj"])
+    keep = (np.floor(fi).astype(int) % nlon) != (shift - 1) % nlon
+    var = np.asarray(inp["obs_var"])[keep]
+    fi, fj, lev = fi[keep], fj[keep], np.asarray(inp["obs_level"])[keep]
+    u = (fi - shift) % nlon
+    y = np.array([coefs[v][0] + coefs[v][1] * uu + coefs[v][2] * jj + coefs[v][3] * uu * jj
+                  for v, uu, jj in zip(var, u, fj)])
+    assert np.any(np.floor(fi) == nlon - 1), "no observation across the periodic edge"
+    obs = oracle.Observations(lev, var, fi, fj, y, np.ones(len(y)))
+    grid = oracle.Grid(nlon, nlat, workloads.RADIUS, workloads.GRAVITY, workloads.OMEGA)
+    dec = oracle.Decomposition.make(nlon, nlat, w.nsteps, w.P1, w.P2, w.Q, inp["lon_cuts"],
+                                    inp["lat_cuts"], inp["t_cuts"], w.o_lon, w.o_lat, w.o_t)
+    st = oracle.Setup(grid, inp["dt"], w.nsteps, inp["x_b0"], obs, w.sigma_b, dec)
+    Ft = torch.as_tensor(F, dtype=F64)
+    seen = 0
+    for lp in st.locals:
+        s = lp.sub
+        xbox = Ft[:, s.j0:s.j0 + s.ny][:, :, lp.cols]
+        for n in lp.obs_arrays:
+            assert float(lp.obs_term(n, xbox)) <= 1e-24
+            seen += len(lp.obs_arrays[n]["y"])
+    assert seen >= len(y)

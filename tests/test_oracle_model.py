@@ -140,3 +140,59 @@ def test_frozen_ghosts_equal_global_run_when_boundary_is_consistent():
     gh = Ghosts(west=x[:, :, -1], east=x[:, :, 0])
     y = rk3_step(x, geo, 400.0, gh, gh)
     assert torch.equal(y, x)
+
+
+def _box_vs_global_errors(steps=(16, 32, 64, 128), T=16 * 400.0):
+    """Max difference, on an interior box, between the global run and the box
+    run whose four lateral ghost sides are taken from that same global
+    trajectory (B = the global levels), at T / k for each k in steps."""
+    g = _grid(48, 24)
+    lam = torch.arange(48, dtype=F64) * g.dlam
+    TH, LA = torch.meshgrid(g.theta, lam, indexing="ij")
+    # an unbalanced height bump plus a zonal jet: waves cross every box edge
+    d2 = (LA - lam[30]) ** 2 * torch.cos(TH) ** 2 + (TH - g.theta[15]) ** 2
+    x0 = torch.zeros(3, 24, 48, dtype=F64)
+    x0[0] = 4000.0 + 50.0 * torch.exp(-d2 / (2.0 * math.radians(10.0) ** 2))
+    x0[1] = 5.0 * torch.cos(TH)
+    j0, ny, i0, nx = 6, 12, 12, 20
+    geo = BoxGeom.make(g, j0, ny)
+    errs = []
+    for k in steps:
+        dt = T / k
+        ref = global_forward(g, x0, dt, k)
+
+        def gh(n):
+            B = ref[n]
+            return Ghosts(west=B[:, j0:j0 + ny, i0 - 1], east=B[:, j0:j0 + ny, i0 + nx],
+                          south=B[:, j0 - 1, i0:i0 + nx], north=B[:, j0 + ny, i0:i0 + nx])
+
+        x = ref[0][:, j0:j0 + ny, i0:i0 + nx].clone()
+        for n in range(k):
+            x = rk3_step(x, geo, dt, gh(n), gh(n + 1))
+        errs.append(float((x - ref[k][:, j0:j0 + ny, i0:i0 + nx]).abs().max()))
+    errs = np.array(errs)
+    return np.log2(errs[:-1] / errs[1:])
+
+
+def test_frozen_ghost_stage_times_give_second_order_agreement_with_global_run():
+    """Convergence pin of the frozen-boundary stage rule (Sec. 3.3, the
+    Exchange of Algorithm 1).  A box whose lateral ghosts come from the
+    global trajectory of the same model differs from the global run only
+    through the ghost values at the three RK3 stages.  The global run's own
+    stage values at the ghost cells are x, x1 = x + dt F = B(n+1) - O(dt^2)
+    and x2 = x + dt/2 F + dt^2/4 F'F + O(dt^3), which equals
+    (B(n) + B(n+1))/2 up to O(dt^3).  Propagated through one step these
+    mismatches are O(dt^3), so over a fixed time the box converges to the
+    global run at second order in dt.  Any other stage time (stage 3 at B(n)
+    or B(n+1), stage 2 at B(n)) leaves an O(dt) ghost error and only first
+    order."""
+    p = _box_vs_global_errors()
+    assert np.all((p > 1.9) & (p < 2.1)), p
+
+
+def test_frozen_ghost_pin_rejects_a_wrong_stage_time(monkeypatch):
+    """The pin above fails for a planted mistake in the oracle: stage 3
+    taking its ghosts at B(n+1) instead of the midpoint."""
+    monkeypatch.setattr(Ghosts, "blend", lambda self, other: other)
+    p = _box_vs_global_errors(steps=(16, 32, 64))
+    assert np.all(p < 1.2), p

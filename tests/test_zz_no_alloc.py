@@ -65,11 +65,15 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     import __graft_entry__ as g
     g.build()
     from paper_2205_06649_gb300 import _abi, lib
-    wl = workloads.preset("small", nlon=1024, nlat=512, nsteps=1)
-    model = _model(wl, 10.0)
-    x0 = torch.zeros((3, 512, 1024), dtype=torch.float64, device="cuda")
-    traj = torch.zeros((2, 3, 512, 1024), dtype=torch.float64, device="cuda")
-    st = lib.dd4dv_forward_noalloc(C.byref(model), C.c_void_p(x0.data_ptr()), C.c_void_p(traj.data_ptr()),
-                                   None)
-    assert st == -1
-    assert b"scratch limit" in lib.dd4dv_last_error(None)
+    # 3*nlat*nlon above 393216 doubles; then nlat above 1024 rows with few
+    # points (3 * 1025 * 3 = 9225 doubles, within the first bound)
+    for nlon, nlat in ((1024, 512), (3, 1025)):
+        wl = workloads.preset("small", nlon=nlon, nlat=nlat, nsteps=1)
+        model = _model(wl, 10.0)
+        x0 = torch.zeros((3, nlat, nlon), dtype=torch.float64, device="cuda")
+        traj = torch.zeros((2, 3, nlat, nlon), dtype=torch.float64, device="cuda")
+        st = lib.dd4dv_forward_noalloc(C.byref(model), C.c_void_p(x0.data_ptr()),
+                                       C.c_void_p(traj.data_ptr()), None)
+        assert st == -1, (nlon, nlat)
+        assert b"scratch limit" in lib.dd4dv_last_error(None)
+        assert float(traj.abs().max()) == 0.0
