@@ -1,16 +1,17 @@
 """Benchmark of the DD-4DVar hot path on GB300 (one JSON line on stdout).
 
-A step is one outer iteration of Algorithm 1 on the medium workload (256x128
-grid, 128 steps, 4x4x4 = 64 overlapping subdomains, overlap 4 points / 4
-steps, recursive-filter B, 5 % of points observed in h, u, v every 8 steps):
-every subdomain is put back at the start point (controls 0, exchange state
-l = 0), then 20 batched L-BFGS iterations with their Armijo trials evaluate
-J and grad J of all active subdomains (initial state, forward sweep,
-observation and overlap terms, adjoint sweep, V^T), and the Exchange runs
-(local trajectories, overlap targets, assembled boundary trajectory,
-outer increment).  The metric is grid-point-steps (one point of a subdomain's
+Default step (N = 1 headline): one batched evaluation of every local
+functional J_s and its gradient on the large workload (2048 x 1024 grid,
+1024 steps, 16 x 16 x 8 = 2048 uneven overlapping subdomains, overlap
+8 points / 8 steps, recursive-filter B, 1e6 observations), FP64: initial
+states x_b + V w, forward sweeps with the observation and overlap terms,
+adjoint sweeps and V^T for all subdomains, 3.3e9 grid-point-steps per
+evaluation.  The metric is grid-point-steps (one point of a subdomain's
 extended box advanced one step forward and back through the adjoint) per
-second over all evaluations of the step.
+second.  Extra legs in the same line: the FP32-state path on the same
+workload, and on the medium workload one outer iteration of Algorithm 1
+(20 batched L-BFGS iterations + Exchange) in FP64 and FP32, time to a fixed
+analysis RMSE, and the Gauss-Newton local solver.
 
 Inputs are seeded and synthetic (module ``workloads``; the truth run and the
 observation sampling use the library's own global model and H).  They stand
@@ -216,12 +217,13 @@ def time_to_analysis(ctx, solver, truth0, max_outer, torch, stream, zeros_dev):
     return out
 
 
-def profile_summary_traffic(kernel: str, src_hash: str, precision: str):
+def profile_summary_traffic(kernel: str, src_hash: str, precision: str, workload: str = "medium"):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)
-    from a committed ncu summary of the medium workload, if it was taken on the
-    current kernel source; otherwise None."""
+    from a committed ncu summary of this workload's sweeps (captured on it, or
+    on a smaller case and scaled to a full launch, as the summary states), if
+    it was taken on the current kernel source; otherwise None."""
     import glob
-    for p in sorted(glob.glob(os.path.join(ROOT, "profiles", f"sweeps_medium_{precision}*.md"))):
+    for p in sorted(glob.glob(os.path.join(ROOT, "profiles", f"sweeps_{workload}_{precision}*.md"))):
         text = open(p).read()
         h = re.search(r"sweep_source_sha256:\s*([0-9a-f]+)", text)
         m = re.search(rf"{kernel}_dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
@@ -235,31 +237,95 @@ def source_hash():
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def cpu_oracle_baseline(wl, inputs, budget_s=20.0):
-    """The CPU oracle as it stands, on a bounded sample of the same workload:
-    J and grad J of subdomains in index order until the time budget is used."""
-    import torch
+def _oracle_sample_setup(wl, inp, y, so, n_subs):
+    """Oracle setup of the first n_subs subdomains of the first time window
+    (index order), the rest of the workload as it is (sample mode of
+    oracle.Setup: background run up to those windows' last level)."""
     import oracle
-    st, _, _ = oracle.build_setup(wl, inputs)
-    B, prev = st.xb_traj, st.background_prev()
-    done = 0
-    pts = 0
-    t0 = time.perf_counter()
-    for lp in st.locals:
-        s = lp.sub
-        lp.J_and_grad(torch.zeros(lp.nctrl, dtype=torch.float64), B, prev)
-        done += 1
-        pts += s.nx * s.ny * (s.b - s.a)
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": pts / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"J and grad J of {done} of {len(st.locals)} subdomains at w = 0, "
-                      f"{pts} pt-steps in {dt:.1f} s (FP64 PyTorch-CPU oracle, autograd adjoint)"}
+    obs = oracle.Observations(inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)
+    grid = oracle.Grid(wl.nlon, wl.nlat, workloads.RADIUS, workloads.GRAVITY, workloads.OMEGA,
+                       workloads.LAT_MIN_DEG, workloads.LAT_MAX_DEG)
+    dec = oracle.Decomposition.make(wl.nlon, wl.nlat, wl.nsteps, wl.P1, wl.P2, wl.Q, inp["lon_cuts"],
+                                    inp["lat_cuts"], inp["t_cuts"], wl.o_lon, wl.o_lat, wl.o_t)
+    q0 = [s.index for s in dec.subs if s.q == 0][:n_subs]
+    st = oracle.Setup(grid, inp["dt"], wl.nsteps, inp["x_b0"], obs, wl.sigma_b, dec,
+                      corr_len=wl.corr_len, rf_passes=wl.rf_passes, lam=wl.lam, mu=wl.mu, sample=q0)
+    return st, len(dec.subs)
+
+
+# subdomains the CPU sample sets up: enough for the time budget
+CPU_SAMPLE_SUBS = {"large": 12, "batching": 12}
+
+
+def _cpu_baseline_child(conn, wl_name, y, so, budget_s):
+    """Spawned process: sets up the oracle sample while the GPU legs run,
+    then, on "go", times J and grad J of the sampled subdomains (index order,
+    w = 0) until the budget is used, alone on the host cores."""
+    import torch
+    try:
+        wl = workloads.preset(wl_name)
+        inp = workloads.generate(wl)
+        t0 = time.perf_counter()
+        st, n_all = _oracle_sample_setup(wl, inp, y, so, CPU_SAMPLE_SUBS.get(wl_name, 64))
+        prev = st.background_prev()
+        setup_s = time.perf_counter() - t0
+        conn.send(("ready", setup_s))
+        if conn.recv() != "go":
+            return
+        done = pts = 0
+        t0 = time.perf_counter()
+        for lp in st.locals:
+            s = lp.sub
+            lp.J_and_grad(torch.zeros(lp.nctrl, dtype=torch.float64), st.xb_traj, prev)
+            done += 1
+            pts += s.nx * s.ny * (s.b - s.a)
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+        conn.send({"value": pts / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                   "sample": f"J and grad J at w = 0 of {done} of the {n_all} subdomains (the first of "
+                             f"the first time window, index order), {pts} pt-steps in {dt:.1f} s; "
+                             f"FP64 PyTorch-CPU oracle, autograd adjoint; set up in {setup_s:.0f} s "
+                             f"beside the GPU legs, timed alone"})
+    except Exception as e:   # reported in the line, never fatal to the GPU measurement
+        conn.send({"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                   "sample": f"failed: {type(e).__name__}: {e}"})
+
+
+class CpuBaseline:
+    """The CPU oracle leg, run in a spawned process (it never touches CUDA)."""
+
+    def __init__(self, wl_name, y, so, budget_s=20.0):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conn, child = ctx.Pipe()
+        self.proc = ctx.Process(target=_cpu_baseline_child, args=(child, wl_name, y, so, budget_s),
+                                daemon=True)
+        self.proc.start()
+
+    def result(self, timeout_s=900.0):
+        try:
+            if not self.conn.poll(timeout_s):
+                return {"value": None, "kind": "oracle", "sample": "set-up did not finish in time"}
+            msg = self.conn.recv()
+            if isinstance(msg, dict):
+                return msg
+            self.conn.send("go")
+            if not self.conn.poll(timeout_s):
+                return {"value": None, "kind": "oracle", "sample": "timed sample did not finish"}
+            return self.conn.recv()
+        finally:
+            self.proc.join(timeout=30)
+            if self.proc.is_alive():
+                self.proc.terminate()
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle on the same workload and metric."""
+    """Reference arm: the CPU oracle on this arm's workload and metric (FP64
+    J and grad J of subdomains, pt-steps/s).  Each step evaluates a bounded
+    sample: the next subdomains of the first time window, one after another.
+    The twin experiment's truth run and observations come from the oracle's
+    own global model, up to the last level those subdomains reach."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -267,9 +333,25 @@ def run_reference(args):
     import oracle
     wl = workloads.preset(args.workload)
     inp = workloads.generate(wl)
-    st, _, _ = oracle.build_setup(wl, inp)
-    B, prev = st.xb_traj, st.background_prev()
-    per_step = max(1, len(st.locals) // 8)
+    n_subs = CPU_SAMPLE_SUBS.get(args.workload, 64)
+    dec = oracle.Decomposition.make(wl.nlon, wl.nlat, wl.nsteps, wl.P1, wl.P2, wl.Q, inp["lon_cuts"],
+                                    inp["lat_cuts"], inp["t_cuts"], wl.o_lon, wl.o_lat, wl.o_t)
+    last = max(s.b for s in dec.subs if s.q == 0)
+    grid = oracle.Grid(wl.nlon, wl.nlat, workloads.RADIUS, workloads.GRAVITY, workloads.OMEGA,
+                       workloads.LAT_MIN_DEG, workloads.LAT_MAX_DEG)
+    with torch.no_grad():
+        truth = oracle.global_forward(grid, torch.as_tensor(inp["x_t0"]), inp["dt"], last)
+    so = np.asarray(wl.sigma_o)[inp["obs_var"]]
+    lev = np.asarray(inp["obs_level"])
+    y = np.zeros(len(lev))
+    k = np.nonzero(lev <= last)[0]
+    y[k] = oracle.observe(wl.nlon, truth, lev[k], np.asarray(inp["obs_var"])[k],
+                          np.asarray(inp["obs_fi"])[k], np.asarray(inp["obs_fj"])[k])
+    y += so * inp["obs_noise"]
+    del truth
+    st, n_all = _oracle_sample_setup(wl, inp, y, so, n_subs)
+    prev = st.background_prev()
+    per_step = 1 if wl.nlon * wl.nlat >= 512 * 256 else max(1, len(st.locals) // 8)
     k = 0
     pts_tot = 0
     t_tot = 0.0
@@ -279,15 +361,15 @@ def run_reference(args):
         for _ in range(per_step):
             lp = st.locals[k % len(st.locals)]
             k += 1
-            lp.J_and_grad(torch.zeros(lp.nctrl, dtype=torch.float64), B, prev)
+            lp.J_and_grad(torch.zeros(lp.nctrl, dtype=torch.float64), st.xb_traj, prev)
             pts += lp.sub.nx * lp.sub.ny * (lp.sub.b - lp.sub.a)
         dt = time.perf_counter() - t0
         if it >= args.warmup:
             pts_tot += pts
             t_tot += dt
     value = pts_tot / t_tot
-    sample = (f"each step: J and grad J of {per_step} of {len(st.locals)} subdomains "
-              f"(FP64 PyTorch-CPU oracle, autograd adjoint)")
+    sample = (f"each step: J and grad J at w = 0 of {per_step} of the {n_all} subdomains (next of the "
+              f"first {len(st.locals)} of the first time window); FP64 PyTorch-CPU oracle, autograd adjoint")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -300,36 +382,190 @@ def run_reference(args):
     return 0
 
 
-def eval_mode(args, ctx, wl, prec, stream, torch):
-    """Steps of one batched J and grad J evaluation of every subdomain
-    (device-resident controls), timed with CUDA events on the library stream."""
-    rng = np.random.default_rng(0)
-    w = torch.tensor(0.3 * rng.standard_normal(ctx.ctrl_total), device="cuda")
-    for _ in range(args.warmup):
-        ctx.eval(w)
-    torch.cuda.synchronize()
+# Launch shapes the autotuner picked on the large workload (forward cluster,
+# forward threads, adjoint cluster, adjoint threads, stored stage states);
+# the benchmark forces them instead of spending ~40 evaluations on tuning.
+DEFAULT_SHAPES = {("large", 0): "16,512,16,512,0", ("large", 1): "16,384,16,512,1"}
+
+
+def roofline_of(ctx, prec, reps=3):
+    """Roofline object of the dominant sweep: durations from CUDA events
+    around each sweep launch on the library stream (dd4dv_profile_sweeps),
+    algorithmic flops / bytes per pt-step times the pt-steps of one launch."""
+    prof = ctx.profile_sweeps(np.zeros(ctx.ctrl_total), reps=reps)
+    pts_eval = ctx.pt_steps()
+    kern = "adjoint" if prof["adjoint_ms"] >= prof["forward_ms"] else "forward"
+    t_k = prof[f"{kern}_ms"] / 1e3
+    peaks, peaks_kind = measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    tsize = 8 if prec == 0 else 4
+    stored = ctx.sweep_config()["stored_stages"]
+    fl = FLOPS_STORED if stored else FLOPS
+    vals = VALUES_STORED if stored else VALUES_PER_PTSTEP
+    flops = fl[kern] * pts_eval / t_k
+    bytes_ = vals[kern] * tsize * pts_eval / t_k
+    hbm_peak = float(peaks["hbm_gbs"]) * 1e9
+    per_clk = FP64_FLOP_PER_CLK_SM if prec == 0 else FP32_FLOP_PER_CLK_SM
+    alu_peak = N_SM * per_clk * sm_mhz * 1e6
+    alu_frac = flops / alu_peak
+    hbm_frac = bytes_ / hbm_peak
+    wl_tag = getattr(ctx, "_bench_workload", "medium")
+    traffic = profile_summary_traffic(kern, source_hash(), "fp64" if prec == 0 else "fp32", wl_tag)
+    if alu_frac >= hbm_frac:
+        roof = {"bound": "alu", "achieved": flops / 1e12, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
+                "frac": alu_frac, "traffic": traffic, "kernel": f"{kern} sweep",
+                "peak_source": f"derived: {N_SM} SMs x {per_clk:.0f} {'FP64' if prec == 0 else 'FP32'} "
+                               f"flop/clk x {sm_mhz:.0f} MHz",
+                "hbm_frac_of_" + peaks_kind: hbm_frac}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_ / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s",
+                "frac": hbm_frac, "traffic": traffic, "kernel": f"{kern} sweep",
+                "peak_source": f"hbm_gbs of {peaks_kind}", "alu_frac": alu_frac}
+    roof["kernel_ms"] = prof[f"{kern}_ms"]
+    roof["pt_steps_per_launch"] = pts_eval
+    roof["algorithmic_per_pt_step"] = {"flops": fl[kern], "bytes": vals[kern] * tsize}
+    roof["sweeps_ms"] = {"forward": prof["forward_ms"], "adjoint": prof["adjoint_ms"], "eval": prof["eval_ms"]}
+    return roof
+
+
+def timed_evals(ctx, w, steps, stream, torch):
+    """steps batched J and grad J evaluations of every subdomain at the
+    device-resident controls w, CUDA events on the library stream."""
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     l0 = ctx.launch_count()
-    with ClockSampler(0) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
-            ctx.eval(w)
-        e1.record(stream)
-        e1.synchronize()
-    ms = e0.elapsed_time(e1)
-    prof = ctx.profile_sweeps(np.zeros(ctx.ctrl_total), reps=3)
-    line = {"metric": "fwd+adjoint grid-point-steps/s (one batched evaluation per step)",
-            "value": ctx.pt_steps() * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
-            "config": {"workload": wl_desc(wl), "n_sub": ctx.n_sub, "pt_steps_per_eval": ctx.pt_steps(),
-                       "sweep_launch": ctx.sweep_config(), "ckpt_k": args.ckpt},
-            "sweeps_ms": {"forward": prof["forward_ms"], "adjoint": prof["adjoint_ms"]},
-            "clocks": clk.summary(), "gpu_launches": ctx.launch_count() - l0}
-    print(json.dumps(line), flush=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.eval(w)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), ctx.launch_count() - l0
+
+
+def e2e_evals(ctx, w_dev, steps, torch):
+    """The same evaluations through the public C call with HOST buffers:
+    each step copies the controls in from pinned host memory and J and the
+    gradient out to pinned host memory (dd4dv_eval, device_ptrs = 0)."""
+    import ctypes as C
+    import paper_2205_06649_gb300 as dd
+    w_h = torch.empty(ctx.ctrl_total, dtype=torch.float64).pin_memory()
+    w_h.copy_(w_dev.cpu())
+    J_h = torch.empty(ctx.n_sub, dtype=torch.float64).pin_memory()
+    g_h = torch.empty(ctx.ctrl_total, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st = dd.lib.dd4dv_eval(ctx._h, C.c_void_p(w_h.data_ptr()), C.c_void_p(J_h.data_ptr()),
+                               C.c_void_p(g_h.data_ptr()), None, 0)
+        if st != 0:
+            raise RuntimeError(ctx.last_error())
+    t = time.perf_counter() - t0
+    return {"value": ctx.pt_steps() * steps / t, "unit": UNIT,
+            "h2d_bytes_per_step": int(ctx.ctrl_total * 8),
+            "d2h_bytes_per_step": int((ctx.n_sub + ctx.ctrl_total) * 8),
+            "api": "dd4dv_eval with host buffers (controls in, J and gradient out, pinned)"}
+
+
+def eval_leg(args, wl, prec, inp, torch, shape, e2e=False, on_obs=None, barrier=None, steps=None,
+             warmup=None):
+    """One context on the workload: warm-up, timed evaluations (and
+    optionally the end-to-end leg), roofline of the dominant sweep.
+    on_obs(obs) runs once the observations exist; barrier() runs on both
+    sides of the timed region.  steps / warmup default to the command line's;
+    the end-to-end leg takes at most 5 steps (it measures a rate)."""
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    stream = torch.cuda.Stream()
+    ctx, inp, truth, obs = build_problem(wl, prec, stream.cuda_stream, inputs=inp, shape=shape,
+                                         ckpt_k=args.ckpt)
+    ctx._bench_workload = wl.name
+    if on_obs:
+        on_obs(obs)
+    rng = np.random.default_rng(0)
+    w = torch.tensor(0.3 * rng.standard_normal(ctx.ctrl_total), device="cuda")
+    for _ in range(warmup):
+        ctx.eval(w)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms, launches = timed_evals(ctx, w, steps, stream, torch)
+    if barrier:
+        barrier()
+    out = {"ms": ms, "steps": steps, "launches": launches, "clocks": clk.summary(), "pt_steps": ctx.pt_steps(),
+           "n_sub": ctx.n_sub, "sweep_launch": ctx.sweep_config(),
+           "traj_bytes": ctx.traj_total * (8 if prec == 0 else 4)}
+    out["roofline"] = roofline_of(ctx, prec)
+    if e2e:
+        out["e2e"] = e2e_evals(ctx, w, min(steps, 5), torch)
     ctx.destroy()
-    return 0
+    del w
+    torch.cuda.empty_cache()
+    return out
+
+
+def medium_extras(args, torch):
+    """Medium workload legs: one outer iteration of Algorithm 1 in FP64 and
+    in FP32 state, time to a fixed analysis RMSE (FP64 runs to its stopping
+    test or max_outer; target = 1.01 x its final RMSE; outer-iteration counts
+    reported), and the Gauss-Newton local solver."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("medium")
+    inp = workloads.generate(wl)
+    solver = solver_for(wl)
+    res = {}
+    ctxs = {}
+    for prec in (0, 1):
+        stream = torch.cuda.Stream()
+        ctx, _, truth, _ = build_problem(wl, prec, stream.cuda_stream, inputs=inp)
+        zeros = torch.zeros(ctx.ctrl_total, dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            ctx.set_controls(zeros)
+            ctx.reset_exchange()
+            ctx.outer_step(solver)
+        ms, st, launches = timed_steps(ctx, solver, args.steps, zeros, stream, torch)
+        prof = ctx.profile_sweeps(np.zeros(ctx.ctrl_total), reps=5)
+        res["fp64" if prec == 0 else "fp32_state"] = {
+            "value": st.pt_steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "evals_per_step": st.evals / args.steps, "gpu_launches_per_step": launches / args.steps,
+            "sweep_launch": ctx.sweep_config(),
+            "sweeps_ms": {"forward": prof["forward_ms"], "adjoint": prof["adjoint_ms"], "eval": prof["eval_ms"]}}
+        ctxs[prec] = (ctx, stream, zeros, truth)
+    ctx, stream, zeros, truth = ctxs[0]
+    ctx32, stream32, zeros32, _ = ctxs[1]
+    h64 = time_to_analysis(ctx, solver, truth[0], wl.max_outer, torch, stream, zeros)
+    h32 = time_to_analysis(ctx32, solver, truth[0], wl.max_outer, torch, stream32, zeros32)
+    target = 1.01 * h64[-1][1]
+    t64 = next(t for t, r, _ in h64 if r <= target)
+    t32 = next((t for t, r, _ in h32 if r <= target), None)
+    res["time_to_analysis"] = {
+        "rmse_h_background": rmse_h(inp["x_b0"], truth[0]),
+        "rmse_h_fp64_final": h64[-1][1], "rmse_h_fp32_final": h32[-1][1],
+        "target_rmse_h": target, "fp64_s": t64, "fp32_s": t32, "speedup": (t64 / t32) if t32 else None,
+        "outer_fp64": len(h64), "outer_fp32": len(h32),
+        "outer_to_target_fp64": next(i + 1 for i, (t, r, _) in enumerate(h64) if r <= target),
+        "outer_to_target_fp32": next((i + 1 for i, (t, r, _) in enumerate(h32) if r <= target), None),
+        "dw_inf_fp64": [d for _, _, d in h64]}
+    ctx32.destroy()
+    gn_solver = dd.solver_defaults(lbfgs_m=wl.lbfgs_m, max_local_iters=wl.local_iters,
+                                   max_outer=wl.max_outer, local_solver=1, gn_iters=3,
+                                   cg_iters=10, cg_tol=1e-6)
+    for _ in range(2):
+        ctx.set_controls(zeros)
+        ctx.reset_exchange()
+        ctx.outer_step(gn_solver)
+    ms_gn, st_gn, _ = timed_steps(ctx, gn_solver, args.steps, zeros, stream, torch)
+    hgn = time_to_analysis(ctx, gn_solver, truth[0], wl.max_outer, torch, stream, zeros)
+    tgn = next((t for t, r, _ in hgn if r <= target), None)
+    res["gauss_newton"] = {
+        "settings": {"gn_iters": 3, "cg_iters": 10, "cg_tol": 1e-6},
+        "value": st_gn.pt_steps / (ms_gn / 1e3), "unit": UNIT, "ms_per_step": ms_gn / args.steps,
+        "rmse_h_final": hgn[-1][1], "s_to_target": tgn, "outer": len(hgn),
+        "speedup_vs_lbfgs_fp64": (t64 / tgn) if tgn else None}
+    ctx.destroy()
+    torch.cuda.empty_cache()
+    res["workload"] = wl_desc(wl)
+    return res
 
 
 # Weak-scaling experiment of Sec. 7 (Table 3): QP spatial subdomains whose
@@ -439,30 +675,114 @@ def wl_desc(wl):
             f"obs of vars {list(wl.obs_vars)} every {wl.obs_every} steps")
 
 
+def headline_line(args, wl, prec, leg, value, t_max, world, extras, cpu):
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
+        "config": {"workload": wl_desc(wl), "precision": "fp64" if prec == 0 else "fp32-state",
+                   "step": f"one batched J and grad J evaluation of all {leg['n_sub']} subdomains "
+                           "(x_b + V w, forward sweeps with observation and overlap terms, adjoint "
+                           "sweeps, V^T), controls resident in HBM",
+                   "sweep_launch": leg["sweep_launch"], "pt_steps_per_eval": leg["pt_steps"],
+                   "l2": f"inputs larger than L2: trajectories {leg['traj_bytes'] / 1e9:.0f} GB",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": leg["roofline"], "cpu_baseline": cpu, "e2e": leg.get("e2e"), "clocks": leg["clocks"],
+        "gpu_launches": int(leg["launches"]), **extras,
+    }
+
+
+def outer_mode(args, wl, prec, torch, world, rank, local_rank):
+    """A step is one outer iteration of Algorithm 1 from the start point
+    (controls 0, exchange state l = 0): 20 batched L-BFGS iterations with
+    their Armijo trials, then the Exchange."""
+    import torch.distributed as dist
+    import paper_2205_06649_gb300 as dd
+    stream = torch.cuda.Stream()
+    inp = workloads.generate(wl)
+    ctx, inp, truth, obs = build_problem(wl, prec, stream.cuda_stream, inputs=inp, shape=args.shape,
+                                         ckpt_k=args.ckpt)
+    ctx._bench_workload = wl.name
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = CpuBaseline(wl.name, obs[4], obs[5])
+    solver = solver_for(wl)
+    zeros = torch.zeros(ctx.ctrl_total, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ctx.set_controls(zeros)
+        ctx.reset_exchange()
+        ctx.outer_step(solver)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(local_rank) as clk:
+        ms, stats, launches = timed_steps(ctx, solver, args.steps, zeros, stream, torch)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t_max, pts_all = aggregate_ranks(ms, float(stats.pt_steps), "cuda")
+    if rank != 0:
+        ctx.destroy()
+        return 0
+    roof = roofline_of(ctx, prec, reps=5)
+    w_host = torch.zeros(ctx.ctrl_total, dtype=torch.float64).pin_memory().numpy()
+    xa_host = torch.zeros(3 * wl.nlat * wl.nlon, dtype=torch.float64).pin_memory().numpy()
+    from paper_2205_06649_gb300 import _abi
+    st_e = _abi.dd4dv_stats()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_controls(w_host)
+        ctx.reset_exchange()
+        ctx.outer_step(solver, st_e)
+        dd.lib.dd4dv_analysis(ctx._h, xa_host.ctypes.data, 0)
+    torch.cuda.synchronize()
+    e2e = {"value": st_e.pt_steps / (time.perf_counter() - t0), "unit": UNIT,
+           "h2d_bytes_per_step": int(ctx.ctrl_total * 8), "d2h_bytes_per_step": int(3 * wl.nlat * wl.nlon * 8),
+           "api": "set_controls(host) + reset_exchange + outer_step + analysis(host)"}
+    leg = {"n_sub": ctx.n_sub, "sweep_launch": ctx.sweep_config(), "pt_steps": ctx.pt_steps(),
+           "traj_bytes": ctx.traj_total * (8 if prec == 0 else 4), "roofline": roof, "e2e": e2e,
+           "clocks": clk.summary(), "launches": launches}
+    ctx.destroy()
+    torch.cuda.empty_cache()
+    extras = {} if args.no_extras or world > 1 else {"medium_legs": medium_extras(args, torch)}
+    line = headline_line(args, wl, prec, leg, pts_all / (t_max / 1e3), t_max, world, extras,
+                         cpu.result() if cpu else None)
+    line["config"]["step"] = (f"one DD-4DVar outer iteration from the start point ({wl.local_iters} batched "
+                              f"L-BFGS iterations over all {leg['n_sub']} subdomains + Exchange)")
+    line["config"]["evals_per_step"] = stats.evals / args.steps
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="medium")
+    ap.add_argument("--workload", default="large")
     ap.add_argument("--precision", default="f64", choices=["f64", "f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip FP32 and time-to-analysis legs")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other-precision leg and the medium-workload legs")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotune the sweep launch shapes instead of the stored defaults of the workload")
     ap.add_argument("--profile-evals", type=int, default=0,
                     help="only run this many evaluations (for an ncu launch list) and exit")
-    ap.add_argument("--mode", default="outer", choices=["outer", "eval", "scaleup", "tta"],
-                    help="outer: a step is one outer iteration (default); eval: a step is one batched "
-                         "J and grad J evaluation of all subdomains (for workloads too large for the "
-                         "outer-iteration bench); scaleup: the weak-scaling experiment of Table 3 "
-                         "(measured scale-up of one outer iteration, QP = 2..64); tta: time to analysis "
-                         "of the FP64 and FP32-state paths over --outer outer iterations")
+    ap.add_argument("--mode", default="eval", choices=["eval", "outer", "scaleup", "tta"],
+                    help="eval: a step is one batched J and grad J evaluation of all subdomains "
+                         "(default); outer: a step is one outer iteration of Algorithm 1; scaleup: the "
+                         "weak-scaling experiment of Table 3 (measured scale-up of one outer iteration, "
+                         "QP = 2..64); tta: time to analysis of the FP64 and FP32-state paths over "
+                         "--outer outer iterations")
     ap.add_argument("--outer", type=int, default=10, help="outer iterations of --mode tta")
     ap.add_argument("--shape32", default="", help="as --shape, for the FP32-state context of --mode tta")
     ap.add_argument("--ckpt", type=int, default=0, help="ckpt_k of the decomposition (0, -1 or k > 0)")
     ap.add_argument("--shape", default="",
                     help="fwd_cluster,fwd_threads,adj_cluster,adj_threads,stored_stages: force the "
-                         "sweep launch shapes (e.g. ones an autotuned run reported) instead of autotuning")
+                         "sweep launch shapes (e.g. ones an autotuned run reported)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -478,7 +798,6 @@ def main():
     torch.cuda.set_device(local_rank)
     import __graft_entry__ as g
     g.build()
-    import paper_2205_06649_gb300 as dd
 
     if args.mode == "scaleup":
         return scaleup_mode(args, torch) if rank == 0 else 0
@@ -487,172 +806,56 @@ def main():
 
     wl = workloads.preset(args.workload)
     prec = 0 if args.precision == "f64" else 1
-    stream = torch.cuda.Stream()
-    ctx, inp, truth, obs = build_problem(wl, prec, stream.cuda_stream, shape=args.shape, ckpt_k=args.ckpt)
-    solver = solver_for(wl)
-    zeros = torch.zeros(ctx.ctrl_total, dtype=torch.float64, device="cuda")
+    shape = args.shape or ("" if args.autotune else DEFAULT_SHAPES.get((wl.name, prec), ""))
 
     if args.profile_evals:
+        stream = torch.cuda.Stream()
+        ctx, _, _, _ = build_problem(wl, prec, stream.cuda_stream, shape=shape, ckpt_k=args.ckpt)
         w0 = np.zeros(ctx.ctrl_total)
         for _ in range(args.profile_evals):
             ctx.eval(w0)
         torch.cuda.synchronize()
-        log(f"profile run: {args.profile_evals} evaluations, cluster {ctx.cluster_size()}")
+        log(f"profile run: {args.profile_evals} evaluations, shapes {ctx.sweep_config()}")
+        ctx.destroy()
         return 0
 
-    if args.mode == "eval":
-        return eval_mode(args, ctx, wl, prec, stream, torch)
+    if args.mode == "outer":
+        args.shape = shape
+        return outer_mode(args, wl, prec, torch, world, rank, local_rank)
 
-    for _ in range(args.warmup):
-        ctx.set_controls(zeros)
-        ctx.reset_exchange()
-        ctx.outer_step(solver)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    with ClockSampler(local_rank) as clk:
-        ms, stats, launches = timed_steps(ctx, solver, args.steps, zeros, stream, torch)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    t_max, pts_all = aggregate_ranks(ms, float(stats.pt_steps), "cuda")
-    value = pts_all / (t_max / 1e3)
-    clocks = clk.summary()
+    inp = workloads.generate(wl)
+    cpu = None
 
-    line = None
+    def on_obs(obs):
+        nonlocal cpu
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            cpu = CpuBaseline(wl.name, obs[4], obs[5])
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    leg = eval_leg(args, wl, prec, inp, torch, shape, e2e=(rank == 0), on_obs=on_obs, barrier=barrier)
+    t_max, pts_all = aggregate_ranks(leg["ms"], float(leg["pt_steps"] * args.steps), "cuda")
+    extras = {}
+    if rank == 0 and not args.no_extras and world == 1:
+        other = 1 - prec
+        o = eval_leg(args, wl, other, inp, torch, DEFAULT_SHAPES.get((wl.name, other), ""),
+                     steps=min(args.steps, 10), warmup=min(args.warmup, 2))
+        extras["fp32_state" if other == 1 else "fp64"] = {
+            "value": o["pt_steps"] * o["steps"] / (o["ms"] / 1e3), "unit": UNIT,
+            "ms_per_step": o["ms"] / o["steps"], "steps": o["steps"],
+            "dtype": "f32 state, f64 reductions" if other == 1 else "f64",
+            "sweep_launch": o["sweep_launch"], "roofline": o["roofline"], "clocks": o["clocks"]}
+        extras["medium_legs"] = medium_extras(args, torch)
     if rank == 0:
-        # kernel timing (CUDA events around each sweep launch, same stream)
-        prof = ctx.profile_sweeps(np.zeros(ctx.ctrl_total), reps=5)
-        pts_eval = ctx.pt_steps()
-        kern = "adjoint" if prof["adjoint_ms"] >= prof["forward_ms"] else "forward"
-        t_k = prof[f"{kern}_ms"] / 1e3
-        peaks, peaks_kind = measured_peaks()
-        sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-        tsize = 8 if prec == 0 else 4
-        stored = ctx.sweep_config()["stored_stages"]
-        fl = FLOPS_STORED if stored else FLOPS
-        vals = VALUES_STORED if stored else VALUES_PER_PTSTEP
-        flops = fl[kern] * pts_eval / t_k
-        bytes_ = vals[kern] * tsize * pts_eval / t_k
-        hbm_peak = float(peaks["hbm_gbs"]) * 1e9
-        if prec == 0:
-            alu_peak = N_SM * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6
-        else:
-            alu_peak = N_SM * FP32_FLOP_PER_CLK_SM * sm_mhz * 1e6
-        alu_frac = flops / alu_peak
-        hbm_frac = bytes_ / hbm_peak
-        traffic = profile_summary_traffic(kern, source_hash(), "fp64" if prec == 0 else "fp32")
-        if alu_frac >= hbm_frac:
-            roof = {"bound": "alu", "achieved": flops / 1e12, "peak": alu_peak / 1e12, "unit": "TFLOP/s",
-                    "frac": alu_frac, "traffic": traffic, "kernel": f"{kern} sweep",
-                    "peak_source": f"derived: {N_SM} SMs x {FP64_FLOP_PER_CLK_SM if prec == 0 else FP32_FLOP_PER_CLK_SM:.0f} "
-                                   f"flop/clk x {sm_mhz:.0f} MHz ({'FP64' if prec == 0 else 'FP32'})",
-                    "hbm_frac_of_" + peaks_kind: hbm_frac}
-        else:
-            roof = {"bound": "hbm", "achieved": bytes_ / 1e9, "peak": hbm_peak / 1e9, "unit": "GB/s",
-                    "frac": hbm_frac, "traffic": traffic, "kernel": f"{kern} sweep",
-                    "peak_source": f"hbm_gbs of {peaks_kind}", "alu_frac": alu_frac}
-        roof["kernel_ms"] = prof[f"{kern}_ms"]
-        roof["algorithmic_per_pt_step"] = {"flops": fl[kern], "bytes": vals[kern] * tsize}
-        roof["sweeps_ms"] = {"forward": prof["forward_ms"], "adjoint": prof["adjoint_ms"],
-                             "eval": prof["eval_ms"]}
-
-        # end to end through the public API with host buffers: controls in
-        # (pinned host -> device), outer iteration, analysis out (device -> pinned host)
-        w_host = torch.zeros(ctx.ctrl_total, dtype=torch.float64).pin_memory().numpy()
-        xa_host = torch.zeros(3 * wl.nlat * wl.nlon, dtype=torch.float64).pin_memory().numpy()
-        from paper_2205_06649_gb300 import _abi
-        st_e = _abi.dd4dv_stats()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            ctx.set_controls(w_host)
-            ctx.reset_exchange()
-            ctx.outer_step(solver, st_e)
-            dd.lib.dd4dv_analysis(ctx._h, xa_host.ctypes.data, 0)
-        torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
-        e2e = {"value": st_e.pt_steps / t_e2e, "unit": UNIT,
-               "h2d_bytes_per_step": int(ctx.ctrl_total * 8),
-               "d2h_bytes_per_step": int(3 * wl.nlat * wl.nlon * 8),
-               "api": "set_controls(host) + reset_exchange + outer_step + analysis(host)"}
-
-        extras = {}
-        if not args.no_extras and world == 1:
-            # FP32-state path on the same step, and time to analysis at fixed RMSE
-            stream32 = torch.cuda.Stream()
-            ctx32, _, _, _ = build_problem(wl, 1, stream32.cuda_stream, inputs=inp)
-            zeros32 = torch.zeros(ctx32.ctrl_total, dtype=torch.float64, device="cuda")
-            for _ in range(2):
-                ctx32.set_controls(zeros32)
-                ctx32.reset_exchange()
-                ctx32.outer_step(solver)
-            ms32, st32, _ = timed_steps(ctx32, solver, args.steps, zeros32, stream32, torch)
-            prof32 = ctx32.profile_sweeps(np.zeros(ctx32.ctrl_total), reps=5)
-            extras["fp32_state"] = {"value": st32.pt_steps / (ms32 / 1e3), "unit": UNIT,
-                                    "ms_per_step": ms32 / args.steps, "dtype": "f32 state, f64 reductions",
-                                    "sweep_launch": ctx32.sweep_config(),
-                                    "sweeps_ms": {"forward": prof32["forward_ms"],
-                                                  "adjoint": prof32["adjoint_ms"],
-                                                  "eval": prof32["eval_ms"]}}
-            h64 = time_to_analysis(ctx, solver, truth[0], wl.max_outer, torch, stream, zeros)
-            h32 = time_to_analysis(ctx32, solver, truth[0], wl.max_outer, torch, stream32, zeros32)
-            target = 1.01 * h64[-1][1]
-            t64 = next(t for t, r, _ in h64 if r <= target)
-            t32 = next((t for t, r, _ in h32 if r <= target), None)
-            extras["time_to_analysis"] = {
-                "rmse_h_background": rmse_h(inp["x_b0"], truth[0]),
-                "rmse_h_fp64_final": h64[-1][1], "rmse_h_fp32_final": h32[-1][1],
-                "target_rmse_h": target, "fp64_s": t64, "fp32_s": t32,
-                "speedup": (t64 / t32) if t32 else None,
-                "outer_fp64": len(h64), "outer_fp32": len(h32)}
-            ctx32.destroy()
-            # Gauss-Newton local solver (Algorithms 6-7) on the FP64 path: one
-            # outer step timed like the L-BFGS step, and its time to the same
-            # analysis RMSE target
-            gn_solver = dd.solver_defaults(lbfgs_m=wl.lbfgs_m, max_local_iters=wl.local_iters,
-                                           max_outer=wl.max_outer, local_solver=1, gn_iters=3,
-                                           cg_iters=10, cg_tol=1e-6)
-            for _ in range(2):
-                ctx.set_controls(zeros)
-                ctx.reset_exchange()
-                ctx.outer_step(gn_solver)
-            ms_gn, st_gn, _ = timed_steps(ctx, gn_solver, args.steps, zeros, stream, torch)
-            hgn = time_to_analysis(ctx, gn_solver, truth[0], wl.max_outer, torch, stream, zeros)
-            tgn = next((t for t, r, _ in hgn if r <= target), None)
-            extras["gauss_newton"] = {
-                "settings": {"gn_iters": 3, "cg_iters": 10, "cg_tol": 1e-6},
-                "value": st_gn.pt_steps / (ms_gn / 1e3), "unit": UNIT, "ms_per_step": ms_gn / args.steps,
-                "pt_steps": "evaluations (forward + adjoint) and Gauss-Newton products (tangent-linear + "
-                            "adjoint) per subdomain",
-                "rmse_h_final": hgn[-1][1], "s_to_target": tgn, "outer": len(hgn),
-                "speedup_vs_lbfgs_fp64": (t64 / tgn) if tgn else None}
-
-        cpu = None
-        if not args.no_cpu_baseline and world == 1:
-            cpu = cpu_oracle_baseline(wl, inp)
-
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
-            "config": {"workload": wl_desc(wl), "precision": "fp64" if prec == 0 else "fp32-state",
-                       "step": "one DD-4DVar outer iteration from the start point (20 batched L-BFGS "
-                               "iterations over all 64 subdomains + Exchange)",
-                       "sweep_launch": ctx.sweep_config(),
-                       "pt_steps_per_eval": pts_eval, "evals_per_step": stats.evals / args.steps,
-                       "l2": "inputs larger than L2: FP64 trajectories + overlap targets "
-                             f"{2 * 8 * ctx.traj_total / 1e6:.0f} MB",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": int(launches), **extras,
-        }
+        line = headline_line(args, wl, prec, leg, pts_all / (t_max / 1e3), t_max, world, extras,
+                             cpu.result() if cpu else None)
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-    ctx.destroy()
     return 0
 
 

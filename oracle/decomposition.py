@@ -20,7 +20,7 @@ that the weights of every point sum to one (Eq. rest).
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List, Sequence
+from typing import List, Optional, Sequence
 
 import numpy as np
 
@@ -144,12 +144,13 @@ def bilinear_support(fi: float, fj: float, nlon: int):
 
 
 def obs_membership(dec: Decomposition, level: Sequence[int], fi: Sequence[float],
-                   fj: Sequence[float]):
+                   fj: Sequence[float], subs: Optional[Sequence[Sub]] = None):
     """For each observation, the subdomains that contain it: its level in
     the window and every non-zero-weight bilinear corner in the box.
     Returns a list (one entry per observation) of lists of subdomain indices.
     (Same test as bilinear_support + Sub.local_row/local_col, evaluated for
-    all observations of one subdomain at a time.)"""
+    all observations of one subdomain at a time.)  subs: test only these
+    subdomains (default: all of dec)."""
     level = np.asarray(level)
     fi = np.asarray(fi, dtype=np.float64)
     fj = np.asarray(fj, dtype=np.float64)
@@ -159,7 +160,7 @@ def obs_membership(dec: Decomposition, level: Sequence[int], fi: Sequence[float]
     has_j1 = (fj - j0) != 0.0
     i1 = (i0 + 1) % dec.nlon
     members = [[] for _ in range(len(level))]
-    for s in dec.subs:
+    for s in (dec.subs if subs is None else subs):
         in_t = (level >= s.a) & (level <= s.b)
         k0 = (i0 - s.i0) % dec.nlon
         k1 = (i1 - s.i0) % dec.nlon
@@ -181,6 +182,16 @@ class Overlap:
     cols_s: np.ndarray
     rows_t: np.ndarray
     cols_t: np.ndarray
+
+
+def meets(s: Sub, t: Sub) -> bool:
+    """Whether the windows x boxes of s and t share a point."""
+    if max(s.a, t.a) > min(s.b, t.b):
+        return False
+    if max(s.j0, t.j0) >= min(s.j0 + s.ny, t.j0 + t.ny):
+        return False
+    cols = set(int(i) for i in t.cols())
+    return any(int(i) in cols for i in s.cols())
 
 
 def overlaps_of(dec: Decomposition, s: Sub) -> List[Overlap]:

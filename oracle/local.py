@@ -38,7 +38,7 @@ import numpy as np
 import torch
 
 from .bcov import BOp
-from .decomposition import Decomposition, Sub, bilinear_support, obs_membership, overlaps_of
+from .decomposition import Decomposition, Sub, bilinear_support, meets, obs_membership, overlaps_of
 from .swe import BoxGeom, Ghosts, Grid, global_forward, rk3_step
 
 F64 = torch.float64
@@ -76,7 +76,15 @@ class Setup:
 
     def __init__(self, grid: Grid, dt: float, nsteps: int, xb0, obs: Observations,
                  sigma_b, dec: Decomposition, corr_len: float = 0.0, rf_passes: int = 4,
-                 lam: float = 1.0, mu: float = 1.0, weight_obs: bool = True):
+                 lam: float = 1.0, mu: float = 1.0, weight_obs: bool = True,
+                 sample: Optional[Sequence[int]] = None):
+        """sample: build the local problems of these subdomains only (a
+        bounded piece of a workload too large to set up whole).  Then
+        ``locals`` holds those problems in the given order, the background
+        trajectory stops at the last level they reach, and observation
+        weights are counted over the subdomains that meet them (every
+        subdomain that contains one of their observations meets them), so
+        each sampled local problem is the same as in the full setup."""
         self.grid = grid
         self.dt = float(dt)
         self.nsteps = nsteps
@@ -88,9 +96,18 @@ class Setup:
         self.rf_passes = rf_passes
         self.lam = lam
         self.mu = mu
+        self.sample = None if sample is None else [int(s) for s in sample]
+        if self.sample is None:
+            chosen = list(dec.subs)
+            near = None
+            bg_steps = nsteps
+        else:
+            chosen = [dec.subs[s] for s in self.sample]
+            near = [t for t in dec.subs if any(meets(s, t) for s in chosen)]
+            bg_steps = max(s.b for s in chosen)
         with torch.no_grad():
-            self.xb_traj = global_forward(grid, self.xb0, self.dt, nsteps)
-        members = obs_membership(dec, obs.level, obs.fi, obs.fj)
+            self.xb_traj = global_forward(grid, self.xb0, self.dt, bg_steps)
+        members = obs_membership(dec, obs.level, obs.fi, obs.fj, subs=near)
         self.obs_members = members
         self.obs_of_sub = [[] for _ in dec.subs]
         for k, m in enumerate(members):
@@ -98,13 +115,26 @@ class Setup:
                 self.obs_of_sub[s].append(k)
         self.obs_weight = np.array([(1.0 / len(m) if (m and weight_obs) else (1.0 if m else 0.0))
                                     for m in members])
-        self.locals = [LocalProblem(self, sub) for sub in dec.subs]
+        self._near = near
+        self.locals = [LocalProblem(self, sub) for sub in chosen]
 
-    def background_prev(self) -> List[torch.Tensor]:
+    def background_prev(self):
         """Trajectories of the outer iteration 'before the first' (l = 0):
         every subdomain's restriction of the background trajectory u^b
-        (Algorithm 1: u_ji^0 = u_ji^b)."""
-        return [lp.restrict_traj(self.xb_traj) for lp in self.locals]
+        (Algorithm 1: u_ji^0 = u_ji^b).  A list over all subdomains; with a
+        sample, a dict over the subdomains that meet it (the only neighbour
+        trajectories its overlap terms read), cut at the background's last
+        level."""
+        if self.sample is None:
+            return [lp.restrict_traj(self.xb_traj) for lp in self.locals]
+        return {t.index: restrict(self.xb_traj, t) for t in self._near}
+
+
+def restrict(traj: torch.Tensor, s: Sub) -> torch.Tensor:
+    """RO of a global trajectory to subdomain s's window x box (levels past
+    the end of traj are left out)."""
+    cols = torch.as_tensor(s.cols(), dtype=torch.long)
+    return traj[s.a:s.b + 1][:, :, s.j0:s.j0 + s.ny][:, :, :, cols].clone()
 
 
 class LocalProblem:

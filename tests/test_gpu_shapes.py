@@ -1,0 +1,153 @@
+"""GPU parity in the launch shapes the big workloads run: 8- and 16-CTA
+clusters, 384 and 512 threads per CTA, stage states stored by the forward
+sweep or recomputed in the adjoint, and k-step checkpoints.  The batching and
+large workloads are too big for the oracle, so their shapes run here on
+workloads the oracle evaluates: every subdomain of the ragged workload
+(boxes of 20-22 rows, so a 16-CTA cluster gives stripes of one and two rows)
+and sampled subdomains of the medium workload at full size.
+
+Bars: FP64 J within 1e-11 relative, grad J within 1e-9 relative (2-norm);
+FP32-state path J within 1e-5 relative and grad J within 2e-3 relative (the
+state arithmetic is FP32; the gradient of a functional evaluated in FP32
+carries its rounding).  The FP32 path's analysis RMSE must also stay within
+1 % of the FP64 oracle's analysis RMSE (spec gate), checked on the
+small workload through Algorithm 1 end to end.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from _helpers import rand_w, rel
+
+pytestmark = pytest.mark.gpu
+
+FP64_BARS = (1e-11, 1e-9)
+FP32_BARS = (1e-5, 2e-3)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _ctx(wl, st, inp, precision, ckpt_k):
+    import paper_2205_06649_gb300 as dd
+    ctx = dd.Context(wl.nlon, wl.nlat, inp["dt"], wl.nsteps, precision=precision)
+    ctx.set_background(inp["x_b0"])
+    ctx.set_background_error(wl.sigma_b, wl.corr_len, wl.rf_passes)
+    ob = st.obs
+    ctx.set_observations(ob.level, ob.var, ob.fi, ob.fj, ob.value, ob.sigma_o)
+    ctx.set_decomposition(wl.P1, wl.P2, wl.Q, wl.o_lon, wl.o_lat, wl.o_t, inp["lon_cuts"],
+                          inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam, cluster=2,
+                          ckpt_k=ckpt_k)
+    return ctx
+
+
+_CACHE = {}
+
+
+def _problem(name):
+    """Oracle setup, controls and oracle J / grad J of the sampled subdomains
+    (computed once per workload)."""
+    if name not in _CACHE:
+        wl = workloads.preset(name)
+        st, inp, truth = oracle.build_setup(wl)
+        w = np.concatenate([rand_w(lp.nctrl, seed=1500 + s, scale=0.3).numpy()
+                            for s, lp in enumerate(st.locals)])
+        samples = list(range(len(st.locals))) if name == "ragged" else [0, 5, 21, 42, 58, 63]
+        prev = st.background_prev()
+        offs = np.cumsum([0] + [lp.nctrl for lp in st.locals])
+        ref = {}
+        for s in samples:
+            J, g, _ = st.locals[s].J_and_grad(w[offs[s]:offs[s + 1]], st.xb_traj, prev)
+            ref[s] = (J, g.numpy())
+        _CACHE[name] = (wl, st, inp, w, ref)
+    return _CACHE[name]
+
+
+def _check(ctx, w, ref, bars, label):
+    jtol, gtol = bars
+    J, g = ctx.eval(w)
+    gs = ctx.split_controls(g)
+    for s, (Jo, go) in ref.items():
+        assert abs(J[s] - Jo) <= jtol * abs(Jo), (label, s, J[s], Jo)
+        assert rel(gs[s], go) <= gtol, (label, s, rel(gs[s], go))
+    return J, g
+
+
+@pytest.mark.parametrize("name", ["ragged", "medium"])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_big_cluster_shapes_match_oracle(name, precision):
+    """8- and 16-CTA clusters at 384 and 512 threads, stored and recomputed
+    stage states (ckpt_k = 0 with and without the stage buffer in use), all
+    against the oracle; the gradient does not depend on the stage mode."""
+    wl, st, inp, w, ref = _problem(name)
+    bars = FP64_BARS if precision == 0 else FP32_BARS
+    fwd_max = 512 if precision == 0 else 384
+    ctx = _ctx(wl, st, inp, precision, ckpt_k=0)
+    try:
+        grads = {}
+        for cl in (8, 16):
+            for nt in (384, 512):
+                for stored in (True, False):
+                    ctx.set_sweep_config((cl, min(nt, fwd_max)), (cl, nt), stored)
+                    label = (name, precision, cl, nt, stored)
+                    _, g = _check(ctx, w, ref, bars, label)
+                    grads.setdefault((cl, nt), []).append(g)
+        for (cl, nt), (g_st, g_rc) in grads.items():
+            assert np.array_equal(g_st, g_rc), (cl, nt)
+    finally:
+        ctx.destroy()
+
+
+@pytest.mark.parametrize("name,precision,ckpt_k", [
+    ("ragged", 0, -1), ("ragged", 1, -1), ("medium", 0, -1),
+    ("ragged", 0, 5), ("medium", 1, 16),
+])
+def test_recomputed_and_checkpointed_adjoint_at_big_clusters(name, precision, ckpt_k):
+    """ckpt_k = -1 (every level stored, stages recomputed: the large
+    workload's FP64 mode) and k-step checkpoint segments, in 16-CTA clusters
+    of 512 threads (the forward of the FP32 path at 384)."""
+    wl, st, inp, w, ref = _problem(name)
+    bars = FP64_BARS if precision == 0 else FP32_BARS
+    ctx = _ctx(wl, st, inp, precision, ckpt_k=ckpt_k)
+    try:
+        ctx.set_sweep_config((16, 512 if precision == 0 else 384), (16, 512), False)
+        _check(ctx, w, ref, bars, (name, precision, ckpt_k))
+    finally:
+        ctx.destroy()
+
+
+def test_fp32_analysis_rmse_within_one_percent_of_fp64_oracle():
+    """North-star gate of the FP32-state path: Algorithm 1 end to end on the
+    small workload (batched device L-BFGS, Exchange, Gather); the analysis
+    RMSE of h at t0 against the truth is within 1 % of that of the FP64
+    oracle's own outer loop with the same settings, and both improve on the
+    background."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("small")
+    st, inp, truth = oracle.build_setup(wl)
+    outer, local = 3, 20
+    ref = oracle.dd4dvar(st, max_outer=outer, eps=0.0, local_iters=local, m=5, gtol=1e-6)
+    t0 = truth[0].numpy()
+
+    def rmse_h(x):
+        return float(np.sqrt(np.mean((np.asarray(x)[0] - t0[0]) ** 2)))
+
+    r_bg = rmse_h(inp["x_b0"])
+    r_or = rmse_h(ref.xa0.numpy())
+    ctx = _ctx(wl, st, inp, 1, ckpt_k=0)
+    try:
+        solver = dd.solver_defaults(lbfgs_m=5, max_local_iters=local, max_outer=outer, eps_outer=0.0)
+        xa, stats, _ = ctx.run(solver)
+    finally:
+        ctx.destroy()
+    r32 = rmse_h(xa)
+    assert stats.outer_iters == outer
+    assert r_or < r_bg and r32 < r_bg, (r_bg, r_or, r32)
+    assert abs(r32 - r_or) <= 0.01 * r_or, (r32, r_or)

@@ -232,3 +232,24 @@ def test_local_observation_term_vanishes_on_exact_bilinear_data():
             assert float(lp.obs_term(n, xbox)) <= 1e-24
             seen += len(lp.obs_arrays[n]["y"])
     assert seen >= len(y)
+
+
+def test_sampled_setup_gives_the_full_setups_local_problems():
+    """The bounded setup used for CPU timing of big workloads (local problems
+    of a few subdomains, background run cut at their last level, observation
+    weights counted over the subdomains that meet them) gives each sampled
+    subdomain exactly the J and grad J of the full setup."""
+    w = workloads.preset("ragged")
+    st, inp, _ = oracle.build_setup(w)
+    sample = [0, 4, 7]
+    sm = oracle.Setup(st.grid, st.dt, st.nsteps, inp["x_b0"], st.obs, w.sigma_b, st.dec,
+                      corr_len=w.corr_len, rf_passes=w.rf_passes, lam=w.lam, mu=w.mu, sample=sample)
+    assert sm.xb_traj.shape[0] == max(st.dec.subs[s].b for s in sample) + 1 < st.xb_traj.shape[0]
+    prev_full, prev_s = st.background_prev(), sm.background_prev()
+    for lp_s, s in zip(sm.locals, sample):
+        lp = st.locals[s]
+        assert lp_s.sub.index == s
+        x = torch.as_tensor(np.random.default_rng(s).standard_normal(lp.nctrl) * 0.4)
+        J, g, parts = lp.J_and_grad(x, st.xb_traj, prev_full)
+        Js, gs, parts_s = lp_s.J_and_grad(x, sm.xb_traj, prev_s)
+        assert J == Js and parts == parts_s and torch.equal(g, gs)
