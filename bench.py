@@ -812,9 +812,12 @@ def main():
         stream = torch.cuda.Stream()
         ctx, _, _, _ = build_problem(wl, prec, stream.cuda_stream, shape=shape, ckpt_k=args.ckpt)
         w0 = np.zeros(ctx.ctrl_total)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("evals")   # ncu --nvtx --nvtx-include "evals/" selects these
         for _ in range(args.profile_evals):
             ctx.eval(w0)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         log(f"profile run: {args.profile_evals} evaluations, shapes {ctx.sweep_config()}")
         ctx.destroy()
         return 0
