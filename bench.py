@@ -442,10 +442,11 @@ def timed_evals(ctx, w, steps, stream, torch):
     return e0.elapsed_time(e1), ctx.launch_count() - l0
 
 
-def e2e_evals(ctx, w_dev, steps, torch):
+def e2e_evals(ctx, w_dev, steps, torch, pts_per_eval=None, barrier=None):
     """The same evaluations through the public C call with HOST buffers:
     each step copies the controls in from pinned host memory and J and the
-    gradient out to pinned host memory (dd4dv_eval, device_ptrs = 0)."""
+    gradient out to pinned host memory (dd4dv_eval, device_ptrs = 0).
+    Returns the line's e2e object and (pt-steps, seconds) of this rank."""
     import ctypes as C
     import paper_2205_06649_gb300 as dd
     w_h = torch.empty(ctx.ctrl_total, dtype=torch.float64).pin_memory()
@@ -453,6 +454,8 @@ def e2e_evals(ctx, w_dev, steps, torch):
     J_h = torch.empty(ctx.n_sub, dtype=torch.float64).pin_memory()
     g_h = torch.empty(ctx.ctrl_total, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     t0 = time.perf_counter()
     for _ in range(steps):
         st = dd.lib.dd4dv_eval(ctx._h, C.c_void_p(w_h.data_ptr()), C.c_void_p(J_h.data_ptr()),
@@ -460,14 +463,15 @@ def e2e_evals(ctx, w_dev, steps, torch):
         if st != 0:
             raise RuntimeError(ctx.last_error())
     t = time.perf_counter() - t0
-    return {"value": ctx.pt_steps() * steps / t, "unit": UNIT,
+    pts = (ctx.pt_steps() if pts_per_eval is None else pts_per_eval) * steps
+    return {"value": pts / t, "unit": UNIT,
             "h2d_bytes_per_step": int(ctx.ctrl_total * 8),
             "d2h_bytes_per_step": int((ctx.n_sub + ctx.ctrl_total) * 8),
-            "api": "dd4dv_eval with host buffers (controls in, J and gradient out, pinned)"}
+            "api": "dd4dv_eval with host buffers (controls in, J and gradient out, pinned)"}, (pts, t)
 
 
 def eval_leg(args, wl, prec, inp, torch, shape, e2e=False, on_obs=None, barrier=None, steps=None,
-             warmup=None):
+             warmup=None, transport=None):
     """One context on the workload: warm-up, timed evaluations (and
     optionally the end-to-end leg), roofline of the dominant sweep.
     on_obs(obs) runs once the observations exist; barrier() runs on both
@@ -481,6 +485,16 @@ def eval_leg(args, wl, prec, inp, torch, shape, e2e=False, on_obs=None, barrier=
     ctx._bench_workload = wl.name
     if on_obs:
         on_obs(obs)
+    pts_rank = ctx.pt_steps()
+    if transport is not None and transport.world > 1:
+        # this rank evaluates its block of the problem's subdomains
+        from paper_2205_06649_gb300 import sharded
+        s0, s1, _ = sharded.owned_block(ctx, transport)
+        owned = np.zeros(ctx.n_sub, dtype=np.int32)
+        owned[s0:s1] = 1
+        ctx.set_owned(owned)
+        b = np.asarray(ctx.boxes).astype(np.int64)
+        pts_rank = int(np.sum(b[s0:s1, 1] * b[s0:s1, 3] * (b[s0:s1, 5] - b[s0:s1, 4])))
     rng = np.random.default_rng(0)
     w = torch.tensor(0.3 * rng.standard_normal(ctx.ctrl_total), device="cuda")
     for _ in range(warmup):
@@ -492,12 +506,16 @@ def eval_leg(args, wl, prec, inp, torch, shape, e2e=False, on_obs=None, barrier=
         ms, launches = timed_evals(ctx, w, steps, stream, torch)
     if barrier:
         barrier()
-    out = {"ms": ms, "steps": steps, "launches": launches, "clocks": clk.summary(), "pt_steps": ctx.pt_steps(),
+    out = {"ms": ms, "steps": steps, "launches": launches, "clocks": clk.summary(), "pt_steps": pts_rank,
            "n_sub": ctx.n_sub, "sweep_launch": ctx.sweep_config(),
            "traj_bytes": ctx.traj_total * (8 if prec == 0 else 4)}
+    if transport is not None and transport.world > 1:
+        ctx.set_owned(None)   # the roofline times the sweeps over the whole problem
     out["roofline"] = roofline_of(ctx, prec)
     if e2e:
-        out["e2e"] = e2e_evals(ctx, w, min(steps, 5), torch)
+        if transport is not None and transport.world > 1:
+            ctx.set_owned(owned)
+        out["e2e"], out["e2e_rank"] = e2e_evals(ctx, w, min(steps, 5), torch, pts_rank, barrier)
     ctx.destroy()
     del w
     torch.cuda.empty_cache()
@@ -679,7 +697,7 @@ def headline_line(args, wl, prec, leg, value, t_max, world, extras, cpu):
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "scaling": "strong", "vs_baseline": None,
         "dtype": "f64" if prec == 0 else "f32", "data": "synthetic",
         "config": {"workload": wl_desc(wl), "precision": "fp64" if prec == 0 else "fp32-state",
                    "step": f"one batched J and grad J evaluation of all {leg['n_sub']} subdomains "
@@ -687,7 +705,9 @@ def headline_line(args, wl, prec, leg, value, t_max, world, extras, cpu):
                            "sweeps, V^T), controls resident in HBM",
                    "sweep_launch": leg["sweep_launch"], "pt_steps_per_eval": leg["pt_steps"],
                    "l2": f"inputs larger than L2: trajectories {leg['traj_bytes'] / 1e9:.0f} GB",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": (f"subdomains sharded over {world} ranks (contiguous blocks balanced by "
+                                   "pt-steps; no data-path collective within an evaluation)")
+                                  if world > 1 else "single GPU"},
         "roofline": leg["roofline"], "cpu_baseline": cpu, "e2e": leg.get("e2e"), "clocks": leg["clocks"],
         "gpu_launches": int(leg["launches"]), **extras,
     }
@@ -751,6 +771,9 @@ def outer_mode(args, wl, prec, torch, world, rank, local_rank):
                          cpu.result() if cpu else None)
     line["config"]["step"] = (f"one DD-4DVar outer iteration from the start point ({wl.local_iters} batched "
                               f"L-BFGS iterations over all {leg['n_sub']} subdomains + Exchange)")
+    if world > 1:   # this mode runs one independent problem per rank
+        line["scaling"] = "weak"
+        line["config"]["parallelism"] = f"replicas x{world} (independent problems)"
     line["config"]["evals_per_step"] = stats.evals / args.steps
     print(json.dumps(line), flush=True)
     return 0
@@ -839,8 +862,17 @@ def main():
         if world > 1:
             dist.barrier()
 
-    leg = eval_leg(args, wl, prec, inp, torch, shape, e2e=(rank == 0), on_obs=on_obs, barrier=barrier)
+    transport = None
+    if world > 1:
+        from paper_2205_06649_gb300 import sharded
+        transport = sharded.TorchDistTransport()
+    leg = eval_leg(args, wl, prec, inp, torch, shape, e2e=True, on_obs=on_obs, barrier=barrier,
+                   transport=transport)
     t_max, pts_all = aggregate_ranks(leg["ms"], float(leg["pt_steps"] * args.steps), "cuda")
+    if world > 1:
+        e_pts, e_s = leg["e2e_rank"]
+        e_t, e_p = aggregate_ranks(e_s, float(e_pts), "cuda")
+        leg["e2e"]["value"] = e_p / e_t
     extras = {}
     if rank == 0 and not args.no_extras and world == 1:
         other = 1 - prec

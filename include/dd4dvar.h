@@ -295,6 +295,29 @@ dd4dv_status dd4dv_observe(dd4dv_ctx* ctx, const double* traj, long long n, cons
  * otherwise its counters are incremented (zero it before the first call). */
 dd4dv_status dd4dv_outer_step(dd4dv_ctx* ctx, const dd4dv_solver* solver, dd4dv_stats* stats);
 
+/* Sharding the subdomains of one problem over several contexts (one per GPU;
+ * the outer loop of Algorithm 1 with the local problems distributed, as the
+ * paper's processors own subdomains in Sec. 7).  owned: host array of n_sub
+ * flags (1 = this context evaluates and solves the subdomain), NULL = all
+ * (the default after dd4dv_set_decomposition).  With a subset owned,
+ * dd4dv_eval, dd4dv_eval_forward / _backward and dd4dv_local_solve work on the
+ * owned subdomains only (the J, parts and gradient entries of the others are
+ * left as they were), dd4dv_exchange still uses every subdomain's control,
+ * and dd4dv_outer_step / dd4dv_run return DD4DV_ESTATE.  EINVAL if a flag is
+ * not 0 or 1. */
+dd4dv_status dd4dv_set_owned(dd4dv_ctx* ctx, const int* owned);
+
+/* The local part of one outer iteration of Algorithm 1: the batched L-BFGS
+ * of dd4dv_outer_step on every owned subdomain from its current control,
+ * without the Exchange.  A sharded outer iteration is: dd4dv_local_solve on
+ * each context, an all-gather of the owned control blocks (layout of
+ * dd4dv_control_layout), dd4dv_set_controls and dd4dv_exchange with the full
+ * vector on each context; every context then holds the same exchange state
+ * as one context running dd4dv_outer_step, bit for bit.  stats (may be NULL)
+ * counts the owned subdomains' work and J; dw_inf and outer_iters are left
+ * to the caller.  EINVAL for local_solver != 0. */
+dd4dv_status dd4dv_local_solve(dd4dv_ctx* ctx, const dd4dv_solver* solver, dd4dv_stats* stats);
+
 /* Algorithm 1: outer iterations until max_s ||w^l - w^(l-1)||_inf < eps_outer
  * or max_outer, then the Gather: xa0 [3][nlat][nlon] (host, may be NULL) is
  * the analysis at t0 = the partition-of-unity sum of the first window's
@@ -333,11 +356,28 @@ dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* ctx, int* shape, double* eval_m
 
 /* Force launch shapes (e.g. ones an earlier autotuning run reported), same
  * layout as dd4dv_sweep_config: cluster sizes 1..16 (<= smallest box height),
- * threads a multiple of 32 in 64..512 (forward sweep of the FP32-state path:
- * at most 384), stored stages 1 only with ckpt_k = 0 and the stage buffer
- * present; DD4DV_EINVAL otherwise.  Results are the same for every shape up
- * to the order of the per-CTA partial sums of J. */
+ * threads a multiple of 32 in 64..640 (the stripe sweeps take at most 512,
+ * 384 for the FP32-state forward; more need the deep-halo FP32 sweeps, see
+ * dd4dv_set_sweep_variant), stored stages 1 only with ckpt_k = 0 and the
+ * stage buffer present; DD4DV_EINVAL for a shape no kernel can run.  Results
+ * are the same for every shape up to the order of the partial sums of J. */
 dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape);
+
+/* Sweep kernels (FP32-state path).  The library has two forms of the forward
+ * and adjoint sweeps.  The stripe sweeps exchange one halo row between the
+ * CTAs of a subdomain after every RK3 stage.  The deep-halo sweeps (FP32
+ * state only) keep three halo rows, recompute the two rows next to each
+ * neighbour edge in the first two stages and exchange once per step; they
+ * run where every CTA stripe has at least 3 rows, a thread holds at most 4
+ * own points and (adjoint) the stage states are stored (ckpt_k = 0, no
+ * Gauss-Newton or external forcing).  Both give the same values bit for bit.
+ * variant: 0 = deep-halo sweeps wherever they apply (default), 1 = stripe
+ * sweeps only.  EINVAL for other values. */
+dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int variant);
+
+/* Which kernels the current launch shapes run: kinds[0] forward, kinds[1]
+ * adjoint; 1 = stripe sweep, 2 = deep-halo sweep. */
+dd4dv_status dd4dv_sweep_kernels(const dd4dv_ctx* ctx, int* kinds);
 
 /* The cluster size (CTAs per subdomain) the sweeps use. */
 dd4dv_status dd4dv_cluster_size(const dd4dv_ctx* ctx, int* n);

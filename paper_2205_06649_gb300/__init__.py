@@ -176,6 +176,16 @@ class Context:
         self.traj_total = int(self.traj_offsets[-1])
 
     # ---- queries ----
+    def set_sweep_variant(self, variant: int):
+        """0: deep-halo FP32 sweeps wherever they apply (default); 1: stripe sweeps only."""
+        self._check(lib.dd4dv_set_sweep_variant(self._h, int(variant)))
+
+    def sweep_kernels(self) -> dict:
+        """Kernels the current shapes run: 1 = stripe sweep, 2 = deep-halo sweep."""
+        k = np.zeros(2, dtype=np.int32)
+        self._check(lib.dd4dv_sweep_kernels(self._h, C.c_void_p(k.ctypes.data)))
+        return {"forward": int(k[0]), "adjoint": int(k[1])}
+
     def cluster_size(self) -> int:
         """Cluster size of the adjoint sweep."""
         n = C.c_int()
@@ -398,6 +408,24 @@ class Context:
         return out
 
     # ---- outer loop (Alg. 1) ----
+    def set_owned(self, owned=None):
+        """Subdomains this context evaluates and solves (n_sub flags; None = all)."""
+        if owned is None:
+            self._check(lib.dd4dv_set_owned(self._h, None))
+            return
+        m = np.ascontiguousarray(owned, dtype=np.int32)
+        if m.shape != (self.n_sub,):
+            raise ValueError(f"owned must have {self.n_sub} entries")
+        self._check(lib.dd4dv_set_owned(self._h, C.c_void_p(m.ctypes.data)))
+
+    def local_solve(self, solver=None, stats=None):
+        """Batched L-BFGS on the owned subdomains (one outer iteration without the Exchange)."""
+        self._fwd_token += 1
+        solver = solver or solver_defaults()
+        stats = stats if stats is not None else _abi.dd4dv_stats()
+        self._check(lib.dd4dv_local_solve(self._h, C.byref(solver), C.byref(stats)))
+        return stats
+
     def outer_step(self, solver=None, stats=None):
         self._fwd_token += 1
         solver = solver or solver_defaults()

@@ -73,6 +73,7 @@ struct dd4dv_ctx {
   int cl = 1, R = 1, W = 3, nthreads = 256;        // adjoint (and TLM base) sweep shape
   int cl_f = 1, R_f = 1, nt_f = 256;               // forward sweep shape
   double tune_ms = 0.0;
+  int variant = 0;            // 0: deep-halo FP32 sweeps where they apply; 1: stripe sweeps only
   size_t tsize = 8;
 
   void* traj = nullptr;
@@ -103,6 +104,9 @@ struct dd4dv_ctx {
   CgState* cgst = nullptr;
   void* gn_dx = nullptr;
   int* phase_d = nullptr;
+  int* owned_d = nullptr;     // [n_sub] 1 = this context evaluates and solves the subdomain
+  std::vector<int> owned_h;
+  bool owned_all = true;      // every subdomain owned (the default)
   int* counter_d = nullptr;
   int* counter_h = nullptr;   // pinned
   int* phase_h = nullptr;     // pinned
@@ -115,8 +119,8 @@ struct dd4dv_ctx {
   // captured CUDA graphs of the outer iteration (start evaluation, L-BFGS
   // direction, one line-search trial, exchange), valid for one solver setting
   struct Graphs {
-    cudaGraphExec_t start = nullptr, dir = nullptr, trial = nullptr, exch = nullptr;
-    long long k_start = 0, k_dir = 0, k_trial = 0, k_exch = 0;
+    cudaGraphExec_t start = nullptr, dir = nullptr, trial = nullptr, exch = nullptr, fin = nullptr;
+    long long k_start = 0, k_dir = 0, k_trial = 0, k_exch = 0, k_fin = 0;
     dd4dv_solver key{};
     bool valid = false;
   } og;
@@ -282,6 +286,8 @@ SweepArgs<T> sweep_args(dd4dv_ctx* ctx) {
   a.R = ctx->R;
   a.W = ctx->W;
   a.err = ctx->err_d;
+  a.min_ny = ctx->min_ny;
+  a.variant = ctx->variant;
   return a;
 }
 
@@ -538,6 +544,10 @@ void background_pass(dd4dv_ctx* ctx, bool xb_a) {
   });
 }
 
+// Ownership mask for evaluations: nullptr when the context owns every
+// subdomain (the unmasked launches), else the device mask (value 1 = owned).
+const int* own_mask(dd4dv_ctx* ctx) { return ctx->owned_all ? nullptr : ctx->owned_d; }
+
 // Copies a host input into a device buffer when device_ptrs == 0.
 const double* stage_in(dd4dv_ctx* ctx, const double* src, double* buf, size_t n, int device_ptrs) {
   if (device_ptrs) return src;
@@ -549,6 +559,26 @@ template <typename F>
 auto by_precision(dd4dv_ctx* ctx, F&& f) {
   if (ctx->m.precision == 1) return f(float{});
   return f(double{});
+}
+
+// Kernel kinds (forward_kind / adjoint_kind: 0 = not launchable, 1 = stripe
+// sweep, 2 = deep-halo FP32 sweep) of the sweeps at c CTAs per subdomain and
+// nt threads per CTA, with the context's current stage-buffer use.
+int fwd_kind_at(dd4dv_ctx* ctx, int c, int nt) {
+  return by_precision(ctx, [&](auto t) {
+    using T = decltype(t);
+    SweepArgs<T> a = sweep_args<T>(ctx);
+    a.R = (ctx->max_ny + c - 1) / c;
+    return forward_kind<T>(a, c, nt);
+  });
+}
+int adj_kind_at(dd4dv_ctx* ctx, int c, int nt) {
+  return by_precision(ctx, [&](auto t) {
+    using T = decltype(t);
+    SweepArgs<T> a = sweep_args<T>(ctx);
+    a.R = (ctx->max_ny + c - 1) / c;
+    return adjoint_kind<T>(a, c, nt);
+  });
 }
 
 // The project's autotuner: for every feasible launch shape -- cluster size
@@ -567,15 +597,19 @@ void autotune(dd4dv_ctx* ctx) {
   CK(cudaMemsetAsync(ctx->io_a, 0, ctx->ctrl_total * sizeof(double), ctx->st));
   cudaEvent_t ev[4];
   for (auto& e : ev) CK(cudaEventCreate(&e));
-  auto smem_f = [&](int R) { return f32 ? smem_forward<float>(R, ctx->W) : smem_forward<double>(R, ctx->W); };
   auto smem_a = [&](int R) { return f32 ? smem_adjoint<float>(R, ctx->W) : smem_adjoint<double>(R, ctx->W); };
   // one evaluation's kernels at the shape (c, nt); returns false if not launchable
   auto run = [&](int c, int nt, float* tf, float* ta) -> bool {
     const int R = (ctx->max_ny + c - 1) / c;
+    // the forward takes nt threads where its kernel allows them, else the
+    // largest count its stripe kernel allows
+    const int ntf = fwd_kind_at(ctx, c, nt) ? nt
+                    : std::min(nt, f32 ? max_threads_forward<float>() : max_threads_forward<double>());
+    if (!fwd_kind_at(ctx, c, ntf) || !adj_kind_at(ctx, c, nt)) return false;
     ctx->cl_f = ctx->cl = c;
     ctx->R_f = ctx->R = R;
     ctx->nthreads = nt;
-    ctx->nt_f = std::min(nt, f32 ? max_threads_forward<float>() : max_threads_forward<double>());
+    ctx->nt_f = ntf;
     try {
       by_precision(ctx, [&](auto tt) {
         using T = decltype(tt);
@@ -601,14 +635,16 @@ void autotune(dd4dv_ctx* ctx) {
   };
   std::vector<int> cls;
   for (int c : {1, 2, 3, 4, 5, 6, 7, 8, 16})
-    if (c <= ctx->min_ny && smem_a((ctx->max_ny + c - 1) / c) <= (size_t)cap) cls.push_back(c);
-  const int nts[] = {512, 448, 384, 320, 256, 192};
+    if (c <= ctx->min_ny && (smem_a((ctx->max_ny + c - 1) / c) <= (size_t)cap || adj_kind_at(ctx, c, 512)))
+      cls.push_back(c);
+  // 640 and 576 threads only reach the deep-halo FP32 sweeps
+  const int nts[] = {640, 576, 512, 448, 384, 320, 256, 192};
   // reference time of the starting shape sets the budget
   float tf0 = 0, ta0 = 0;
   const int c0 = ctx->cl, n0 = ctx->nthreads;
   run(c0, n0, &tf0, &ta0);
   run(c0, n0, &tf0, &ta0);
-  const double budget_ms = std::max(2000.0, 40.0 * (tf0 + ta0));
+  const double budget_ms = std::max(2000.0, 60.0 * (tf0 + ta0));
   double spent = 0.0;
   struct Best { double t = 1e300; int c = 0, nt = 0; };
   Best best_f[2], best_a[2];
@@ -625,7 +661,7 @@ void autotune(dd4dv_ctx* ctx) {
         spent += tf + ta + tf2 + ta2;
         tf = std::min(tf, tf2);
         ta = std::min(ta, ta2);
-        if (smem_f((ctx->max_ny + c - 1) / c) <= (size_t)cap && tf < best_f[use].t) best_f[use] = {tf, c, ctx->nt_f};
+        if (tf < best_f[use].t) best_f[use] = {tf, c, ctx->nt_f};
         if (ta < best_a[use].t) best_a[use] = {ta, c, nt};
       }
   }
@@ -985,6 +1021,9 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   ctx->rho = dalloc<double>(ctx, (size_t)m * n_sub, &L);
   ctx->lbst = dalloc<LbState>(ctx, n_sub, &L);
   ctx->phase_d = dalloc<int>(ctx, n_sub, &L);
+  ctx->owned_d = dalloc<int>(ctx, n_sub, &L);
+  ctx->owned_h.assign(n_sub, 1);
+  ctx->owned_all = true;
   ctx->obs_d = dalloc<ObsRec>(ctx, recs.size(), &L);
   ctx->obs_force_d = dalloc<double>(ctx, recs.size(), &L);
   ctx->lvl_obs_d = dalloc<int>(ctx, lvl_obs.size(), &L);
@@ -1012,6 +1051,10 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   }
   h2d(ctx, ctx->subs_d, subs.data(), subs.size() * sizeof(SubDesc));
   h2d(ctx, ctx->order_d, order.data(), order.size() * sizeof(int));
+  {
+    const std::vector<int> ones(n_sub, 1);
+    h2d(ctx, ctx->owned_d, ones.data(), n_sub * sizeof(int));
+  }
   if (!recs.empty()) h2d(ctx, ctx->obs_d, recs.data(), recs.size() * sizeof(ObsRec));
   h2d(ctx, ctx->lvl_obs_d, lvl_obs.data(), lvl_obs.size() * sizeof(int));
   h2d(ctx, ctx->lvl_sc_d, lvl_sc.data(), lvl_sc.size() * sizeof(int));
@@ -1078,7 +1121,7 @@ dd4dv_ctx::~dd4dv_ctx() {
 }
 
 void dd4dv_ctx::drop_graphs() {
-  for (cudaGraphExec_t* g : {&og.start, &og.dir, &og.trial, &og.exch})
+  for (cudaGraphExec_t* g : {&og.start, &og.dir, &og.trial, &og.exch, &og.fin})
     if (*g) {
       cudaGraphExecDestroy(*g);
       *g = nullptr;
@@ -1323,7 +1366,7 @@ dd4dv_status dd4dv_eval(dd4dv_ctx* ctx, const double* w_all, double* J_all, doub
     double* gr = grad_all ? (device_ptrs ? grad_all : ctx->io_b) : nullptr;
     by_precision(ctx, [&](auto t) {
       using T = decltype(t);
-      eval_T<T>(ctx, w, J, gr, pa, nullptr, 0, nullptr);
+      eval_T<T>(ctx, w, J, gr, pa, own_mask(ctx), 1, nullptr);
       return 0;
     });
     ctx->fwd_pending = false;
@@ -1350,10 +1393,10 @@ dd4dv_status dd4dv_eval_forward(dd4dv_ctx* ctx, const double* w_all, double* J_a
     double* pa = device_ptrs ? parts : (parts ? ctx->io_p + ctx->n_sub : nullptr);
     by_precision(ctx, [&](auto t) {
       using T = decltype(t);
-      init_states<T>(ctx, ctx->io_c, ctx->vw, nullptr, 0);
-      forward_sweep<T>(ctx, nullptr, 0);
+      init_states<T>(ctx, ctx->io_c, ctx->vw, own_mask(ctx), 1);
+      forward_sweep<T>(ctx, own_mask(ctx), 1);
       KL(launch_finalize_J(ctx->subs_d, ctx->n_sub, ctx->io_c, ctx->part, ctx->cl_f, ctx->vconst,
-                           ctx->dec.lambda, ctx->dec.mu, J, pa, nullptr, 0, ctx->st));
+                           ctx->dec.lambda, ctx->dec.mu, J, pa, own_mask(ctx), 1, ctx->st));
       return 0;
     });
     ctx->fwd_pending = true;
@@ -1377,8 +1420,10 @@ dd4dv_status dd4dv_eval_backward(dd4dv_ctx* ctx, const double* scale, double* gr
     by_precision(ctx, [&](auto t) {
       using T = decltype(t);
       SweepArgs<T> a = sweep_args<T>(ctx);
+      a.active = own_mask(ctx);
+      a.active_value = 1;
       KL(launch_adjoint<T>(a, ctx->cl, ctx->nthreads, ctx->st));
-      apply_VT(ctx, ctx->lam_a, ctx->io_c, sc, gr, nullptr, 0);
+      apply_VT(ctx, ctx->lam_a, ctx->io_c, sc, gr, own_mask(ctx), 1);
       return 0;
     });
     ctx->fwd_pending = false;
@@ -1768,7 +1813,7 @@ static void gn_outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats*
 // direction); the device work of each step is one graph launch when
 // sv.use_graphs is set.
 template <typename T>
-static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* stats) {
+static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* stats, bool exchange = true) {
   if (sv.local_solver == 1) {
     gn_outer_step_T<T>(ctx, sv, stats);
     return;
@@ -1793,9 +1838,10 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
   la.c1 = sv.c1;
   la.counter = ctx->counter_d;
   la.phase = ctx->phase_d;
+  la.owned = ctx->owned_d;
 
-  auto q_start = [&] {   // evaluation at every local problem's start point
-    eval_T<T>(ctx, ctx->w, ctx->J, ctx->g, nullptr, nullptr, 0, nullptr);
+  auto q_start = [&] {   // evaluation at every owned local problem's start point
+    eval_T<T>(ctx, ctx->w, ctx->J, ctx->g, nullptr, ctx->owned_d, 1, nullptr);
     LbArgs l2 = la;
     l2.J_eval = ctx->J;
     KL(launch_lb_start(l2, ctx->st));
@@ -1816,6 +1862,9 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
     KL(launch_lb_linesearch(l2, ctx->st));
     d2h(ctx, ctx->counter_h, ctx->counter_d, 2 * sizeof(int));
   };
+  auto q_fin = [&] {     // local solve only: the L-BFGS states for the statistics
+    d2h(ctx, ctx->lbst_h, ctx->lbst, ctx->n_sub * sizeof(LbState));
+  };
   auto q_exch = [&] {    // Exchange at the new local solutions, outer increment
     exchange_T<T>(ctx, ctx->w);
     KL(launch_max_abs_diff(ctx->w, ctx->w_prev, ctx->ctrl_total, ctx->scal_d, ctx->st));
@@ -1833,6 +1882,7 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
     og.dir = capture_graph(ctx, q_dir, &og.k_dir);
     og.trial = capture_graph(ctx, q_trial, &og.k_trial);
     og.exch = capture_graph(ctx, q_exch, &og.k_exch);
+    og.fin = capture_graph(ctx, q_fin, &og.k_fin);
     og.key = sv;
     og.valid = true;
   }
@@ -1848,12 +1898,14 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
   long long evals = 0, sub_evals = 0, pts = 0;
   run(q_start, og.start, og.k_start);
   ++evals;
-  sub_evals += ctx->n_sub;
-  pts += ctx->pt_steps;
   std::vector<long long> sub_pts(ctx->n_sub);
   for (int s = 0; s < ctx->n_sub; ++s) {
     const SubDesc& d = ctx->subs_h[s];
     sub_pts[s] = (long long)d.nx * d.ny * (d.b - d.a);
+    if (ctx->owned_h[s]) {
+      ++sub_evals;
+      pts += sub_pts[s];
+    }
   }
   const int guard_iters = sv.max_local_iters + 2;
   for (int it = 0; it < guard_iters; ++it) {
@@ -1872,17 +1924,19 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
       if (ctx->counter_h[0] == 0) break;
     }
   }
-  run(q_exch, og.exch, og.k_exch);
+  if (exchange) run(q_exch, og.exch, og.k_exch);
+  else run(q_fin, og.fin, og.k_fin);
   sync(ctx);
   if (stats) {
-    stats->outer_iters += 1;
+    stats->outer_iters += exchange ? 1 : 0;
     stats->evals += evals;
     stats->sub_evals += sub_evals;
     stats->pt_steps += pts;
-    stats->dw_inf = ctx->scal_h[0];
+    if (exchange) stats->dw_inf = ctx->scal_h[0];
     double Js = 0.0, gmax = 0.0;
     int fails = 0;
     for (int s = 0; s < ctx->n_sub; ++s) {
+      if (!ctx->owned_h[s]) continue;
       const LbState& l = ctx->lbst_h[s];
       Js += l.J;
       if (l.g0n > 0.0) gmax = std::max(gmax, l.gn / l.g0n);
@@ -1896,10 +1950,46 @@ static void outer_step_T(dd4dv_ctx* ctx, const dd4dv_solver& sv, dd4dv_stats* st
 
 extern "C" {
 
+dd4dv_status dd4dv_set_owned(dd4dv_ctx* ctx, const int* owned) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    std::vector<int> m(ctx->n_sub, 1);
+    if (owned)
+      for (int s = 0; s < ctx->n_sub; ++s) {
+        if (owned[s] != 0 && owned[s] != 1) fail(ctx, DD4DV_EINVAL, "owned[%d] must be 0 or 1", s);
+        m[s] = owned[s];
+      }
+    h2d(ctx, ctx->owned_d, m.data(), ctx->n_sub * sizeof(int));
+    sync(ctx);
+    ctx->owned_h = m;
+    ctx->owned_all = std::all_of(m.begin(), m.end(), [](int v) { return v == 1; });
+    ctx->fwd_pending = false;
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_local_solve(dd4dv_ctx* ctx, const dd4dv_solver* solver, dd4dv_stats* stats) {
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    check_solver(ctx, solver);
+    if (solver->local_solver != 0) fail(ctx, DD4DV_EINVAL, "dd4dv_local_solve runs the L-BFGS local solver only");
+    by_precision(ctx, [&](auto t) {
+      using T = decltype(t);
+      outer_step_T<T>(ctx, *solver, stats, false);
+      return 0;
+    });
+    ctx->fwd_pending = false;
+    return DD4DV_OK;
+  });
+}
+
 dd4dv_status dd4dv_outer_step(dd4dv_ctx* ctx, const dd4dv_solver* solver, dd4dv_stats* stats) {
   return guard(ctx, [&] {
     require_dec(ctx);
     check_solver(ctx, solver);
+    if (!ctx->owned_all)
+      fail(ctx, DD4DV_ESTATE, "the context owns a subset of the subdomains: run dd4dv_local_solve, gather the "
+                              "controls, dd4dv_set_controls and dd4dv_exchange instead");
     by_precision(ctx, [&](auto t) {
       using T = decltype(t);
       outer_step_T<T>(ctx, *solver, stats);
@@ -1914,6 +2004,9 @@ dd4dv_status dd4dv_run(dd4dv_ctx* ctx, const dd4dv_solver* solver, double* xa0, 
   return guard(ctx, [&] {
     require_dec(ctx);
     check_solver(ctx, solver);
+    if (!ctx->owned_all)
+      fail(ctx, DD4DV_ESTATE, "the context owns a subset of the subdomains: drive the outer loop with "
+                              "dd4dv_local_solve and dd4dv_exchange");
     dd4dv_stats local{};
     dd4dv_stats* stp = stats ? stats : &local;
     std::memset(stp, 0, sizeof(*stp));
@@ -2055,20 +2148,44 @@ dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape) {
       if (c < 1 || c > 16 || c > ctx->min_ny)
         fail(ctx, DD4DV_EINVAL, "cluster sizes must be 1..16 and <= the smallest box height %d", ctx->min_ny);
     for (int t : {tf, ta})
-      if (t < 64 || t > 512 || t % 32) fail(ctx, DD4DV_EINVAL, "threads must be a multiple of 32 in 64..512");
-    const int tf_max = ctx->m.precision == 1 ? max_threads_forward<float>() : max_threads_forward<double>();
-    if (tf > tf_max) fail(ctx, DD4DV_EINVAL, "forward sweep threads must be <= %d at this precision", tf_max);
+      if (t < 64 || t > 640 || t % 32) fail(ctx, DD4DV_EINVAL, "threads must be a multiple of 32 in 64..640");
     if (sg && !ctx->stg) fail(ctx, DD4DV_EINVAL, "no stage buffer (ckpt_k != 0 or freed by the autotuner)");
     const int Rf = (ctx->max_ny + cf - 1) / cf, Ra = (ctx->max_ny + ca - 1) / ca;
-    const bool f32 = ctx->m.precision == 1;
-    if ((f32 ? smem_forward<float>(Rf, ctx->W) : smem_forward<double>(Rf, ctx->W)) > 232448 ||
-        (f32 ? smem_adjoint<float>(Ra, ctx->W) : smem_adjoint<double>(Ra, ctx->W)) > 232448)
-      fail(ctx, DD4DV_EINVAL, "shape needs too much shared memory");
+    const bool stg0 = ctx->use_stg;
+    ctx->use_stg = sg != 0;
+    const int kf = fwd_kind_at(ctx, cf, tf), ka = adj_kind_at(ctx, ca, ta);
+    ctx->use_stg = stg0;
+    if (!kf || !ka)
+      fail(ctx, DD4DV_EINVAL,
+           "%s sweep shape cannot run: too much shared memory, or more threads than the stripe sweep allows "
+           "(FP32 forward 384, else 512) where the deep-halo FP32 sweep does not apply (it needs stripes of "
+           ">= 3 rows, <= 4 own points per thread and <= 640 threads)",
+           !kf ? "forward" : "adjoint");
     ctx->cl_f = cf; ctx->nt_f = tf; ctx->R_f = Rf;
     ctx->cl = ca; ctx->nthreads = ta; ctx->R = Ra;
     ctx->use_stg = sg != 0;
     ctx->dec.cluster = ca;
     ctx->drop_graphs();
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int variant) {
+  return guard(ctx, [&] {
+    if (variant != 0 && variant != 1) fail(ctx, DD4DV_EINVAL, "variant must be 0 (automatic) or 1 (stripe sweeps)");
+    ctx->variant = variant;
+    ctx->drop_graphs();
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_sweep_kernels(const dd4dv_ctx* cctx, int* kinds) {
+  auto* ctx = const_cast<dd4dv_ctx*>(cctx);
+  return guard(ctx, [&] {
+    require_dec(ctx);
+    if (!kinds) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    kinds[0] = fwd_kind_at(ctx, ctx->cl_f, ctx->nt_f);
+    kinds[1] = adj_kind_at(ctx, ctx->cl, ctx->nthreads);
     return DD4DV_OK;
   });
 }

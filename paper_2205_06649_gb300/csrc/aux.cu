@@ -434,6 +434,10 @@ __global__ void lb_start_kernel(LbArgs a) {
     st.alpha = 1.0;
     st.phase = (st.g0n > 0.0) ? 0 : 2;
     st.status = (st.g0n > 0.0) ? 0 : 1;
+    if (a.owned && !a.owned[s]) {   // solved by another context: done from the start
+      st.phase = 2;
+      st.status = 4;
+    }
     a.st[s] = st;
     a.phase[s] = st.phase;
   }

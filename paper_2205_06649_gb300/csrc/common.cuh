@@ -102,6 +102,9 @@ struct SweepArgs {
   int* err;                   // device error word (0 = ok)
   int tgb_on;                 // set by the launcher: the FP32 sweep's shared memory holds a
                               // buffer of prefetched overlap targets (only if it still fits)
+  int min_ny;                 // smallest box height of the decomposition
+  int variant;                // 0: deep-halo FP32 sweeps where they apply, else the stripe
+                              // sweeps; 1: stripe sweeps only
 };
 
 // Largest CTA of the forward sweep: 384 threads on the FP32 path, whose
@@ -110,6 +113,12 @@ struct SweepArgs {
 template <typename T> constexpr int max_threads_forward() { return sizeof(T) == 4 ? 384 : 512; }
 
 // ---- launchers (sweep.cu) ----
+// Which kernel a sweep launch with cl CTAs per subdomain and nthreads threads
+// per CTA would run: 0 = none (shape not launchable), 1 = the stripe sweep
+// (one halo row per stage), 2 = the deep-halo FP32 sweep (three halo rows, one
+// exchange per step).
+template <typename T> int forward_kind(const SweepArgs<T>& a, int cl, int nthreads);
+template <typename T> int adjoint_kind(const SweepArgs<T>& a, int cl, int nthreads);
 template <typename T> cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);
 template <typename T> cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);
 template <typename T> cudaError_t launch_tlm(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);
@@ -209,6 +218,7 @@ struct LbArgs {
   double gtol, c1;
   int* counter;                        // [2]: # in line search, # needing a direction
   int* phase;                          // [n_sub] mirror of LbState::phase (sweep masks)
+  const int* owned;                    // [n_sub] 1 = this context solves the subdomain, or nullptr
 };
 cudaError_t launch_lb_start(const LbArgs& a, cudaStream_t st);
 cudaError_t launch_lb_direction(const LbArgs& a, cudaStream_t st);

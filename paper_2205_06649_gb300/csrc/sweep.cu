@@ -605,6 +605,33 @@ __device__ __forceinline__ void rhs_tl_pt(const Pt5<T>& z, const Pt5<T>& d, T A,
         BinvC * ((dhN * vN + hN * dvN) * cN - (dhS * vS + hS * dvS) * cS);
 }
 
+// The arithmetic of the transposed RK3 step at one point, shared by every
+// adjoint sweep so that all of them round alike.  A stage adjoint
+// mu_out = m + dt F'(z)^T m ...
+template <typename T, bool DEV>
+__device__ __forceinline__ void adj_stage_math(const Pt5<T>& z, const Pt5<T>& m, const T (&rc)[8], T dt, T Bth,
+                                               T gBth, T href, int wall, T& v0, T& v1, T& v2) {
+  T Gh, Gu, Gv;
+  rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], rc[7], Bth, gBth, href, wall, Gh, Gu, Gv);
+  v0 = xfma(dt, Gh, m.h);
+  v1 = xfma(dt, Gu, m.u);
+  v2 = xfma(dt, Gv, m.v);
+}
+// ... and lambda(n) = lambda'/3 + mu2/2 + (mu1 + dt F'(x)^T mu1)/6 from the
+// stencil m of mu1, z of x, and lambda' = (ph, pu, pv), mu2 = (qh, qu, qv) at
+// the point.
+template <typename T, bool DEV>
+__device__ __forceinline__ void adj_lambda_math(const Pt5<T>& z, const Pt5<T>& m, const T (&rc)[8], T dt, T Bth,
+                                                T gBth, T href, int wall, T ph, T pu, T pv, T qh, T qu, T qv,
+                                                T& v0, T& v1, T& v2) {
+  const T c13 = (T)(1.0 / 3.0), c16 = (T)(1.0 / 6.0);
+  T Gh, Gu, Gv;
+  rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], rc[7], Bth, gBth, href, wall, Gh, Gu, Gv);
+  v0 = xfma(c16, xfma(dt, Gh, m.h), xfma((T)0.5, qh, xmul(c13, ph)));
+  v1 = xfma(c16, xfma(dt, Gu, m.u), xfma((T)0.5, qu, xmul(c13, pu)));
+  v2 = xfma(c16, xfma(dt, Gv, m.v), xfma((T)0.5, qv, xmul(c13, pv)));
+}
+
 template <typename T>
 __device__ __forceinline__ void block_reduce2(double& x, double& y, double* scratch) {
   for (int o = 16; o > 0; o >>= 1) {
@@ -833,21 +860,15 @@ __device__ __forceinline__ bool setup_geo(const SweepArgs<T>& a, cg::cluster_gro
   return true;
 }
 
-// One RK3 stage at own point (rr, k): out = cx X + cy (Y + dt F(Y)); the
-// three new values are also returned.
+// The arithmetic of one RK3 stage at one point, out = cx X + cy (Y + dt F(Y)),
+// from the point's stencil y of Y, its row constants rc and its X values (read
+// only when cx != 0).  Every sweep (forward, stage recomputation, checkpoint
+// segments, tangent-linear, the deep-halo FP32 sweeps) calls this one
+// function, so all of them round every stage identically.
 template <typename T, bool DEV>
-__device__ __forceinline__ void stage_point(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs,
-                                            T* out, const T* X, const T* Y, T cx, T cy, int rr, int k,
-                                            T& o0, T& o1, T& o2) {
-  const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
-  const int P = g.P;
-  const int o = pidx(g, rr, k);
-  const int ri = rr + 1;
+__device__ __forceinline__ void stage_math(const Pt5<T>& y, const T (&rc)[8], T dt, T Bth, T gBth, T href, T cx,
+                                           T cy, T xh, T xu, T xv, T& o0, T& o1, T& o2) {
   T Fh, Fu, Fv;
-  T rc[8];
-  load_rec8(rs.fw + 8 * ri, rc);
-  Pt5<T> y;
-  load5(Y, o, P, Lay<T>::CS, g.RS, y);
   rhs_pt<T, DEV>(y, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], Bth, gBth, href, Fh, Fu, Fv);
   o0 = xfma(dt, Fh, y.h);
   o1 = xfma(dt, Fu, y.u);
@@ -858,12 +879,28 @@ __device__ __forceinline__ void stage_point(const SweepArgs<T>& a, const Geo<T>&
     o2 = xmul(cy, o2);
   }
   if (cx != (T)0) {
-    T xh, xu, xv;
-    ld3(X, o, P, xh, xu, xv);
     o0 = xfma(cx, xh, o0);
     o1 = xfma(cx, xu, o1);
     o2 = xfma(cx, xv, o2);
   }
+}
+
+// One RK3 stage at own point (rr, k): out = cx X + cy (Y + dt F(Y)); the
+// three new values are also returned.
+template <typename T, bool DEV>
+__device__ __forceinline__ void stage_point(const SweepArgs<T>& a, const Geo<T>& g, const RowSmem<T>& rs,
+                                            T* out, const T* X, const T* Y, T cx, T cy, int rr, int k,
+                                            T& o0, T& o1, T& o2) {
+  const int P = g.P;
+  const int o = pidx(g, rr, k);
+  const int ri = rr + 1;
+  T rc[8];
+  load_rec8(rs.fw + 8 * ri, rc);
+  Pt5<T> y;
+  load5(Y, o, P, Lay<T>::CS, g.RS, y);
+  T xh = (T)0, xu = (T)0, xv = (T)0;
+  if (cx != (T)0) ld3(X, o, P, xh, xu, xv);
+  stage_math<T, DEV>(y, rc, a.dt_s, a.Bth_s, a.gBth_s, a.href_s, cx, cy, xh, xu, xv, o0, o1, o2);
   st3(out, o, P, o0, o1, o2);
 }
 
@@ -1297,7 +1334,6 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   const bool pre_tg = g.tgb && a.mu != 0.0 && !a.gn_dx && !a.yforce;
   for (int i = threadIdx.x; i < g.BUF; i += blockDim.x) Lp[i] = (T)0;
   const T dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
-  const T c13 = (T)(1.0 / 3.0), c16 = (T)(1.0 / 6.0);
   const int wall_s = (g.flags & F_SWALL) ? 1 : 0;
   const int wall_n = (g.flags & F_NWALL) ? 2 : 0;
   const size_t lvl_sz = (size_t)3 * g.ny * g.d.nxp;
@@ -1372,17 +1408,12 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
         [&](int rr, int k, T& v0, T& v1, T& v2) {
       const int o = pidx(g, rr, k), ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
-      T Gh, Gu, Gv;
       T rc[8];
       load_rec8(rs.bw + 8 * ri, rc);
       Pt5<T> z, m;
       load5(X2, o, P, CS, g.RS, z);
       load5(Lp, o, P, CS, g.RS, m);
-      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], rc[7], Bth, gBth, href, wall, Gh, Gu,
-                         Gv);
-      v0 = xfma(dt, Gh, m.h);
-      v1 = xfma(dt, Gu, m.u);
-      v2 = xfma(dt, Gv, m.v);
+      adj_stage_math<T, DEV>(z, m, rc, dt, Bth, gBth, href, wall, v0, v1, v2);
       st3(L2, o, P, v0, v1, v2);
         },
         1);
@@ -1393,17 +1424,12 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
         [&](int rr, int k, T& v0, T& v1, T& v2) {
       const int o = pidx(g, rr, k), ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
-      T Gh, Gu, Gv;
       T rc[8];
       load_rec8(rs.bw + 8 * ri, rc);
       Pt5<T> z, m;
       load5(X1, o, P, CS, g.RS, z);
       load5(L2, o, P, CS, g.RS, m);
-      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], rc[7], Bth, gBth, href, wall, Gh, Gu,
-                         Gv);
-      v0 = xfma(dt, Gh, m.h);
-      v1 = xfma(dt, Gu, m.u);
-      v2 = xfma(dt, Gv, m.v);
+      adj_stage_math<T, DEV>(z, m, rc, dt, Bth, gBth, href, wall, v0, v1, v2);
       st3(L1, o, P, v0, v1, v2);
         },
         0);   // the prefetched targets land before the next phase reads them
@@ -1411,20 +1437,15 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
     const auto lam_n = [&](int rr, int k, T& v0, T& v1, T& v2) {
       const int o = pidx(g, rr, k), ri = rr + 1;
       const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
-      T Gh, Gu, Gv;
       T rc[8];
       load_rec8(rs.bw + 8 * ri, rc);
       Pt5<T> z, m;
       load5(X, o, P, CS, g.RS, z);
       load5(L1, o, P, CS, g.RS, m);
-      rhs_adj_pt<T, DEV>(z, m, rc[0], rc[1], rc[2], rc[3], rc[4], rc[5], rc[6], rc[7], Bth, gBth, href, wall, Gh, Gu,
-                         Gv);
       T ph, pu, pv, qh, qu, qv;
       ld3(Lp, o, P, ph, pu, pv);
       ld3(L2, o, P, qh, qu, qv);
-      v0 = xfma(c16, xfma(dt, Gh, m.h), xfma((T)0.5, qh, xmul(c13, ph)));
-      v1 = xfma(c16, xfma(dt, Gu, m.u), xfma((T)0.5, qu, xmul(c13, pu)));
-      v2 = xfma(c16, xfma(dt, Gv, m.v), xfma((T)0.5, qv, xmul(c13, pv)));
+      adj_lambda_math<T, DEV>(z, m, rc, dt, Bth, gBth, href, wall, ph, pu, pv, qh, qu, qv, v0, v1, v2);
     };
     // With no external forcing, no Gauss-Newton product and no observation
     // at this level, lambda(n) takes its overlap forcing point by point and
@@ -1603,6 +1624,793 @@ __global__ void __launch_bounds__(512) tlm_kernel(SweepArgs<T> a) {
   cl.sync();
 }
 
+// ===========================================================================
+// Deep-halo FP32 sweeps: the throughput form of the FP32-state path.
+//
+// The stripe sweeps above exchange one halo row per RK3 stage, so a forward
+// step has three cluster-barrier phases and an adjoint step three or four,
+// each with a few points per thread.  Every such phase costs a roughly fixed
+// latency (cluster barrier, memory fence, phase passes) whatever its work,
+// and the FP32 sweeps, whose arithmetic is cheap, spend most of their time
+// there.  The deep-halo sweeps keep kH = 3 halo rows on each side that has a
+// neighbour CTA.  The first two stages of a step also compute the rows next to
+// each neighbour's edge (four and two extra rows: the stencil of stage s + 1
+// needs stage s one row further out), so a stripe needs its neighbours' values
+// only once per step:
+//   * after the last stage, a CTA stores its three edge rows of the new state
+//     into its neighbours' exchange buffers HX (distributed shared memory) and
+//     arrives at the cluster barrier (release); at the start of the next step
+//     it waits (acquire) and copies its own HX into its halo rows;
+//   * a second barrier phase, which a CTA arrives at once it has copied HX out
+//     and waits on only before it stores into its neighbours' HX three stages
+//     later, keeps a store from overwriting a buffer not yet copied out.
+// The stage-state, trajectory and overlap work runs inside the stages from
+// registers, with no separate passes.  Each point uses the same arithmetic
+// (stage_math, adj_stage_math, adj_lambda_math) as the stripe sweeps, so both
+// give the same values bit for bit.  Every stripe needs at least kH rows.
+// Buffers: [R + 2 kH rows][W][4] FP32 slots (h, u, v, 0), rows -kH .. R + kH - 1.
+
+constexpr int kH = 3;            // halo rows per side
+constexpr int kMaxP = 4;         // own points per thread (register state of the last stage)
+constexpr int kDeepThreads = 640;
+
+struct G2 {
+  int s, rank, CL, R0, Rn, nx, ny, L, a, W, flags, RS, R;
+  bool hasS, hasN;                // neighbour CTA to the south / north
+  SubDesc d;
+  unsigned mnx;
+  float* gh;                      // ghost cache: 3 slots of [6 (R + 4) column | 6 W row] values
+  int* gh_tag;
+  int gh_len;
+};
+
+__device__ __forceinline__ int p2(const G2& g, int rr, int k) { return ((rr + kH) * g.W + k + 1) * 4; }
+// rows computed by stage st = 1, 2, 3 (kH - st rows beyond a neighbour edge)
+__device__ __forceinline__ int lo_st(const G2& g, int st) { return g.hasS ? st - kH : 0; }
+__device__ __forceinline__ int hi_st(const G2& g, int st) { return g.hasN ? g.Rn - 1 + kH - st : g.Rn - 1; }
+
+__device__ __forceinline__ bool setup_g2(const SweepArgs<float>& a, cg::cluster_group& cl, G2& g) {
+  g.rank = cl.block_rank();
+  g.CL = cl.num_blocks();
+  const int cid = blockIdx.x / g.CL;
+  if (cid >= a.n_sub) return false;
+  g.s = a.order[cid];
+  if (a.active && a.active[g.s] != a.active_value) return false;
+  g.d = a.subs[g.s];
+  g.nx = g.d.nx;
+  g.ny = g.d.ny;
+  g.a = g.d.a;
+  g.L = g.d.b - g.d.a;
+  g.flags = g.d.flags;
+  if (g.ny < kH * g.CL || g.nx + 2 > a.W || (g.ny + g.CL - 1) / g.CL > a.R ||
+      (g.ny + g.CL - 1) / g.CL * g.nx > kMaxP * (int)blockDim.x) {   // uniform over the cluster
+    if (threadIdx.x == 0 && g.rank == 0) atomicExch(a.err, 2);
+    return false;
+  }
+  split_rows(g.ny, g.CL, g.rank, g.R0, g.Rn);
+  g.R = a.R;
+  g.W = a.W;
+  g.RS = g.W * 4;
+  g.hasS = g.rank > 0;
+  g.hasN = g.rank < g.CL - 1;
+  if (g.rank != 0) g.flags &= ~F_SWALL;
+  if (g.rank != g.CL - 1) g.flags &= ~F_NWALL;
+  g.mnx = magic_of(g.nx);
+  return true;
+}
+
+// nbuf state buffers, the exchange buffer (2 kH rows of [W][4]), row constants
+// of rows -kH .. R + kH - 1 (forward and adjoint records), reduction scratch,
+// ghost cache.
+__host__ __device__ constexpr size_t deep_buf_floats(int R, int W) { return (size_t)(R + 2 * kH) * W * 4; }
+size_t smem_deep(int nbuf, int R, int W) {
+  size_t b = (nbuf * deep_buf_floats(R, W) + (size_t)2 * kH * W * 4 + 16 * (size_t)(R + 2 * kH)) * sizeof(float);
+  b = (b + 15) / 16 * 16 + 64 * sizeof(double);
+  return b + 3 * (size_t)(6 * (R + 4) + 6 * W) * sizeof(float) + 3 * sizeof(int) + 16;
+}
+
+__device__ void carve2(G2& g, int nbuf, float** bufs, float** hx, float** fw, float** bw, double** scratch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* p = reinterpret_cast<float*>(smem_raw);
+  for (int b = 0; b < nbuf; ++b) {
+    bufs[b] = p;
+    p += deep_buf_floats(g.R, g.W);
+  }
+  *hx = p;
+  p += 2 * kH * g.W * 4;
+  *fw = p;
+  p += 8 * (g.R + 2 * kH);
+  *bw = p;
+  p += 8 * (g.R + 2 * kH);
+  uintptr_t q = reinterpret_cast<uintptr_t>(p);
+  q = (q + 15) & ~uintptr_t(15);
+  *scratch = reinterpret_cast<double*>(q);
+  q += 64 * sizeof(double);
+  g.gh_len = 6 * (g.R + 4) + 6 * g.W;
+  g.gh = reinterpret_cast<float*>(q);
+  g.gh_tag = reinterpret_cast<int*>(q + 3 * (size_t)g.gh_len * sizeof(float));
+  if (threadIdx.x < 3) g.gh_tag[threadIdx.x] = -1;
+}
+
+// Row constants (as load_rows) of rows -kH .. Rn + kH - 1.
+__device__ void load_rows2(const SweepArgs<float>& a, const G2& g, float* fw, float* bw) {
+  for (int i = threadIdx.x; i < g.Rn + 2 * kH; i += blockDim.x) {
+    const int j = g.d.j0 + g.R0 + i - kH;
+    const int jc = min(max(j, 0), a.nlat - 1);
+    const int jn = min(max(j + 1, 0), a.nlat - 1);
+    const int js = min(max(j - 1, 0), a.nlat - 1);
+    const RowConst rc = a.rows[jc];
+    const double cn = a.rows[jn].c, cs = a.rows[js].c;
+    float* f = fw + 8 * i;
+    f[0] = (float)rc.A;
+    f[1] = (float)rc.f;
+    f[2] = (float)rc.tau;
+    f[3] = (float)rc.BinvC;
+    f[4] = (float)rc.gA;
+    f[5] = (float)cn;
+    f[6] = (float)cs;
+    f[7] = 0.0f;
+    float* b = bw + 8 * i;
+    b[0] = (float)rc.A;
+    b[1] = (float)rc.f;
+    b[2] = (float)rc.tau;
+    b[3] = (float)rc.gA;
+    b[4] = (float)(a.Bth * rc.c);
+    b[5] = (float)(1.0 / cn);
+    b[6] = (float)(1.0 / cs);
+    b[7] = (float)(2.0 * rc.tau);
+  }
+}
+
+// Ghost values of boundary level n into slot n % 3 (cp.async, joins the
+// caller's next commit group): west / east columns (box not periodic) of the
+// rows the first stage computes, and the south / north rows of a stripe at a
+// frozen box edge.
+__device__ void ghost_prefetch2(const SweepArgs<float>& a, const G2& g, int n) {
+  if (n < 0 || n > a.nsteps) return;
+  const int slot = n % 3;
+  float* dst = g.gh + (size_t)slot * g.gh_len;
+  const size_t plane = (size_t)a.nlat * a.nlon;
+  const float* src = a.bnd + (size_t)n * 3 * plane;
+  const int RC = g.R + 4;
+  if (!(g.flags & F_PERIODIC)) {
+    const int r0 = lo_st(g, 1), nr = hi_st(g, 1) - r0 + 1;
+    const int iw = (g.d.i0 - 1 + a.nlon) % a.nlon, ie = (g.d.i0 + g.nx) % a.nlon;
+    for (int idx = threadIdx.x; idx < 6 * nr; idx += blockDim.x) {
+      const int q = idx / nr;   // side * 3 + v
+      const int side = q / 3;
+      const int v = q - 3 * side, rr = r0 + idx - q * nr;
+      const int j = g.d.j0 + g.R0 + rr;
+      cp_async_4or8(dst + q * RC + rr + 2, src + ((size_t)v * a.nlat + j) * a.nlon + (side ? ie : iw), 4);
+    }
+  }
+  const bool south = g.rank == 0 && !(g.flags & F_SWALL);
+  const bool north = g.rank == g.CL - 1 && !(g.flags & F_NWALL);
+  if (south || north) {
+    for (int idx = threadIdx.x; idx < 6 * g.nx; idx += blockDim.x) {
+      const int q = mdiv(idx, g.mnx);
+      const int side = q / 3;
+      if ((side == 0 && !south) || (side == 1 && !north)) continue;
+      const int v = q - 3 * side, k = idx - q * g.nx;
+      const int j = side ? g.d.j0 + g.ny : g.d.j0 - 1;
+      cp_async_4or8(dst + 6 * RC + q * g.W + k, src + ((size_t)v * a.nlat + j) * a.nlon + (g.d.i0 + k) % a.nlon,
+                    4);
+    }
+  }
+  if (threadIdx.x == 0) g.gh_tag[slot] = n;
+}
+
+// The boundary trajectory blended between levels nA and nB, from the ghost
+// cache when both levels are there (else from HBM; same values).
+struct GS2 {
+  const float* ca;
+  const float* cb;
+  int nA, nB;
+  float wA, wB;
+};
+__device__ __forceinline__ GS2 ghost_src2(const G2& g, int nA, int nB, float wA, float wB) {
+  GS2 s{nullptr, nullptr, nA, nB, wA, wB};
+  if (nA >= 0 && nB >= 0 && g.gh_tag[nA % 3] == nA && (wB == 0.0f || g.gh_tag[nB % 3] == nB)) {
+    s.ca = g.gh + (size_t)(nA % 3) * g.gh_len;
+    s.cb = (wB == 0.0f) ? nullptr : g.gh + (size_t)(nB % 3) * g.gh_len;
+  }
+  return s;
+}
+__device__ __forceinline__ float bnd_blend2(const SweepArgs<float>& a, const GS2& s, int v, int j, int i) {
+  const size_t plane = (size_t)a.nlat * a.nlon;
+  const size_t o = ((size_t)v * a.nlat + j) * a.nlon + i;
+  const float xa = a.bnd[(size_t)s.nA * 3 * plane + o];
+  if (s.wB == 0.0f) return xa;
+  return xfma(s.wA, xa, xmul(s.wB, a.bnd[(size_t)s.nB * 3 * plane + o]));
+}
+__device__ __forceinline__ float gh_col2(const SweepArgs<float>& a, const G2& g, const GS2& s, int side, int v,
+                                         int rr) {
+  if (s.ca) {
+    const int o = (side * 3 + v) * (g.R + 4) + rr + 2;
+    const float xa = s.ca[o];
+    return s.cb ? xfma(s.wA, xa, xmul(s.wB, s.cb[o])) : xa;
+  }
+  const int i = side == 0 ? (g.d.i0 - 1 + a.nlon) % a.nlon : (g.d.i0 + g.nx) % a.nlon;
+  return bnd_blend2(a, s, v, g.d.j0 + g.R0 + rr, i);
+}
+__device__ __forceinline__ float gh_row2(const SweepArgs<float>& a, const G2& g, const GS2& s, int side, int v,
+                                         int k) {
+  if (s.ca) {
+    const int o = 6 * (g.R + 4) + (side * 3 + v) * g.W + k;
+    const float xa = s.ca[o];
+    return s.cb ? xfma(s.wA, xa, xmul(s.wB, s.cb[o])) : xa;
+  }
+  return bnd_blend2(a, s, v, side ? g.d.j0 + g.ny : g.d.j0 - 1, (g.d.i0 + k) % a.nlon);
+}
+
+// Ghost cells of buffer Z that do not depend on its values, for stencil
+// centres on rows [lo, hi]: at a frozen box edge the boundary trajectory
+// (state buffers) or zero (adjoint buffers, which are also zero at walls);
+// ghost columns when the box is not periodic.  Highest-numbered threads first.
+__device__ void fill_fixed2(const SweepArgs<float>& a, const G2& g, float* Z, int lo, int hi, const GS2& gs,
+                            bool adj) {
+  const bool cols = !(g.flags & F_PERIODIC);
+  const bool srow = g.rank == 0 && (adj || !(g.flags & F_SWALL));
+  const bool nrow = g.rank == g.CL - 1 && (adj || !(g.flags & F_NWALL));
+  const int nr = hi - lo + 1;
+  const int n = 2 * g.nx + (cols ? 2 * nr : 0);
+  for (int idx = blockDim.x - 1 - threadIdx.x; idx < n; idx += blockDim.x) {
+    float h = 0.0f, u = 0.0f, v = 0.0f;
+    if (idx < 2 * g.nx) {
+      const int side = idx >= g.nx ? 1 : 0;
+      if (side ? !nrow : !srow) continue;
+      const int k = idx - side * g.nx;
+      if (!adj) {
+        h = gh_row2(a, g, gs, side, 0, k);
+        u = gh_row2(a, g, gs, side, 1, k);
+        v = gh_row2(a, g, gs, side, 2, k);
+      }
+      st3(Z, p2(g, side ? g.Rn : -1, k), 1, h, u, v);
+    } else {
+      const int j = idx - 2 * g.nx;
+      const int side = j >= nr ? 1 : 0;
+      const int rr = lo + j - side * nr;
+      if (!adj) {
+        h = gh_col2(a, g, gs, side, 0, rr);
+        u = gh_col2(a, g, gs, side, 1, rr);
+        v = gh_col2(a, g, gs, side, 2, rr);
+      }
+      st3(Z, p2(g, rr, side ? g.nx : -1), 1, h, u, v);
+    }
+  }
+}
+
+// Halo data a computed point (rr, k) of Z publishes in its own buffer: the
+// periodic ghost columns and, for state buffers, the wall mirror row.
+__device__ __forceinline__ void publish2(const G2& g, float* Z, bool state, int rr, int k, float v0, float v1,
+                                         float v2) {
+  if (g.flags & F_PERIODIC) {
+    if (k == 0) st3(Z, p2(g, rr, g.nx), 1, v0, v1, v2);
+    if (k == g.nx - 1) st3(Z, p2(g, rr, -1), 1, v0, v1, v2);
+  }
+  if (state) {
+    if (rr == 0 && (g.flags & F_SWALL)) st3(Z, p2(g, -1, k), 1, v0, v1, -v2);
+    if (rr == g.Rn - 1 && (g.flags & F_NWALL)) st3(Z, p2(g, g.Rn, k), 1, v0, v1, -v2);
+  }
+}
+
+// Stores point (rr, k) of a buffer's new edge rows into the neighbours'
+// exchange buffers (their halo rows -kH .. -1 and Rn .. Rn + kH - 1).
+__device__ __forceinline__ void push2(const G2& g, float* hxS, float* hxN, int rr, int k, float v0, float v1,
+                                      float v2) {
+  if (hxS && rr < kH) *reinterpret_cast<float4*>(hxS + ((kH + rr) * g.W + k) * 4) = make_float4(v0, v1, v2, 0.0f);
+  if (hxN && rr >= g.Rn - kH)
+    *reinterpret_cast<float4*>(hxN + ((rr - (g.Rn - kH)) * g.W + k) * 4) = make_float4(v0, v1, v2, 0.0f);
+}
+
+// Halo rows of Z from this CTA's exchange buffer (with their periodic ghost
+// columns).
+__device__ void copy_hx2(const G2& g, const float* HX, float* Z) {
+  const int nrow = (g.hasS ? kH : 0) + (g.hasN ? kH : 0);
+  for (int idx = threadIdx.x; idx < nrow * g.nx; idx += blockDim.x) {
+    const int q = mdiv(idx, g.mnx);
+    const int k = idx - q * g.nx;
+    const int hr = g.hasS ? q : q + kH;
+    const int rr = hr < kH ? hr - kH : g.Rn + hr - kH;
+    const float4 v = *reinterpret_cast<const float4*>(HX + (hr * g.W + k) * 4);
+    *reinterpret_cast<float4*>(Z + p2(g, rr, k)) = v;
+    if (g.flags & F_PERIODIC) {
+      if (k == 0) *reinterpret_cast<float4*>(Z + p2(g, rr, g.nx)) = v;
+      if (k == g.nx - 1) *reinterpret_cast<float4*>(Z + p2(g, rr, -1)) = v;
+    }
+  }
+}
+
+// Rows [lo, hi] of a stored [3][ny][nxp] block into Z with cp.async (the
+// caller commits and waits), their periodic ghost columns too, and at a wall
+// the mirror row (read directly).
+__device__ void load_rows_async2(const G2& g, float* Z, const float* src, int lo, int hi) {
+  const size_t pl = (size_t)g.ny * g.d.nxp;
+  const int n = (hi - lo + 1) * g.nx;
+  const bool per = g.flags & F_PERIODIC;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int q = mdiv(idx, g.mnx);
+    const int rr = lo + q, k = idx - q * g.nx;
+    const float* s = src + (size_t)(g.R0 + rr) * g.d.nxp + k;
+    float* d = Z + p2(g, rr, k);
+    cp_async_4or8(d, s, 4);
+    cp_async_4or8(d + 1, s + pl, 4);
+    cp_async_4or8(d + 2, s + 2 * pl, 4);
+    if (per && (k == 0 || k == g.nx - 1)) {
+      float* e = Z + p2(g, rr, k == 0 ? g.nx : -1);
+      cp_async_4or8(e, s, 4);
+      cp_async_4or8(e + 1, s + pl, 4);
+      cp_async_4or8(e + 2, s + 2 * pl, 4);
+    }
+    if ((rr == 0 && (g.flags & F_SWALL)) || (rr == g.Rn - 1 && (g.flags & F_NWALL)))
+      st3(Z, p2(g, rr == 0 ? -1 : g.Rn, k), 1, s[0], s[pl], -s[2 * pl]);
+  }
+}
+
+// Rows a stored state must cover for stencil centres [lo, hi]: one row more
+// on each side that has a neighbour (the box edge rows come from the rules).
+__device__ __forceinline__ int load_lo2(const G2& g, int lo) { return g.hasS ? lo - 1 : 0; }
+__device__ __forceinline__ int load_hi2(const G2& g, int hi) { return g.hasN ? hi + 1 : g.Rn - 1; }
+
+__device__ __forceinline__ int overlap_count2(const G2& g, int l, int r, int k) {
+  const SubDesc& d = g.d;
+  const int cx = 1 + (k < d.wL) + (k >= d.nx - d.wR);
+  const int cy = 1 + (r < d.wS) + (r >= d.ny - d.wN);
+  const int ct = 1 + (l < d.tA) + (l > g.L - d.tB);
+  return cx * cy * ct - 1;
+}
+__device__ __forceinline__ bool level_overlaps2(const G2& g, int l) {
+  const SubDesc& d = g.d;
+  return (l < d.tA) || (l > g.L - d.tB) || d.wL || d.wR || d.wS || d.wN;
+}
+
+// Overlap counts and targets of level l at this thread's own points (points
+// t + i T of the own rows, i < kMaxP), loaded ahead of their use.
+__device__ __forceinline__ void prefetch_own_targets2(const SweepArgs<float>& a, const G2& g, int l, int (&cv)[kMaxP],
+                                                      float (&tv)[kMaxP][3]) {
+  const bool any = a.mu != 0.0 && level_overlaps2(g, l);
+  const size_t pl = (size_t)g.ny * g.d.nxp;
+  const float* tg = a.tgt + g.d.traj_off + (size_t)l * 3 * pl;
+#pragma unroll
+  for (int i = 0; i < kMaxP; ++i) {
+    cv[i] = 0;
+    tv[i][0] = tv[i][1] = tv[i][2] = 0.0f;
+    const int idx = threadIdx.x + i * blockDim.x;
+    if (any && idx < g.Rn * g.nx) {
+      const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+      const int c = overlap_count2(g, l, g.R0 + rr, k);
+      cv[i] = c;
+      if (c) {
+        const float* t = tg + (size_t)(g.R0 + rr) * g.d.nxp + k;
+        tv[i][0] = t[0];
+        tv[i][1] = t[pl];
+        tv[i][2] = t[2 * pl];
+      }
+    }
+  }
+}
+
+// Observation misfit of level l (as obs_level): J_o += 1/2 w d^2, obs_force.
+__device__ void obs_level2(const SweepArgs<float>& a, const G2& g, const float* X, int l, double& Jo) {
+  const int o0 = a.lvl_obs[g.d.obs_lvl + l], o1 = a.lvl_obs[g.d.obs_lvl + l + 1];
+  for (int o = o0 + threadIdx.x; o < o1; o += blockDim.x) {
+    const ObsRec ob = a.obs[o];
+    const int rr = ob.r0 - g.R0;
+    if (rr < 0 || rr >= g.Rn) continue;
+    double acc = 0.0;
+    const double wj0 = 1.0 - ob.dj, wi0 = 1.0 - ob.di;
+    acc += (wj0 * wi0) * (double)X[p2(g, rr, ob.k0) + ob.var];
+    if (ob.di != 0.0) acc += (wj0 * ob.di) * (double)X[p2(g, rr, ob.k1) + ob.var];
+    if (ob.dj != 0.0) {
+      acc += (ob.dj * wi0) * (double)X[p2(g, rr + 1, ob.k0) + ob.var];
+      if (ob.di != 0.0) acc += (ob.dj * ob.di) * (double)X[p2(g, rr + 1, ob.k1) + ob.var];
+    }
+    const double d = acc - ob.y;
+    Jo += 0.5 * ob.w * d * d;
+    a.obs_force[o] = a.lam * ob.w * d;
+  }
+}
+
+// One forward stage st on rows [lo_st, hi_st]: out = cx X + cy (Y + dt F(Y));
+// own rows also go to the stage buffer hbm (when given).
+template <int ST>
+__device__ __forceinline__ void stage_rows2(const SweepArgs<float>& a, const G2& g, const float* fw, float* out,
+                                            const float* X, const float* Y, float cx, float cy, float* hbm) {
+  const int lo = lo_st(g, ST), hi = hi_st(g, ST);
+  const int n = (hi - lo + 1) * g.nx;
+  const size_t pl = (size_t)g.ny * g.d.nxp;
+  for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+    const int q = mdiv(idx, g.mnx);
+    const int rr = lo + q, k = idx - q * g.nx;
+    const int o = p2(g, rr, k);
+    float rc[8];
+    load_rec8(fw + 8 * (rr + kH), rc);
+    Pt5<float> y;
+    load5(Y, o, 1, 4, g.RS, y);
+    float xh = 0.0f, xu = 0.0f, xv = 0.0f;
+    if (cx != 0.0f) ld3(X, o, 1, xh, xu, xv);
+    float o0, o1, o2;
+    stage_math<float, true>(y, rc, a.dt_s, a.Bth_s, a.gBth_s, a.href_s, cx, cy, xh, xu, xv, o0, o1, o2);
+    st3(out, o, 1, o0, o1, o2);
+    publish2(g, out, true, rr, k, o0, o1, o2);
+    if (hbm && rr >= 0 && rr < g.Rn) {
+      float* d = hbm + (size_t)(g.R0 + rr) * g.d.nxp + k;
+      d[0] = o0;
+      d[pl] = o1;
+      d[2 * pl] = o2;
+    }
+  }
+}
+
+__device__ __forceinline__ float* stage_ptr2(const SweepArgs<float>& a, const SubDesc& d, int l, int which) {
+  return a.stg + d.stg_off + ((size_t)l * 2 + which) * 3 * d.ny * d.nxp;
+}
+// All but the two (one) most recently committed cp.async groups complete.
+__device__ __forceinline__ void cp_async_wait_prev2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one2() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+}
+
+// Forward sweep, deep-halo form (same results as fwd_kernel<float>).
+__global__ void __launch_bounds__(kDeepThreads, 1) fwd_deep_kernel(SweepArgs<float> a) {
+  cg::cluster_group cl = cg::this_cluster();
+  G2 g;
+  if (!setup_g2(a, cl, g)) return;
+  float* buf[3];
+  float *HX, *fw, *bw;
+  double* scratch;
+  carve2(g, 3, buf, &HX, &fw, &bw, &scratch);
+  float* X = buf[0];
+  float* S1 = buf[1];
+  float* S2 = buf[2];
+  float* hxS = g.hasS ? cl.map_shared_rank(HX, g.rank - 1) : nullptr;
+  float* hxN = g.hasN ? cl.map_shared_rank(HX, g.rank + 1) : nullptr;
+  load_rows2(a, g, fw, bw);
+  __syncthreads();   // ghost tags initialised
+  ghost_prefetch2(a, g, g.a);
+  if (g.L > 0) ghost_prefetch2(a, g, g.a + 1);
+  const size_t pl = (size_t)g.ny * g.d.nxp;
+  const size_t lvl = 3 * pl;
+  // x(a) (written by the initial-state kernel): own rows and the halo rows of stage 1
+  load_rows_async2(g, X, a.traj + g.d.traj_off, load_lo2(g, lo_st(g, 1)), load_hi2(g, hi_st(g, 1)));
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  fill_fixed2(a, g, X, lo_st(g, 1), hi_st(g, 1), ghost_src2(g, g.a, g.a, 1.0f, 0.0f), false);
+  __syncthreads();
+  double Jo = 0.0, Jm = 0.0;
+  obs_level2(a, g, X, 0, Jo);
+  {
+    int cv[kMaxP];
+    float tv[kMaxP][3];
+    prefetch_own_targets2(a, g, 0, cv, tv);
+    const float i0 = a.isb2_s[0], i1 = a.isb2_s[1], i2 = a.isb2_s[2];
+    float part = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kMaxP; ++i) {
+      const int idx = threadIdx.x + i * blockDim.x;
+      if (cv[i]) {
+        const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+        float x0, x1, x2;
+        ld3(X, p2(g, rr, k), 1, x0, x1, x2);
+        const float e0 = x0 - tv[i][0], e1 = x1 - tv[i][1], e2 = x2 - tv[i][2];
+        part += (float)cv[i] * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
+      }
+    }
+    Jm += (double)part;
+  }
+  const float c13 = (float)(1.0 / 3.0), c23 = (float)(2.0 / 3.0);
+  for (int l = 0; l < g.L; ++l) {
+    const int n = g.a + l;
+    if (l > 0) {
+      cluster_wait_acquire();   // neighbours' edge rows of x(n) are in HX
+      copy_hx2(g, HX, X);
+      cp_async_wait_all();      // ghost levels n, n + 1
+      __syncthreads();
+      fill_fixed2(a, g, X, lo_st(g, 1), hi_st(g, 1), ghost_src2(g, n, n, 1.0f, 0.0f), false);
+      __syncthreads();
+      obs_level2(a, g, X, l, Jo);
+    }
+    cluster_arrive_relaxed();   // this CTA has copied its exchange buffer out
+    if (n + 2 <= g.d.b) ghost_prefetch2(a, g, n + 2);
+    cp_async_commit();
+    int cv[kMaxP];
+    float tv[kMaxP][3];
+    prefetch_own_targets2(a, g, l + 1, cv, tv);
+    // stage 1: x1 = x + dt F(x)
+    fill_fixed2(a, g, S1, lo_st(g, 2), hi_st(g, 2), ghost_src2(g, n + 1, n + 1, 1.0f, 0.0f), false);
+    stage_rows2<1>(a, g, fw, S1, X, X, 0.0f, 1.0f, a.stg ? stage_ptr2(a, g.d, l, 0) : nullptr);
+    __syncthreads();
+    // stage 2: x2 = 3/4 x + 1/4 (x1 + dt F(x1))
+    fill_fixed2(a, g, S2, 0, g.Rn - 1, ghost_src2(g, n, n + 1, 0.5f, 0.5f), false);
+    stage_rows2<2>(a, g, fw, S2, X, S1, 0.75f, 0.25f, a.stg ? stage_ptr2(a, g.d, l, 1) : nullptr);
+    __syncthreads();
+    cluster_wait_acquire();   // neighbours have copied their exchange buffers out
+    // stage 3: x(n+1) = 1/3 x + 2/3 (x2 + dt F(x2)) on own rows, in place;
+    // edge rows into the neighbours' exchange buffers; overlap term of level l + 1
+    const float i0 = a.isb2_s[0], i1 = a.isb2_s[1], i2 = a.isb2_s[2];
+    float part = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kMaxP; ++i) {
+      const int idx = threadIdx.x + i * blockDim.x;
+      if (idx < g.Rn * g.nx) {
+        const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+        const int o = p2(g, rr, k);
+        float rc[8];
+        load_rec8(fw + 8 * (rr + kH), rc);
+        Pt5<float> y;
+        load5(S2, o, 1, 4, g.RS, y);
+        float xh, xu, xv;
+        ld3(X, o, 1, xh, xu, xv);
+        float o0, o1, o2;
+        stage_math<float, true>(y, rc, a.dt_s, a.Bth_s, a.gBth_s, a.href_s, c13, c23, xh, xu, xv, o0, o1, o2);
+        st3(X, o, 1, o0, o1, o2);
+        publish2(g, X, true, rr, k, o0, o1, o2);
+        push2(g, hxS, hxN, rr, k, o0, o1, o2);
+        if (cv[i]) {
+          const float e0 = o0 - tv[i][0], e1 = o1 - tv[i][1], e2 = o2 - tv[i][2];
+          part += (float)cv[i] * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
+        }
+      }
+    }
+    Jm += (double)part;
+    cluster_arrive_release();   // x(n+1) edge rows are in the neighbours' exchange buffers
+    if (a.ckpt == 0 || (l + 1) % a.ckpt == 0) {
+      float* dst = a.traj + g.d.traj_off + (size_t)(l + 1) * lvl;
+#pragma unroll
+      for (int i = 0; i < kMaxP; ++i) {
+        const int idx = threadIdx.x + i * blockDim.x;
+        if (idx < g.Rn * g.nx) {
+          const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+          float h, u, v;
+          ld3(X, p2(g, rr, k), 1, h, u, v);   // written by this thread
+          float* d = dst + (size_t)(g.R0 + rr) * g.d.nxp + k;
+          d[0] = h;
+          d[pl] = u;
+          d[2 * pl] = v;
+        }
+      }
+    }
+  }
+  if (g.L > 0) {
+    cluster_wait_acquire();
+    copy_hx2(g, HX, X);
+    __syncthreads();
+    obs_level2(a, g, X, g.L, Jo);
+  }
+  Jm *= 0.5;
+  block_reduce2<float>(Jo, Jm, scratch);
+  if (threadIdx.x == 0) {
+    a.part[((size_t)g.s * a.cl_max + g.rank) * 2 + 0] = Jo;
+    a.part[((size_t)g.s * a.cl_max + g.rank) * 2 + 1] = Jm;
+  }
+}
+
+// Adjoint forcing on own rows at level l that follows the overlap term: the
+// observation scatter (H^T of lambda w d, fixed order per target), as in
+// add_forcing.
+__device__ void scatter2(const SweepArgs<float>& a, const G2& g, float* Lb, int l) {
+  const int t0 = a.lvl_sc[g.d.sc_lvl + l], t1 = a.lvl_sc[g.d.sc_lvl + l + 1];
+  const unsigned mny = magic_of(g.ny);
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+    const int tg = a.sc_tgt[t];
+    const int q = mdiv(tg, g.mnx);   // v * ny + r
+    const int v = mdiv(q, mny);
+    const int r = q - v * g.ny, k = tg - q * g.nx;
+    const int rr = r - g.R0;
+    if (rr < 0 || rr >= g.Rn) continue;
+    double acc = 0.0;
+    for (int c = a.sc_off[t]; c < a.sc_off[t + 1]; ++c) acc += a.sc_w[c] * a.obs_force[a.sc_obs[c]];
+    Lb[p2(g, rr, k) + v] += (float)acc;
+  }
+}
+
+// Overlap forcing mu c (x - m) / sb^2 added to (l0, l1, l2), the arithmetic of
+// overlap_force with the targets given.
+__device__ __forceinline__ void overlap_force2(const SweepArgs<float>& a, float x0, float x1, float x2,
+                                               const float (&t)[3], int c, float& l0, float& l1, float& l2) {
+  const float cc = (float)c;
+  l0 = xfma(xmul(cc, a.musb2_s[0]), xsub(x0, t[0]), l0);
+  l1 = xfma(xmul(cc, a.musb2_s[1]), xsub(x1, t[1]), l1);
+  l2 = xfma(xmul(cc, a.musb2_s[2]), xsub(x2, t[2]), l2);
+}
+
+// Adjoint sweep, deep-halo form, with stage states stored by the forward
+// sweep (same results as adj_kernel<float> in that mode).
+__global__ void __launch_bounds__(kDeepThreads, 1) adj_deep_kernel(SweepArgs<float> a) {
+  cg::cluster_group cl = cg::this_cluster();
+  G2 g;
+  if (!setup_g2(a, cl, g)) return;
+  float* buf[5];
+  float *HX, *fw, *bw;
+  double* scratch;
+  carve2(g, 5, buf, &HX, &fw, &bw, &scratch);
+  float* X = buf[0];
+  float* X1 = buf[1];
+  float* X2 = buf[2];   // x2, then mu1
+  float* Lp = buf[3];   // lambda(n+1), then lambda(n)
+  float* L2 = buf[4];   // mu2
+  float* hxS = g.hasS ? cl.map_shared_rank(HX, g.rank - 1) : nullptr;
+  float* hxN = g.hasN ? cl.map_shared_rank(HX, g.rank + 1) : nullptr;
+  load_rows2(a, g, fw, bw);
+  // adjoint buffers start at zero: their box-edge ghost rows and the ghost
+  // columns of a non-periodic box stay zero
+  const int BUF = (int)deep_buf_floats(g.R, g.W);
+  for (int i = threadIdx.x; i < BUF; i += blockDim.x) {
+    Lp[i] = 0.0f;
+    L2[i] = 0.0f;
+  }
+  __syncthreads();   // ghost tags initialised
+  ghost_prefetch2(a, g, g.a + g.L);
+  if (g.L > 0) ghost_prefetch2(a, g, g.a + g.L - 1);
+  cp_async_commit();
+  const size_t pl = (size_t)g.ny * g.d.nxp;
+  const size_t lvl = 3 * pl;
+  const float dt = a.dt_s, Bth = a.Bth_s, gBth = a.gBth_s, href = a.href_s;
+  // lambda(b) = forcing(b) on own rows
+  load_rows_async2(g, X, a.traj + g.d.traj_off + (size_t)g.L * lvl, 0, g.Rn - 1);
+  cp_async_commit();
+  int cv[kMaxP];
+  float tv[kMaxP][3];
+  prefetch_own_targets2(a, g, g.L, cv, tv);
+  cp_async_wait_all();
+  __syncthreads();
+  cl.sync();   // every CTA of the cluster runs before any exchange-buffer store
+#pragma unroll
+  for (int i = 0; i < kMaxP; ++i) {
+    const int idx = threadIdx.x + i * blockDim.x;
+    if (cv[i]) {
+      const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+      const int o = p2(g, rr, k);
+      float x0, x1, x2, l0, l1, l2;
+      ld3(X, o, 1, x0, x1, x2);
+      ld3(Lp, o, 1, l0, l1, l2);
+      overlap_force2(a, x0, x1, x2, tv[i], cv[i], l0, l1, l2);
+      st3(Lp, o, 1, l0, l1, l2);
+    }
+  }
+  __syncthreads();
+  scatter2(a, g, Lp, g.L);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kMaxP; ++i) {
+    const int idx = threadIdx.x + i * blockDim.x;
+    if (idx < g.Rn * g.nx) {
+      const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+      float v0, v1, v2;
+      ld3(Lp, p2(g, rr, k), 1, v0, v1, v2);
+      publish2(g, Lp, false, rr, k, v0, v1, v2);
+      push2(g, hxS, hxN, rr, k, v0, v1, v2);
+    }
+  }
+  cluster_arrive_release();
+  const int wall_s = (g.flags & F_SWALL) ? 1 : 0;
+  const int wall_n = (g.flags & F_NWALL) ? 2 : 0;
+  for (int l = g.L - 1; l >= 0; --l) {
+    const int n = g.a + l;
+    cluster_wait_acquire();   // lambda(n+1) edge rows in HX; the previous step's phases are done
+    if (l > 0) ghost_prefetch2(a, g, n - 1);
+    cp_async_commit();
+    const float* trl = a.traj + g.d.traj_off + (size_t)l * lvl;
+    const float* s1 = a.stg + g.d.stg_off + ((size_t)l * 2 + 0) * lvl;
+    const float* s2 = a.stg + g.d.stg_off + ((size_t)l * 2 + 1) * lvl;
+    load_rows_async2(g, X2, s2, load_lo2(g, lo_st(g, 1)), load_hi2(g, hi_st(g, 1)));
+    cp_async_commit();
+    load_rows_async2(g, X1, s1, load_lo2(g, lo_st(g, 2)), load_hi2(g, hi_st(g, 2)));
+    cp_async_commit();
+    load_rows_async2(g, X, trl, load_lo2(g, lo_st(g, 3)), load_hi2(g, hi_st(g, 3)));
+    cp_async_commit();
+    copy_hx2(g, HX, Lp);
+    prefetch_own_targets2(a, g, l, cv, tv);
+    fill_fixed2(a, g, X2, lo_st(g, 1), hi_st(g, 1), ghost_src2(g, n, n + 1, 0.5f, 0.5f), false);
+    fill_fixed2(a, g, X1, lo_st(g, 2), hi_st(g, 2), ghost_src2(g, n + 1, n + 1, 1.0f, 0.0f), false);
+    fill_fixed2(a, g, X, 0, g.Rn - 1, ghost_src2(g, n, n, 1.0f, 0.0f), false);
+    cp_async_wait_prev2();   // ghost level n - 1 and x2 have landed (x1, x may still be in flight)
+    __syncthreads();
+    cluster_arrive_relaxed();   // this CTA has copied its exchange buffer out
+    // mu2 = lambda' + dt F'(x2)^T lambda'
+    {
+      const int lo = lo_st(g, 1), hi = hi_st(g, 1);
+      for (int idx = threadIdx.x; idx < (hi - lo + 1) * g.nx; idx += blockDim.x) {
+        const int q = mdiv(idx, g.mnx);
+        const int rr = lo + q, k = idx - q * g.nx;
+        const int o = p2(g, rr, k);
+        const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
+        float rc[8];
+        load_rec8(bw + 8 * (rr + kH), rc);
+        Pt5<float> z, m;
+        load5(X2, o, 1, 4, g.RS, z);
+        load5(Lp, o, 1, 4, g.RS, m);
+        float v0, v1, v2;
+        adj_stage_math<float, true>(z, m, rc, dt, Bth, gBth, href, wall, v0, v1, v2);
+        st3(L2, o, 1, v0, v1, v2);
+        publish2(g, L2, false, rr, k, v0, v1, v2);
+      }
+    }
+    cp_async_wait_one2();   // x1 has landed
+    __syncthreads();
+    // mu1 = mu2 + dt F'(x1)^T mu2, into x2's buffer, whose ghosts become adjoint zeros
+    {
+      fill_fixed2(a, g, X2, 0, g.Rn - 1, ghost_src2(g, n, n, 1.0f, 0.0f), true);
+      const int lo = lo_st(g, 2), hi = hi_st(g, 2);
+      for (int idx = threadIdx.x; idx < (hi - lo + 1) * g.nx; idx += blockDim.x) {
+        const int q = mdiv(idx, g.mnx);
+        const int rr = lo + q, k = idx - q * g.nx;
+        const int o = p2(g, rr, k);
+        const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
+        float rc[8];
+        load_rec8(bw + 8 * (rr + kH), rc);
+        Pt5<float> z, m;
+        load5(X1, o, 1, 4, g.RS, z);
+        load5(L2, o, 1, 4, g.RS, m);
+        float v0, v1, v2;
+        adj_stage_math<float, true>(z, m, rc, dt, Bth, gBth, href, wall, v0, v1, v2);
+        st3(X2, o, 1, v0, v1, v2);
+        publish2(g, X2, false, rr, k, v0, v1, v2);
+      }
+    }
+    cp_async_wait_all();   // x has landed
+    __syncthreads();
+    cluster_wait_acquire();   // neighbours have copied their exchange buffers out
+    // lambda(n) on own rows, in place, with the overlap forcing of level l;
+    // without observations at this level the edge rows go to the neighbours here
+    const bool obs_here = a.lvl_sc[g.d.sc_lvl + l] != a.lvl_sc[g.d.sc_lvl + l + 1];
+#pragma unroll
+    for (int i = 0; i < kMaxP; ++i) {
+      const int idx = threadIdx.x + i * blockDim.x;
+      if (idx < g.Rn * g.nx) {
+        const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+        const int o = p2(g, rr, k);
+        const int wall = (rr == 0 ? wall_s : 0) | (rr == g.Rn - 1 ? wall_n : 0);
+        float rc[8];
+        load_rec8(bw + 8 * (rr + kH), rc);
+        Pt5<float> z, m;
+        load5(X, o, 1, 4, g.RS, z);
+        load5(X2, o, 1, 4, g.RS, m);
+        float ph, pu, pv, qh, qu, qv;
+        ld3(Lp, o, 1, ph, pu, pv);
+        ld3(L2, o, 1, qh, qu, qv);
+        float v0, v1, v2;
+        adj_lambda_math<float, true>(z, m, rc, dt, Bth, gBth, href, wall, ph, pu, pv, qh, qu, qv, v0, v1, v2);
+        if (cv[i]) overlap_force2(a, z.h, z.u, z.v, tv[i], cv[i], v0, v1, v2);
+        st3(Lp, o, 1, v0, v1, v2);
+        if (!obs_here) {
+          publish2(g, Lp, false, rr, k, v0, v1, v2);
+          push2(g, hxS, hxN, rr, k, v0, v1, v2);
+        }
+      }
+    }
+    if (obs_here) {
+      __syncthreads();
+      scatter2(a, g, Lp, l);
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < kMaxP; ++i) {
+        const int idx = threadIdx.x + i * blockDim.x;
+        if (idx < g.Rn * g.nx) {
+          const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
+          float v0, v1, v2;
+          ld3(Lp, p2(g, rr, k), 1, v0, v1, v2);
+          publish2(g, Lp, false, rr, k, v0, v1, v2);
+          push2(g, hxS, hxN, rr, k, v0, v1, v2);
+        }
+      }
+    }
+    cluster_arrive_release();   // lambda(n) edge rows are in the neighbours' exchange buffers
+  }
+  cluster_wait_acquire();
+  // lambda(a) -> packed control layout (FP64)
+  double* out = a.lam_a + g.d.ctrl_off;
+  for (int idx = threadIdx.x; idx < 3 * g.Rn * g.nx; idx += blockDim.x) {
+    const int q = mdiv(idx, g.mnx);   // v * Rn + rr
+    const int v = q / g.Rn;
+    const int rr = q - v * g.Rn, k = idx - q * g.nx;
+    out[((size_t)v * g.ny + g.R0 + rr) * g.nx + k] = (double)Lp[p2(g, rr, k) + v];
+  }
+}
+
 // The dynamic shared-memory attribute is a cap: it is set once per kernel and
 // device to the device's opt-in maximum, together with permission for
 // non-portable (16-CTA) clusters, so that no attribute call is made again
@@ -1669,14 +2477,48 @@ int occupancy_adjoint(int R, int W, int nthreads) {
   return n;
 }
 
+// Whether the deep-halo FP32 sweep with nbuf state buffers can run a launch:
+// every stripe has at least kH rows, a thread holds at most kMaxP own points,
+// the threads fit its register budget and its shared memory fits.
+template <typename T>
+bool deep_fits(const SweepArgs<T>& a, int cl, int nthreads, int nbuf) {
+  if (sizeof(T) != 4 || a.variant == 1 || cl < 1) return false;
+  if (a.min_ny < kH * cl || nthreads > kDeepThreads || nthreads < 64 || nthreads % 32) return false;
+  if ((long long)a.R * (a.W - 2) > (long long)kMaxP * nthreads) return false;
+  return smem_deep(nbuf, a.R, a.W) <= kSmemOptinMax;
+}
+
+template <typename T>
+int forward_kind(const SweepArgs<T>& a, int cl, int nthreads) {
+  if (deep_fits(a, cl, nthreads, 3)) return 2;
+  if (nthreads > max_threads_forward<T>() || smem_forward<T>(a.R, a.W) > kSmemOptinMax) return 0;
+  return 1;
+}
+// The deep-halo adjoint covers evaluations with stored stage states (no
+// checkpoints, no external or Gauss-Newton forcing).
+template <typename T>
+int adjoint_kind(const SweepArgs<T>& a, int cl, int nthreads) {
+  if (a.stg && a.ckpt == 0 && !a.yforce && !a.gn_dx && deep_fits(a, cl, nthreads, 5)) return 2;
+  if (nthreads > 512 || smem_adjoint<T>(a.R, a.W) > kSmemOptinMax) return 0;
+  return 1;
+}
+
 template <typename T>
 cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (forward_kind(a, cl, nthreads) == 2)
+      return launch_cluster(fwd_deep_kernel, a, cl, nthreads, smem_deep(3, a.R, a.W), st);
+  }
   SweepArgs<T> b = a;
   b.tgb_on = use_target_buffer<T>(3, a.R, a.W, true) ? 1 : 0;
   return launch_cluster(fwd_kernel<T>, b, cl, nthreads, smem_forward<T>(a.R, a.W), st);
 }
 template <typename T>
 cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (adjoint_kind(a, cl, nthreads) == 2)
+      return launch_cluster(adj_deep_kernel, a, cl, nthreads, smem_deep(5, a.R, a.W), st);
+  }
   SweepArgs<T> b = a;
   b.tgb_on = use_target_buffer<T>(5, a.R, a.W, true) ? 1 : 0;
   return launch_cluster(adj_kernel<T>, b, cl, nthreads, smem_adjoint<T>(a.R, a.W), st);
@@ -1687,6 +2529,8 @@ cudaError_t launch_tlm(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t
 }
 
 #define DD4DV_INST(T)                                                                        \
+  template int forward_kind<T>(const SweepArgs<T>&, int, int);                               \
+  template int adjoint_kind<T>(const SweepArgs<T>&, int, int);                               \
   template size_t smem_forward<T>(int, int);                                                 \
   template size_t smem_adjoint<T>(int, int);                                                 \
   template size_t smem_tlm<T>(int, int);                                                     \

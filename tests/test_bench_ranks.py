@@ -1,6 +1,7 @@
-"""Multi-GPU runs are replicas: bench.py's only collectives are a max over
-ranks of the elapsed time and a sum of the work.  Checked with world size 2
-on the gloo backend (CPU)."""
+"""bench.py with several ranks: its timing collectives are a max over ranks
+of the elapsed time and a sum of the work (each rank evaluates its own block
+of subdomains, or its own problem in the outer-iteration mode).  Checked with
+world size 2 on the gloo backend (CPU)."""
 import os
 import socket
 

@@ -118,20 +118,34 @@ def test_gpu_outer_loop_reaches_blue_closed_form():
 
 
 def test_sweep_shape_limits():
-    """Launch shapes outside the documented limits are refused with EINVAL
-    (FP32-state forward sweep: at most 384 threads per CTA), and a shape at
-    the limit gives the autotuned result up to the order of J's partial sums."""
+    """Launch shapes no kernel can run are refused with EINVAL: the stripe
+    sweeps take at most 384 (FP32-state forward) / 512 threads, the deep-halo
+    FP32 sweeps at most 640 and need stripes of >= 3 rows (and, for the
+    adjoint, stored stage states).  A shape at a limit gives the autotuned
+    result up to the order of J's partial sums."""
     import paper_2205_06649_gb300 as dd
     wl = workloads.preset("ragged")
     st, inp, _ = oracle.build_setup(wl)
     w = np.concatenate([rand_w(lp.nctrl, seed=700 + s).numpy() for s, lp in enumerate(st.locals)])
     ctx = make_context(wl, st, inp, precision=1, cluster=2)
     J0, g0 = ctx.eval(w)
-    for fwd, adj in (((2, 416), (2, 256)), ((2, 256), (2, 544)), ((17, 256), (2, 256)), ((2, 100), (2, 256))):
+    bad = [(0, (8, 416), (2, 256)),     # stripes of 2 rows: no deep-halo sweep, stripe limit 384
+           (1, (2, 416), (2, 256)),     # stripe sweeps requested
+           (0, (2, 256), (2, 544)),     # recomputed stages: stripe adjoint, limit 512
+           (0, (2, 672), (2, 256)),     # above the deep-halo limit
+           (0, (17, 256), (2, 256)), (0, (2, 100), (2, 256))]
+    for variant, fwd, adj in bad:
+        ctx.set_sweep_variant(variant)
         with pytest.raises(dd.DD4DVError) as e:
             ctx.set_sweep_config(fwd, adj, False)
-        assert e.value.status == -1, (fwd, adj)
+        assert e.value.status == -1, (variant, fwd, adj)
+    ctx.set_sweep_variant(1)
     ctx.set_sweep_config((2, 384), (2, 512), False)
+    J, g = ctx.eval(w)
+    assert rel(J, J0) <= 1e-6 and np.array_equal(g, g0)
+    ctx.set_sweep_variant(0)
+    ctx.set_sweep_config((2, 640), (2, 512), False)
+    assert ctx.sweep_kernels() == {"forward": 2, "adjoint": 1}
     J, g = ctx.eval(w)
     assert rel(J, J0) <= 1e-6 and np.array_equal(g, g0)
     ctx.destroy()

@@ -151,3 +151,67 @@ def test_fp32_analysis_rmse_within_one_percent_of_fp64_oracle():
     assert stats.outer_iters == outer
     assert r_or < r_bg and r32 < r_bg, (r_bg, r_or, r32)
     assert abs(r32 - r_or) <= 0.01 * r_or, (r32, r_or)
+
+
+def _deep_cases():
+    # (workload, overrides, cluster sizes): periodic boxes (P1 = 1), walls,
+    # uneven boxes, stripes of 3 rows (ragged at 6 CTAs: 20 / 6)
+    return [("ragged", {}, (1, 4, 6)), ("ragged", {"P1": 1}, (2, 5)),
+            ("medium", {}, (4, 8))]
+
+
+@pytest.mark.parametrize("case", range(3))
+def test_deep_halo_fp32_sweeps_match_stripe_sweeps_and_oracle(case):
+    """The deep-halo FP32 sweeps (three halo rows, one exchange per step) give
+    the stripe sweeps' gradients bit for bit and J up to the order of its
+    partial sums, and match the oracle within the FP32 bars, at several
+    cluster sizes and thread counts up to 640."""
+    name, over, cls = _deep_cases()[case]
+    if over:
+        wl = workloads.preset(name, **over)
+        st, inp, _ = oracle.build_setup(wl)
+        w = np.concatenate([rand_w(lp.nctrl, seed=1500 + s, scale=0.3).numpy() for s, lp in enumerate(st.locals)])
+        offs = np.cumsum([0] + [lp.nctrl for lp in st.locals])
+        prev = st.background_prev()
+        ref = {}
+        for s in range(len(st.locals)):
+            J, g, _ = st.locals[s].J_and_grad(w[offs[s]:offs[s + 1]], st.xb_traj, prev)
+            ref[s] = (J, g.numpy())
+    else:
+        wl, st, inp, w, ref = _problem(name)
+    ctx = _ctx(wl, st, inp, 1, ckpt_k=0)
+    try:
+        for cl in cls:
+            for nt in (256, 640):
+                ctx.set_sweep_variant(1)
+                ctx.set_sweep_config((cl, min(nt, 384)), (cl, min(nt, 512)), True)
+                assert ctx.sweep_kernels() == {"forward": 1, "adjoint": 1}
+                Js, gs_ = _check(ctx, w, ref, FP32_BARS, (name, cl, nt, "stripe"))
+                ctx.set_sweep_variant(0)
+                ctx.set_sweep_config((cl, nt), (cl, nt), True)
+                assert ctx.sweep_kernels() == {"forward": 2, "adjoint": 2}, (cl, nt)
+                Jd, gd = _check(ctx, w, ref, FP32_BARS, (name, cl, nt, "deep"))
+                assert np.array_equal(gd, gs_), (name, cl, nt)
+                assert rel(Jd, Js) <= 1e-6, (name, cl, nt)
+    finally:
+        ctx.destroy()
+
+
+def test_deep_halo_fp32_forward_in_the_exchange_and_outer_loop():
+    """Algorithm 1 with the deep-halo FP32 sweeps (evaluations, line-search
+    trials, and the exchange, which runs the forward sweep without stage
+    stores) gives the same analysis as with the stripe sweeps."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("ragged")
+    st, inp, _ = oracle.build_setup(wl)
+    out = []
+    for variant in (1, 0):
+        ctx = _ctx(wl, st, inp, 1, ckpt_k=0)
+        ctx.set_sweep_variant(variant)
+        ctx.set_sweep_config((4, 256), (4, 256), True)
+        sv = dd.solver_defaults(max_local_iters=5, max_outer=2, eps_outer=0.0)
+        xa, stats, _ = ctx.run(sv)
+        out.append((xa, ctx.get_controls(), ctx.sweep_kernels()))
+        ctx.destroy()
+    assert out[0][2] == {"forward": 1, "adjoint": 1} and out[1][2] == {"forward": 2, "adjoint": 2}
+    assert rel(out[1][0], out[0][0]) <= 1e-9 and rel(out[1][1], out[0][1]) <= 1e-6
