@@ -161,8 +161,13 @@ def build_problem(wl, precision, stream, inputs=None, shape="", ckpt_k=0):
     ctx.set_decomposition(wl.P1, wl.P2, wl.Q, wl.o_lon, wl.o_lat, wl.o_t, inp["lon_cuts"],
                           inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam,
                           cluster=-1 if not shape else 0, ckpt_k=ckpt_k)
-    if shape:
-        cf, tf, ca, ta, sg = (int(x) for x in shape.split(","))
+    if shape == "model":   # the library's model-based launch shape, no autotuning
+        pass
+    elif shape:
+        v = [int(x) for x in shape.split(",")]
+        cf, tf, ca, ta, sg = v[:5]
+        vf, va = (v[5], v[6]) if len(v) >= 7 else (0, 0)
+        ctx.set_sweep_variant(vf, va)
         ctx.set_sweep_config((cf, tf), (ca, ta), bool(sg))
     return ctx, inp, truth, (inp["obs_level"], inp["obs_var"], inp["obs_fi"], inp["obs_fj"], y, so)
 
@@ -382,10 +387,12 @@ def run_reference(args):
     return 0
 
 
-# Launch shapes the autotuner picked on the large workload (forward cluster,
-# forward threads, adjoint cluster, adjoint threads, stored stage states);
-# the benchmark forces them instead of spending ~40 evaluations on tuning.
-DEFAULT_SHAPES = {("large", 0): "16,512,16,512,0", ("large", 1): "16,384,16,512,1"}
+# Launch shapes for the large workload, as the autotuner picks them on its
+# boxes (forward cluster, forward threads, adjoint cluster, adjoint threads,
+# stored stage states, forward variant, adjoint variant; variant 1 = stripe
+# sweep, 0 = deep-halo FP32 sweep): the benchmark forces them instead of
+# spending ~80 evaluations of 0.7-3.5 s on tuning.
+DEFAULT_SHAPES = {("large", 0): "16,512,16,512,0", ("large", 1): "16,384,16,640,1,1,0"}
 
 
 def roofline_of(ctx, prec, reps=3):
@@ -608,12 +615,12 @@ def scaleup_workloads(qp, nsteps=16):
     return base, base.replace(name=f"scaleup_qp{qp}_undecomposed", P1=1, P2=1), lon_cuts, lat_cuts
 
 
-def scaleup_mode(args, torch):
-    import paper_2205_06649_gb300 as dd
+def scaleup_rows(torch, steps, warmup, autotune=True):
     """Measured scale-up of one outer iteration (Sec. 6-7, Eq. measurscale,
     Table 3), read as Sc_1,QP = T(undecomposed problem of size 3 n_loc^2 QP)
     / T(the same problem in QP subdomains), both on this GPU (all subdomains
     of one problem in one launch per sweep)."""
+    import paper_2205_06649_gb300 as dd
     rows = []
     for qp in sorted(SCALEUP_LAYOUT):
         times = {}
@@ -625,25 +632,31 @@ def scaleup_mode(args, torch):
                 inp["lon_cuts"] = np.asarray(lon_cuts)
                 inp["lat_cuts"] = np.asarray(lat_cuts)
             try:
-                ctx, inp, truth, obs = build_problem(wl, 0, stream.cuda_stream, inputs=inp)
+                ctx, inp, truth, obs = build_problem(wl, 0, stream.cuda_stream, inputs=inp,
+                                                     shape="" if autotune else "model")
             except dd.DD4DVError as e:   # one box larger than a 16-CTA cluster's shared memory
                 times[wl.P1 * wl.P2] = (None, str(e), 0)
                 continue
             solver = solver_for(wl)
             zeros = torch.zeros(ctx.ctrl_total, dtype=torch.float64, device="cuda")
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 ctx.set_controls(zeros)
                 ctx.reset_exchange()
                 ctx.outer_step(solver)
-            ms, stats, _ = timed_steps(ctx, solver, args.steps, zeros, stream, torch)
-            times[wl.P1 * wl.P2] = (ms / args.steps, ctx.sweep_config(), ctx.n_sub)
+            ms, stats, _ = timed_steps(ctx, solver, steps, zeros, stream, torch)
+            times[wl.P1 * wl.P2] = (ms / steps, ctx.sweep_config(), ctx.n_sub)
             ctx.destroy()
         t1, tq = times[1][0], times[qp][0]
         sc = (t1 / tq) if (t1 and tq) else None
         rows.append({"QP": qp, "problem_size": 3 * 32 * 32 * qp, "grid": [wl_dd.nlon, wl_dd.nlat],
-                     "ms_undecomposed": t1, "ms_decomposed": tq,
-                     "scale_up": sc, "shape_undecomposed": times[1][1], "shape_decomposed": times[qp][1]})
+                     "ms_undecomposed": t1, "ms_decomposed": tq, "scale_up": sc,
+                     "shape_undecomposed": times[1][1], "shape_decomposed": times[qp][1]})
         log(f"QP={qp}: T1 {t1} ms, TQP {tq} ms, Sc {sc}")
+    return rows
+
+
+def scaleup_mode(args, torch):
+    rows = scaleup_rows(torch, args.steps, args.warmup)
     print(json.dumps({"metric": "measured scale-up Sc_1,QP of one DD-4DVar outer iteration (n_loc = 32)",
                       "unit": "ratio", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
                       "warmup": args.warmup, "dtype": "f64", "data": "synthetic", "rows": rows}), flush=True)
@@ -804,8 +817,9 @@ def main():
     ap.add_argument("--shape32", default="", help="as --shape, for the FP32-state context of --mode tta")
     ap.add_argument("--ckpt", type=int, default=0, help="ckpt_k of the decomposition (0, -1 or k > 0)")
     ap.add_argument("--shape", default="",
-                    help="fwd_cluster,fwd_threads,adj_cluster,adj_threads,stored_stages: force the "
-                         "sweep launch shapes (e.g. ones an autotuned run reported)")
+                    help="fwd_cluster,fwd_threads,adj_cluster,adj_threads,stored_stages[,fwd_variant,"
+                         "adj_variant]: force the sweep launch shapes (e.g. ones an autotuned run reported); "
+                         "variants 0 = deep-halo FP32 sweep where it applies, 1 = stripe sweep")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -884,6 +898,10 @@ def main():
             "dtype": "f32 state, f64 reductions" if other == 1 else "f64",
             "sweep_launch": o["sweep_launch"], "roofline": o["roofline"], "clocks": o["clocks"]}
         extras["medium_legs"] = medium_extras(args, torch)
+        extras["scaleup_table3"] = {
+            "metric": "measured scale-up Sc_1,QP of one DD-4DVar outer iteration (n_loc = 32, Table 3)",
+            "steps": min(args.steps, 5), "warmup": 2, "launch_shapes": "model-based (no autotuning)",
+            "rows": scaleup_rows(torch, min(args.steps, 5), 2, autotune=False)}
     if rank == 0:
         line = headline_line(args, wl, prec, leg, pts_all / (t_max / 1e3), t_max, world, extras,
                              cpu.result() if cpu else None)

@@ -107,7 +107,12 @@ typedef struct {
  * level, the adjoint recomputes the stage states; k > 0 = checkpointing:
  * evaluations store only the levels 0, k, 2k, ... and the adjoint
  * recomputes each k-step segment from its checkpoint before running back
- * through it (the exchange and dd4dv_trajectories still store every level).
+ * through it (the exchange and dd4dv_trajectories still store every level);
+ * -2 = choose by timing: after the launch shapes are set (or autotuned), one
+ * evaluation is timed with stored stage states (when their buffer fits),
+ * with recomputed stages and with checkpoints every 8, 16 and 32 levels, the
+ * fastest is kept and the unused buffers are freed (dd4dv_checkpoint_interval
+ * reports the choice).
  */
 typedef struct {
   int P1, P2, Q;
@@ -363,6 +368,12 @@ dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* ctx, int* shape, double* eval_m
  * are the same for every shape up to the order of the partial sums of J. */
 dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape);
 
+/* Trajectory storage the evaluations use: *k = 0 stored stage states,
+ * -1 stages recomputed, k > 0 checkpoints every k levels (ckpt_k of
+ * dd4dv_decomp, or the choice made for ckpt_k = -2); eval_ms (may be NULL)
+ * = the evaluation time measured for that choice (0 unless ckpt_k = -2). */
+dd4dv_status dd4dv_checkpoint_interval(const dd4dv_ctx* ctx, int* k, double* eval_ms);
+
 /* Sweep kernels (FP32-state path).  The library has two forms of the forward
  * and adjoint sweeps.  The stripe sweeps exchange one halo row between the
  * CTAs of a subdomain after every RK3 stage.  The deep-halo sweeps (FP32
@@ -371,9 +382,12 @@ dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape);
  * run where every CTA stripe has at least 3 rows, a thread holds at most 4
  * own points and (adjoint) the stage states are stored (ckpt_k = 0, no
  * Gauss-Newton or external forcing).  Both give the same values bit for bit.
- * variant: 0 = deep-halo sweeps wherever they apply (default), 1 = stripe
- * sweeps only.  EINVAL for other values. */
-dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int variant);
+ * forward, adjoint: the variant of each sweep, 0 = deep-halo sweep wherever
+ * it applies (default), 1 = stripe sweep only.  EINVAL for other values.  The
+ * autotuner (cluster = -1 in dd4dv_decomp) times both forms wherever the
+ * deep-halo form applies and keeps the faster one for each sweep;
+ * dd4dv_sweep_kernels reports which run. */
+dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int forward, int adjoint);
 
 /* Which kernels the current launch shapes run: kinds[0] forward, kinds[1]
  * adjoint; 1 = stripe sweep, 2 = deep-halo sweep. */

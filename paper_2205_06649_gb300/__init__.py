@@ -176,9 +176,11 @@ class Context:
         self.traj_total = int(self.traj_offsets[-1])
 
     # ---- queries ----
-    def set_sweep_variant(self, variant: int):
-        """0: deep-halo FP32 sweeps wherever they apply (default); 1: stripe sweeps only."""
-        self._check(lib.dd4dv_set_sweep_variant(self._h, int(variant)))
+    def set_sweep_variant(self, forward: int, adjoint: int = None):
+        """Per sweep: 0 = deep-halo FP32 sweep wherever it applies (default),
+        1 = stripe sweep only (adjoint defaults to the forward's value)."""
+        adjoint = forward if adjoint is None else adjoint
+        self._check(lib.dd4dv_set_sweep_variant(self._h, int(forward), int(adjoint)))
 
     def sweep_kernels(self) -> dict:
         """Kernels the current shapes run: 1 = stripe sweep, 2 = deep-halo sweep."""
@@ -196,8 +198,14 @@ class Context:
         sh = np.zeros(5, dtype=np.int32)
         ms = C.c_double()
         self._check(lib.dd4dv_sweep_config(self._h, C.c_void_p(sh.ctypes.data), C.byref(ms)))
+        k = C.c_int()
+        kms = C.c_double()
+        self._check(lib.dd4dv_checkpoint_interval(self._h, C.byref(k), C.byref(kms)))
+        kinds = self.sweep_kernels()
         return {"forward": [int(sh[0]), int(sh[1])], "adjoint": [int(sh[2]), int(sh[3])],
-                "stored_stages": bool(sh[4]), "eval_ms": ms.value}
+                "stored_stages": bool(sh[4]), "eval_ms": ms.value, "ckpt_k": k.value,
+                "kernels": {"forward": "deep-halo" if kinds["forward"] == 2 else "stripe",
+                            "adjoint": "deep-halo" if kinds["adjoint"] == 2 else "stripe"}}
 
     def set_sweep_config(self, forward, adjoint, stored_stages: bool):
         """forward, adjoint: (cluster size, threads per CTA)."""

@@ -73,7 +73,9 @@ struct dd4dv_ctx {
   int cl = 1, R = 1, W = 3, nthreads = 256;        // adjoint (and TLM base) sweep shape
   int cl_f = 1, R_f = 1, nt_f = 256;               // forward sweep shape
   double tune_ms = 0.0;
-  int variant = 0;            // 0: deep-halo FP32 sweeps where they apply; 1: stripe sweeps only
+  double ckpt_ms = 0.0;       // ckpt_k = -2: measured evaluation time of the chosen storage
+  int variant_f = 0;          // forward sweep: 0 = deep-halo FP32 sweep where it applies,
+  int variant_a = 0;          // 1 = stripe sweep only; variant_a: the same for the adjoint
   size_t tsize = 8;
 
   void* traj = nullptr;
@@ -287,7 +289,7 @@ SweepArgs<T> sweep_args(dd4dv_ctx* ctx) {
   a.W = ctx->W;
   a.err = ctx->err_d;
   a.min_ny = ctx->min_ny;
-  a.variant = ctx->variant;
+  a.variant = ctx->variant_a;   // adjoint (and tangent-linear) launches; forward_sweep sets its own
   return a;
 }
 
@@ -358,6 +360,7 @@ void forward_sweep(dd4dv_ctx* ctx, const int* active, int av, bool full = false)
     a.stg = nullptr;
   }
   a.R = ctx->R_f;
+  a.variant = ctx->variant_f;
   KL(launch_forward<T>(a, ctx->cl_f, ctx->nt_f, ctx->st));
 }
 
@@ -569,6 +572,7 @@ int fwd_kind_at(dd4dv_ctx* ctx, int c, int nt) {
     using T = decltype(t);
     SweepArgs<T> a = sweep_args<T>(ctx);
     a.R = (ctx->max_ny + c - 1) / c;
+    a.variant = ctx->variant_f;
     return forward_kind<T>(a, c, nt);
   });
 }
@@ -579,6 +583,15 @@ int adj_kind_at(dd4dv_ctx* ctx, int c, int nt) {
     a.R = (ctx->max_ny + c - 1) / c;
     return adjoint_kind<T>(a, c, nt);
   });
+}
+
+// Frees one decomposition buffer ahead of dd4dv_destroy.
+void free_dec_buffer(dd4dv_ctx* ctx, void*& p) {
+  if (!p) return;
+  auto it = std::find(ctx->dec_allocs.begin(), ctx->dec_allocs.end(), p);
+  if (it != ctx->dec_allocs.end()) ctx->dec_allocs.erase(it);
+  cudaFree(p);
+  p = nullptr;
 }
 
 // The project's autotuner: for every feasible launch shape -- cluster size
@@ -644,26 +657,37 @@ void autotune(dd4dv_ctx* ctx) {
   const int c0 = ctx->cl, n0 = ctx->nthreads;
   run(c0, n0, &tf0, &ta0);
   run(c0, n0, &tf0, &ta0);
-  const double budget_ms = std::max(2000.0, 60.0 * (tf0 + ta0));
+  const double budget_ms = std::max(2000.0, 80.0 * (tf0 + ta0));
   double spent = 0.0;
-  struct Best { double t = 1e300; int c = 0, nt = 0; };
+  struct Best { double t = 1e300; int c = 0, nt = 0, var = 0; };
   Best best_f[2], best_a[2];
   const bool have_stg = ctx->stg != nullptr;
+  const int var0 = ctx->variant_f;   // the caller's choice: 1 keeps the stripe sweeps
   for (int use : {1, 0}) {
     if (use && !have_stg) continue;
     ctx->use_stg = use;
     for (int c : cls)
-      for (int nt : nts) {
-        if (spent > budget_ms) break;
-        float tf = 0, ta = 0, tf2 = 0, ta2 = 0;
-        if (!run(c, nt, &tf, &ta)) continue;
-        if (!run(c, nt, &tf2, &ta2)) continue;
-        spent += tf + ta + tf2 + ta2;
-        tf = std::min(tf, tf2);
-        ta = std::min(ta, ta2);
-        if (tf < best_f[use].t) best_f[use] = {tf, c, ctx->nt_f};
-        if (ta < best_a[use].t) best_a[use] = {ta, c, nt};
-      }
+      for (int nt : nts)
+        for (int var : {0, 1}) {
+          if (spent > budget_ms) break;
+          if (var < var0) continue;
+          ctx->variant_f = ctx->variant_a = var;
+          // the stripe form is timed separately only where the deep form applied
+          if (var == 1 && var0 == 0) {
+            ctx->variant_f = ctx->variant_a = 0;
+            const bool deep = fwd_kind_at(ctx, c, nt) == 2 || adj_kind_at(ctx, c, nt) == 2;
+            ctx->variant_f = ctx->variant_a = 1;
+            if (!deep) continue;
+          }
+          float tf = 0, ta = 0, tf2 = 0, ta2 = 0;
+          if (!run(c, nt, &tf, &ta)) continue;
+          if (!run(c, nt, &tf2, &ta2)) continue;
+          spent += tf + ta + tf2 + ta2;
+          tf = std::min(tf, tf2);
+          ta = std::min(ta, ta2);
+          if (tf < best_f[use].t) best_f[use] = {tf, c, ctx->nt_f, var};
+          if (ta < best_a[use].t) best_a[use] = {ta, c, nt, var};
+        }
   }
   for (auto& e : ev) cudaEventDestroy(e);
   int use = 0;
@@ -671,10 +695,12 @@ void autotune(dd4dv_ctx* ctx) {
       (!best_f[0].c || best_f[1].t + best_a[1].t < best_f[0].t + best_a[0].t))
     use = 1;
   if (!best_f[use].c || !best_a[use].c) {   // nothing measured: keep the starting shape
-    best_f[use] = {tf0, c0, n0};
-    best_a[use] = {ta0, c0, n0};
+    best_f[use] = {tf0, c0, n0, var0};
+    best_a[use] = {ta0, c0, n0, var0};
   }
   ctx->use_stg = use;
+  ctx->variant_f = best_f[use].var;
+  ctx->variant_a = best_a[use].var;
   ctx->cl_f = best_f[use].c;
   ctx->nt_f = best_f[use].nt;
   ctx->R_f = (ctx->max_ny + ctx->cl_f - 1) / ctx->cl_f;
@@ -684,13 +710,59 @@ void autotune(dd4dv_ctx* ctx) {
   ctx->dec.cluster = ctx->cl;
   ctx->tune_ms = best_f[use].t + best_a[use].t;
   sync(ctx);
-  if (!use && ctx->stg) {   // recomputing the stages won: give the memory back
-    auto it = std::find(ctx->dec_allocs.begin(), ctx->dec_allocs.end(), ctx->stg);
-    if (it != ctx->dec_allocs.end()) ctx->dec_allocs.erase(it);
-    cudaFree(ctx->stg);
-    ctx->stg = nullptr;
+  if (!use && ctx->stg && ctx->dec.ckpt_k != -2) {   // recomputing the stages won: give the memory back
+    free_dec_buffer(ctx, ctx->stg);
     ctx->stg_elems = 0;
   }
+}
+
+// Checkpoint intervals the library tries for ckpt_k = -2.
+constexpr int kTunedCkpt[3] = {8, 16, 32};
+
+// ckpt_k = -2: time one forward + adjoint evaluation (w = 0, CUDA events,
+// best of two) with stored stage states (when their buffer exists), with the
+// stages recomputed, and with k-step checkpoints for k in kTunedCkpt, at the
+// current launch shapes; keep the fastest and free the buffers it does not
+// use.  Results do not depend on the choice.
+void tune_checkpoint(dd4dv_ctx* ctx) {
+  CK(cudaMemsetAsync(ctx->io_a, 0, ctx->ctrl_total * sizeof(double), ctx->st));
+  cudaEvent_t ev[2];
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  auto time_eval = [&](int k, bool stg) -> float {
+    ctx->ckpt = k;
+    ctx->use_stg = stg;
+    float best = 1e30f;
+    for (int r = 0; r < 3; ++r) {
+      by_precision(ctx, [&](auto t) {
+        using T = decltype(t);
+        CK(cudaEventRecord(ev[0], ctx->st));
+        eval_T<T>(ctx, ctx->io_a, ctx->io_p, ctx->io_b, nullptr, nullptr, 0, nullptr);
+        CK(cudaEventRecord(ev[1], ctx->st));
+        return 0;
+      });
+      CK(cudaEventSynchronize(ev[1]));
+      float ms = 0;
+      CK(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+      if (r > 0) best = std::min(best, ms);   // the first run warms up
+    }
+    return best;
+  };
+  struct Cand { int k; bool stg; float ms; };
+  std::vector<Cand> c;
+  if (ctx->stg) c.push_back({0, true, time_eval(0, true)});
+  c.push_back({0, false, time_eval(0, false)});
+  for (int k : kTunedCkpt) c.push_back({k, false, time_eval(k, false)});
+  for (auto& e : ev) cudaEventDestroy(e);
+  const Cand best = *std::min_element(c.begin(), c.end(), [](const Cand& a, const Cand& b) { return a.ms < b.ms; });
+  ctx->ckpt = best.k;
+  ctx->use_stg = best.stg;
+  sync(ctx);
+  if (!best.stg && ctx->stg) {
+    free_dec_buffer(ctx, ctx->stg);
+    ctx->stg_elems = 0;
+  }
+  if (best.k == 0 && ctx->seg) free_dec_buffer(ctx, ctx->seg);
+  ctx->ckpt_ms = best.ms;
 }
 
 // ---------------------------------------------------------------------------
@@ -742,7 +814,9 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
       const int core = ctx->t_cuts[k + 1] - ctx->t_cuts[k];
       if (core < 2 * d.o_t + 1) fail(ctx, DD4DV_EINVAL, "time core block %d (%d) < 2*o_t+1", k, core);
     }
-  if (d.ckpt_k < -1) fail(ctx, DD4DV_EINVAL, "ckpt_k must be >= -1");
+  if (d.ckpt_k < -2) fail(ctx, DD4DV_EINVAL, "ckpt_k must be >= -2");
+  // ckpt_k = -2: the segment buffers are sized for the largest interval tried
+  const int seg_k = d.ckpt_k > 0 ? d.ckpt_k : (d.ckpt_k == -2 ? kTunedCkpt[2] : 0);
 
   const int n_sub = d.P1 * d.P2 * d.Q;
   std::vector<SubDesc> subs(n_sub);
@@ -786,7 +860,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
         s.stg_off = stgl;
         stgl += (long long)L * 2 * 3 * s.ny * s.nxp;
         s.seg_off = segl;
-        if (d.ckpt_k > 0) segl += (long long)(std::min(d.ckpt_k, std::max(L, 1)) + 1) * 3 * s.ny * s.nxp;
+        if (seg_k > 0) segl += (long long)(std::min(seg_k, std::max(L, 1)) + 1) * 3 * s.ny * s.nxp;
         ctrl += 3LL * s.ny * s.nx;
         trj += (long long)(L + 1) * 3 * s.ny * s.nxp;
         ptrj += (long long)(L + 1) * 3 * s.ny * s.nx;
@@ -990,7 +1064,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   ctx->gn_dx = nullptr;
   ctx->ckpt = d.ckpt_k > 0 ? d.ckpt_k : 0;
   ctx->seg = nullptr;
-  if (d.ckpt_k > 0) ctx->seg = dalloc<unsigned char>(ctx, std::max<long long>(1, segl) * ctx->tsize, &L);
+  if (seg_k > 0) ctx->seg = dalloc<unsigned char>(ctx, std::max<long long>(1, segl) * ctx->tsize, &L);
   ctx->tgt = dalloc<unsigned char>(ctx, ctx->traj_elems * ctx->tsize, &L);
   ctx->bnd = dalloc<unsigned char>(ctx, ctx->gtraj * ctx->tsize, &L);
   const size_t C = (size_t)ctrl;
@@ -1038,7 +1112,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   // Stored stage states (ckpt_k = 0) are twice the trajectory: allocate them
   // last, and only if they leave a reserve of 4 GB + 5 % of the device free;
   // otherwise the adjoint recomputes the stages.
-  if (d.ckpt_k == 0) {
+  if (d.ckpt_k == 0 || d.ckpt_k == -2) {
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     const double need = (double)std::max<long long>(1, stgl) * ctx->tsize;
@@ -1099,6 +1173,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   sync(ctx);
   ctx->has_dec = true;
   if (d.cluster < 0) autotune(ctx);
+  if (d.ckpt_k == -2) tune_checkpoint(ctx);
 }
 
 }  // namespace
@@ -2170,10 +2245,21 @@ dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape) {
   });
 }
 
-dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int variant) {
+dd4dv_status dd4dv_checkpoint_interval(const dd4dv_ctx* cctx, int* k, double* eval_ms) {
+  auto* ctx = const_cast<dd4dv_ctx*>(cctx);
+  if (!ctx) return DD4DV_EINVAL;
+  if (!ctx->has_dec) return DD4DV_ESTATE;
+  if (k) *k = ctx->use_stg ? 0 : (ctx->ckpt > 0 ? ctx->ckpt : -1);
+  if (eval_ms) *eval_ms = ctx->ckpt_ms;
+  return DD4DV_OK;
+}
+
+dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int forward, int adjoint) {
   return guard(ctx, [&] {
-    if (variant != 0 && variant != 1) fail(ctx, DD4DV_EINVAL, "variant must be 0 (automatic) or 1 (stripe sweeps)");
-    ctx->variant = variant;
+    for (int v : {forward, adjoint})
+      if (v != 0 && v != 1) fail(ctx, DD4DV_EINVAL, "variants must be 0 (automatic) or 1 (stripe sweeps)");
+    ctx->variant_f = forward;
+    ctx->variant_a = adjoint;
     ctx->drop_graphs();
     return DD4DV_OK;
   });

@@ -1923,19 +1923,25 @@ __device__ void copy_hx2(const G2& g, const float* HX, float* Z) {
 
 // Rows [lo, hi] of a stored [3][ny][nxp] block into Z with cp.async (the
 // caller commits and waits), their periodic ghost columns too, and at a wall
-// the mirror row (read directly).
+// the mirror row (read directly).  A warp's 4-byte copies into 16-byte slots
+// would hit every bank four times; each group of eight lanes starts at a
+// different slot component instead (four copies per point, the unused fourth
+// component taking h), which spreads every copy instruction over all banks.
 __device__ void load_rows_async2(const G2& g, float* Z, const float* src, int lo, int hi) {
   const size_t pl = (size_t)g.ny * g.d.nxp;
   const int n = (hi - lo + 1) * g.nx;
   const bool per = g.flags & F_PERIODIC;
+  const int rot = (threadIdx.x >> 3) & 3;
   for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
     const int q = mdiv(idx, g.mnx);
     const int rr = lo + q, k = idx - q * g.nx;
     const float* s = src + (size_t)(g.R0 + rr) * g.d.nxp + k;
     float* d = Z + p2(g, rr, k);
-    cp_async_4or8(d, s, 4);
-    cp_async_4or8(d + 1, s + pl, 4);
-    cp_async_4or8(d + 2, s + 2 * pl, 4);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int v = (c + rot) & 3;
+      cp_async_4or8(d + v, s + (size_t)(v < 3 ? v : 0) * pl, 4);
+    }
     if (per && (k == 0 || k == g.nx - 1)) {
       float* e = Z + p2(g, rr, k == 0 ? g.nx : -1);
       cp_async_4or8(e, s, 4);

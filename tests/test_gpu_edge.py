@@ -149,3 +149,25 @@ def test_sweep_shape_limits():
     J, g = ctx.eval(w)
     assert rel(J, J0) <= 1e-6 and np.array_equal(g, g0)
     ctx.destroy()
+
+
+def test_forced_line_search_failures_are_counted_and_reported():
+    """Host-forced failure of the local minimiser: with the Armijo constant
+    c1 = 1 - 1e-9 and one trial per iteration, the sufficient-decrease test
+    J(w + p) <= J(w) + c1 g.p cannot hold for a J with curvature (the
+    background term alone gives p.Hp >= |p|^2 = 1 for the first direction
+    -g/|g|).  Every subdomain's first line search fails, its control stays at
+    the start point, each outer iteration counts one failure per subdomain,
+    and with eps_outer = 0 dd4dv_run ends with DD4DV_NOTCONV."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("small")
+    st, inp, _ = oracle.build_setup(wl)
+    ctx = make_context(wl, st, inp, cluster=2)
+    sv = dd.solver_defaults(max_local_iters=5, max_trials=1, c1=1.0 - 1e-9, max_outer=2, eps_outer=0.0)
+    xa, stats, status = ctx.run(sv)
+    assert status == 1   # DD4DV_NOTCONV
+    assert stats.outer_iters == 2
+    assert stats.n_linesearch_fail == 2 * ctx.n_sub
+    assert float(np.abs(ctx.get_controls()).max()) == 0.0
+    assert stats.dw_inf == 0.0
+    ctx.destroy()

@@ -215,3 +215,26 @@ def test_deep_halo_fp32_forward_in_the_exchange_and_outer_loop():
         ctx.destroy()
     assert out[0][2] == {"forward": 1, "adjoint": 1} and out[1][2] == {"forward": 2, "adjoint": 2}
     assert rel(out[1][0], out[0][0]) <= 1e-9 and rel(out[1][1], out[0][1]) <= 1e-6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_checkpoint_interval_matches_oracle(precision):
+    """ckpt_k = -2: the library times stored stages, recomputed stages and
+    checkpoints every 8, 16 and 32 levels, keeps the fastest (reported by
+    dd4dv_checkpoint_interval) and still matches the oracle."""
+    import paper_2205_06649_gb300 as dd
+    wl, st, inp, w, ref = _problem("ragged")
+    ctx = dd.Context(wl.nlon, wl.nlat, inp["dt"], wl.nsteps, precision=precision)
+    ctx.set_background(inp["x_b0"])
+    ctx.set_background_error(wl.sigma_b, wl.corr_len, wl.rf_passes)
+    ob = st.obs
+    ctx.set_observations(ob.level, ob.var, ob.fi, ob.fj, ob.value, ob.sigma_o)
+    ctx.set_decomposition(wl.P1, wl.P2, wl.Q, wl.o_lon, wl.o_lat, wl.o_t, inp["lon_cuts"],
+                          inp["lat_cuts"], inp["t_cuts"], mu=wl.mu, lam=wl.lam, cluster=2, ckpt_k=-2)
+    try:
+        cfg = ctx.sweep_config()
+        assert cfg["ckpt_k"] in (0, -1, 8, 16, 32), cfg
+        assert cfg["stored_stages"] == (cfg["ckpt_k"] == 0)
+        _check(ctx, w, ref, FP64_BARS if precision == 0 else FP32_BARS, ("ckpt-tuned", precision, cfg))
+    finally:
+        ctx.destroy()
