@@ -34,4 +34,4 @@ from .lbfgs import lbfgs, LbfgsResult  # noqa: F401
 from .gauss_newton import residuals, gn_operator, gn_hessvec, cg, gauss_newton, CgResult, GnResult  # noqa: F401
 from .dd4dvar import dd4dvar, global_J, rmse, DDResult  # noqa: F401
 from .problem import build_setup  # noqa: F401
-from .tz import tz_rhs, tz_forward  # noqa: F401
+from .tz import tz_rhs, tz_forward, tz_global_J  # noqa: F401

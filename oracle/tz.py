@@ -37,6 +37,7 @@ form, equal to the flux form wherever h is uniform.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from .swe import F64, Grid
@@ -145,3 +146,28 @@ def tz_forward(grid: Grid, x0: torch.Tensor, dt: float, nsteps: int, p: int, q: 
         x = x / 3.0 + (2.0 / 3.0) * (x2 + dt * tz_rhs(x2, grid, p, q, alpha))
         out.append(x)
     return torch.stack(out)
+
+
+def tz_global_J(grid: Grid, dt: float, nsteps: int, xb0, sigma_b, obs, p: int, q: int, alpha: float,
+                w: torch.Tensor, lam: float = 1.0) -> torch.Tensor:
+    """Global 4D-Var functional of the undecomposed problem with the
+    Turkel-Zwas tendencies (Eq. min3sec with halves of squares, as the local
+    functional of oracle/local.py; diagonal B = diag(sigma_b)^2):
+
+        J(w) = 1/2 w.w + lam/2 sum_obs (H x_(n_obs) - y)^2 / sigma_o^2,
+        x_0 = u_0^b + sigma_b w,  x_(n+1) = SSP-RK3 step of tz_rhs (tz_forward),
+
+    with H the bilinear operator of decomposition.bilinear_support.  Written
+    with torch operations so that its gradient is the reverse-mode derivative."""
+    from .decomposition import bilinear_support
+    sb = torch.as_tensor(np.asarray(sigma_b, dtype=np.float64))[:, None, None]
+    x0 = torch.as_tensor(np.asarray(xb0), dtype=F64) + sb * w.reshape(3, grid.nlat, grid.nlon)
+    traj = tz_forward(grid, x0, dt, nsteps, p, q, alpha)
+    J = 0.5 * (w * w).sum()
+    for k in range(len(obs.level)):
+        hx = 0.0
+        for (j, i, wgt) in bilinear_support(float(obs.fi[k]), float(obs.fj[k]), grid.nlon):
+            hx = hx + wgt * traj[int(obs.level[k]), int(obs.var[k]), j, i]
+        d = hx - float(obs.value[k])
+        J = J + lam * 0.5 * d * d / float(obs.sigma_o[k]) ** 2
+    return J

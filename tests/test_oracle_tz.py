@@ -156,3 +156,76 @@ def test_fourier_symbol_of_the_averaged_terms(p, q, alpha):
     assert _rel(F[1, rows], Fu[rows]) <= 1e-12
     assert _rel(F[0, rows], Fh) <= 1e-12
     assert float(F[2, rows].abs().max()) <= 1e-12 * float(Fu.abs().max())
+
+
+def _tz_obs(nlon, nlat, nsteps, levels, seed, grid_points=False, n=30):
+    import oracle
+    rng = np.random.default_rng(seed)
+    if grid_points:
+        # distinct grid points (each observed once per variable)
+        flat = rng.choice(nlon * nlat, size=n, replace=False)
+        fi, fj = (flat % nlon).astype(np.float64), (flat // nlon).astype(np.float64)
+    else:
+        fi = rng.uniform(0, nlon, n)
+        fj = rng.uniform(0, nlat - 1, n)
+    lev = rng.choice(levels, n)
+    var = rng.integers(0, 3, n)
+    val = rng.standard_normal(n)
+    so = np.where(var == 0, 1.0, 0.05)
+    return oracle.Observations(lev, var, fi, fj, val, so)
+
+
+def test_tz_global_functional_gives_the_blue_analysis_at_level_zero():
+    """Closed form: with observations of distinct grid points at level 0
+    only and diagonal B, J(w) = 1/2 w.w + 1/2 sum (x_b + sigma_b w - y)^2 /
+    sigma_o^2 has its minimum at w* = sigma_b (y - x_b) / (sigma_b^2 +
+    sigma_o^2) at the observed components (0 elsewhere), whatever the
+    model: the reverse-mode gradient vanishes there and J(w*) is the
+    closed-form minimum 1/2 sum (y - x_b)^2 / (sigma_b^2 + sigma_o^2)."""
+    from oracle.tz import tz_global_J
+    g = _grid(12, 8)
+    x = _analytic_state(g)
+    sb = np.array([5.0, 0.1, 0.1])
+    ob = _tz_obs(12, 8, 3, [0], seed=1, grid_points=True)
+    ob.value = np.array([float(x[v, int(j), int(i)]) for v, j, i in zip(ob.var, ob.fj, ob.fi)]) + ob.value
+    w = torch.zeros(3 * 8 * 12, dtype=F64)
+    jmin = 0.0
+    for k in range(len(ob.level)):
+        v, j, i = int(ob.var[k]), int(ob.fj[k]), int(ob.fi[k])
+        dv = ob.value[k] - float(x[v, j, i])
+        w[(v * 8 + j) * 12 + i] = sb[v] * dv / (sb[v] ** 2 + ob.sigma_o[k] ** 2)
+        jmin += 0.5 * dv * dv / (sb[v] ** 2 + ob.sigma_o[k] ** 2)
+    w.requires_grad_(True)
+    J = tz_global_J(g, 300.0, 3, x, sb, ob, 2, 1, 0.5, w)
+    (gr,) = torch.autograd.grad(J, w)
+    assert float(gr.abs().max()) <= 1e-11
+    assert abs(float(J) - jmin) <= 1e-12 * jmin
+
+
+@pytest.mark.parametrize("p,q,alpha", [(1, 1, 0.0), (2, 1, 0.5), (1, 2, 1.0)])
+def test_tz_global_functional_gradient_by_brute_force_differences(p, q, alpha):
+    """The functional's reverse-mode gradient equals central differences of
+    J in every component (tiny grid, observations at levels 1..3, so every
+    step of the Turkel-Zwas model and the walls enter)."""
+    from oracle.tz import tz_global_J
+    g = _grid(8, 6)
+    x = _analytic_state(g)
+    sb = np.array([5.0, 0.1, 0.1])
+    import oracle
+    ob = _tz_obs(8, 6, 3, [1, 2, 3], seed=2)
+    # values near the model's (y = H x_0 + noise): J stays small enough for
+    # central differences to resolve every component
+    ob.value = oracle.observe(8, x[None], np.zeros(len(ob.level), dtype=int), ob.var, ob.fi, ob.fj) + ob.value
+    n = 3 * 6 * 8
+    w = (0.3 * torch.randn(n, generator=torch.Generator().manual_seed(5), dtype=F64)).requires_grad_(True)
+    J = tz_global_J(g, 300.0, 3, x, sb, ob, p, q, alpha, w)
+    (gr,) = torch.autograd.grad(J, w)
+    fd = np.zeros(n)
+    h = 1e-4
+    with torch.no_grad():
+        for k in range(n):
+            e = torch.zeros(n, dtype=F64)
+            e[k] = h
+            fd[k] = (float(tz_global_J(g, 300.0, 3, x, sb, ob, p, q, alpha, w + e))
+                     - float(tz_global_J(g, 300.0, 3, x, sb, ob, p, q, alpha, w - e))) / (2 * h)
+    assert np.linalg.norm(gr.numpy() - fd) <= 1e-7 * np.linalg.norm(fd)
