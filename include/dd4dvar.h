@@ -289,6 +289,41 @@ dd4dv_status dd4dv_boundary_trajectory(dd4dv_ctx* ctx, double* traj, int device_
  * traj [nsteps+1][3][nlat][nlon], FP64 on the device. */
 dd4dv_status dd4dv_forward(dd4dv_ctx* ctx, const double* x0, double* traj, int device_ptrs);
 
+/* The Turkel-Zwas scheme of Sec. 7 (the paper's discretisation, with
+ * longitude stride p, latitude stride q and averaging weight alpha) on the
+ * undecomposed problem (the whole sphere, P = Q = 1).  Pressure gradients
+ * over i +- p and j +- q, the Coriolis terms of the u (v) equation averaged
+ * over i +- p (j +- q), the divergence averaged over (i +- p, j +- q), with
+ * weight alpha; advection with stride 1; walls mirror (h, u, -v) to depth q;
+ * SSP-RK3 steps of dt.  Readings of the garbled print: the printed leapfrog
+ * increments are semi-discrete tendencies with sigma_lon = 1/(2 a dlambda),
+ * sigma_lat = 1/(2 a dtheta); the meridional advection of v uses v
+ * differences; H carries the sigma factors and h / cos(theta).  FP64, global
+ * memory, one thread per grid point; the decomposed sweeps keep the centred
+ * scheme (p = q = 1, alpha = 0, flux-form continuity).
+ * Arguments: 1 <= p < nlon/2, 1 <= q < nlat, 0 <= alpha <= 1 (else EINVAL);
+ * states [3][nlat][nlon], trajectories [nsteps+1][3][nlat][nlon];
+ * device_ptrs as in the conventions.
+ *   dd4dv_tz_forward: traj = the model run from x0.
+ *   dd4dv_tz_tlm: dtraj = the tangent-linear run from dx0 about the run from
+ *     x0 (Algorithm 6, TLM).
+ *   dd4dv_tz_adjoint: dx0 = sum_n (d x_n / d x_0)^T y_n (Algorithm 6, ADJ),
+ *     the transpose of dd4dv_tz_tlm.
+ *   dd4dv_tz_eval: the global functional J(w) = 1/2 w.w + 1/2 sum_obs
+ *     (H x_n - y)^2 / sigma_o^2 with x_0 = u_0^b + sigma_b w (diagonal B:
+ *     set_background_error with corr_len_cells = 0, else EINVAL; ESTATE
+ *     before set_background / set_background_error), the context's
+ *     observations, and its gradient w + sigma_b lambda_0 (grad may be NULL).
+ * Each call allocates its trajectory and scratch for the call. */
+dd4dv_status dd4dv_tz_forward(dd4dv_ctx* ctx, int p, int q, double alpha, const double* x0, double* traj,
+                              int device_ptrs);
+dd4dv_status dd4dv_tz_tlm(dd4dv_ctx* ctx, int p, int q, double alpha, const double* x0, const double* dx0,
+                          double* dtraj, int device_ptrs);
+dd4dv_status dd4dv_tz_adjoint(dd4dv_ctx* ctx, int p, int q, double alpha, const double* x0, const double* ytraj,
+                              double* dx0, int device_ptrs);
+dd4dv_status dd4dv_tz_eval(dd4dv_ctx* ctx, int p, int q, double alpha, const double* w, double* J, double* grad,
+                           int device_ptrs);
+
 /* Observation operator H (bilinear, as in dd4dv_set_observations) applied to
  * a global trajectory traj [nsteps+1][3][nlat][nlon]: out[k] = H_k traj. */
 dd4dv_status dd4dv_observe(dd4dv_ctx* ctx, const double* traj, long long n, const int* level,

@@ -416,6 +416,36 @@ class Context:
         return out
 
     # ---- outer loop (Alg. 1) ----
+    # ---- Turkel-Zwas scheme, undecomposed problem (host numpy arrays) ----
+    def _state(self, x):
+        return np.ascontiguousarray(x, dtype=np.float64)
+
+    def tz_forward(self, p, q, alpha, x0):
+        out = np.zeros((self.nsteps + 1, 3, self.nlat, self.nlon))
+        self._check(lib.dd4dv_tz_forward(self._h, p, q, alpha, _ptr(self._state(x0), np.float64, False),
+                                         C.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def tz_tlm(self, p, q, alpha, x0, dx0):
+        out = np.zeros((self.nsteps + 1, 3, self.nlat, self.nlon))
+        self._check(lib.dd4dv_tz_tlm(self._h, p, q, alpha, _ptr(self._state(x0), np.float64, False),
+                                     _ptr(self._state(dx0), np.float64, False), C.c_void_p(out.ctypes.data), 0))
+        return out
+
+    def tz_adjoint(self, p, q, alpha, x0, ytraj):
+        out = np.zeros((3, self.nlat, self.nlon))
+        self._check(lib.dd4dv_tz_adjoint(self._h, p, q, alpha, _ptr(self._state(x0), np.float64, False),
+                                         _ptr(self._state(ytraj), np.float64, False), C.c_void_p(out.ctypes.data),
+                                         0))
+        return out
+
+    def tz_eval(self, p, q, alpha, w):
+        J = np.zeros(1)
+        g = np.zeros(3 * self.nlat * self.nlon)
+        self._check(lib.dd4dv_tz_eval(self._h, p, q, alpha, _ptr(self._state(w), np.float64, False),
+                                      C.c_void_p(J.ctypes.data), C.c_void_p(g.ctypes.data), 0))
+        return float(J[0]), g
+
     def set_owned(self, owned=None):
         """Subdomains this context evaluates and solves (n_sub flags; None = all)."""
         if owned is None:

@@ -1778,6 +1778,242 @@ static void check_solver(dd4dv_ctx* ctx, const dd4dv_solver* s) {
 
 }  // extern "C"
 
+// ---------------------------------------------------------------------------
+// The Turkel-Zwas scheme (Sec. 7, strides p, q, averaging weight alpha) on the
+// undecomposed problem: global model runs, tangent-linear and adjoint runs,
+// and the global 4D-Var functional with its gradient.  Kernels in tz.cu.
+namespace {
+
+TzArgs tz_args(dd4dv_ctx* ctx, int p, int q, double alpha) {
+  const dd4dv_model& m = ctx->m;
+  if (p < 1 || q < 1 || 2 * p >= m.nlon || q >= m.nlat || !(alpha >= 0.0 && alpha <= 1.0))
+    fail(ctx, DD4DV_EINVAL, "Turkel-Zwas parameters need 1 <= p < nlon/2, 1 <= q < nlat, 0 <= alpha <= 1");
+  TzArgs t;
+  t.rows = ctx->rows_d;
+  t.nlon = m.nlon;
+  t.nlat = m.nlat;
+  t.p = p;
+  t.q = q;
+  t.alpha = alpha;
+  const double pi = 3.14159265358979323846;
+  t.slon = 1.0 / (2.0 * m.radius * (2.0 * pi / m.nlon));
+  t.slat = ctx->Bth;
+  t.g = m.gravity;
+  t.dt = m.dt;
+  return t;
+}
+
+// Device scratch that lives for one call.
+struct TzBufs {
+  std::vector<void*> ptrs;
+  dd4dv_ctx* ctx;
+  explicit TzBufs(dd4dv_ctx* c) : ctx(c) {}
+  double* get(size_t n) {
+    double* p = dalloc<double>(ctx, n);
+    ptrs.push_back(p);
+    return p;
+  }
+  ~TzBufs() {
+    if (ctx->st) cudaStreamSynchronize(ctx->st);
+    for (void* p : ptrs) cudaFree(p);
+  }
+};
+
+void tz_step(dd4dv_ctx* ctx, const TzArgs& t, const double* x, double* s1, double* s2, double* nx) {
+  KL(launch_tz_stage(t, x, x, s1, 0.0, 1.0, ctx->st));
+  KL(launch_tz_stage(t, x, s1, s2, 0.75, 0.25, ctx->st));
+  KL(launch_tz_stage(t, x, s2, nx, 1.0 / 3.0, 2.0 / 3.0, ctx->st));
+}
+
+void tz_run(dd4dv_ctx* ctx, const TzArgs& t, const double* x0, double* traj, double* s1, double* s2) {
+  const size_t G = ctx->gstate;
+  CK(cudaMemcpyAsync(traj, x0, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  for (int n = 0; n < ctx->m.nsteps; ++n) tz_step(ctx, t, traj + (size_t)n * G, s1, s2, traj + (size_t)(n + 1) * G);
+}
+
+// lam <- M_n^T lam for the step from x = x(n): the stage states recomputed,
+// then mu2 = lam + dt F'(x2)^T lam, mu1 = mu2 + dt F'(x1)^T mu2,
+// lam(n) = lam/3 + mu2/2 + (mu1 + dt F'(x)^T mu1)/6 (the transposed SSP-RK3
+// step, as in the box sweeps).
+void tz_adjoint_step(dd4dv_ctx* ctx, const TzArgs& t, const double* x, double* s1, double* s2, double* lam,
+                     double* mu2, double* mu1, double* g3) {
+  const size_t G = ctx->gstate;
+  KL(launch_tz_stage(t, x, x, s1, 0.0, 1.0, ctx->st));
+  KL(launch_tz_stage(t, x, s1, s2, 0.75, 0.25, ctx->st));
+  CK(cudaMemcpyAsync(mu2, lam, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  KL(launch_tz_adj_scatter(t, s2, lam, mu2, t.dt, ctx->st));
+  CK(cudaMemcpyAsync(mu1, mu2, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  KL(launch_tz_adj_scatter(t, s1, mu2, mu1, t.dt, ctx->st));
+  CK(cudaMemcpyAsync(g3, mu1, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  KL(launch_tz_adj_scatter(t, x, mu1, g3, t.dt, ctx->st));
+  KL(launch_tz_lincomb(lam, lam, mu2, g3, 1.0 / 3.0, 0.5, 1.0 / 6.0, (long long)G, ctx->st));
+}
+
+const double* tz_in(dd4dv_ctx* ctx, TzBufs& b, const double* src, size_t n, int device_ptrs) {
+  if (device_ptrs) return src;
+  double* d = b.get(n);
+  h2d(ctx, d, src, n * sizeof(double));
+  return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+dd4dv_status dd4dv_tz_forward(dd4dv_ctx* ctx, int p, int q, double alpha, const double* x0, double* traj,
+                              int device_ptrs) {
+  return guard(ctx, [&] {
+    const TzArgs t = tz_args(ctx, p, q, alpha);
+    if (!x0 || !traj) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    const size_t G = ctx->gstate, T = (size_t)(ctx->m.nsteps + 1) * G;
+    TzBufs b(ctx);
+    const double* x = tz_in(ctx, b, x0, G, device_ptrs);
+    double* out = device_ptrs ? traj : b.get(T);
+    double* s = b.get(2 * G);
+    tz_run(ctx, t, x, out, s, s + G);
+    if (!device_ptrs) d2h(ctx, traj, out, T * sizeof(double));
+    sync(ctx);
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_tz_tlm(dd4dv_ctx* ctx, int p, int q, double alpha, const double* x0, const double* dx0,
+                          double* dtraj, int device_ptrs) {
+  return guard(ctx, [&] {
+    const TzArgs t = tz_args(ctx, p, q, alpha);
+    if (!x0 || !dx0 || !dtraj) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    const size_t G = ctx->gstate, T = (size_t)(ctx->m.nsteps + 1) * G;
+    TzBufs b(ctx);
+    const double* xin = tz_in(ctx, b, x0, G, device_ptrs);
+    const double* dxin = tz_in(ctx, b, dx0, G, device_ptrs);
+    double* dout = device_ptrs ? dtraj : b.get(T);
+    double* w = b.get(6 * G);
+    double *xa = w, *xb = w + G, *s1 = w + 2 * G, *s2 = w + 3 * G, *d1 = w + 4 * G, *d2 = w + 5 * G;
+    CK(cudaMemcpyAsync(xa, xin, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(cudaMemcpyAsync(dout, dxin, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    for (int n = 0; n < ctx->m.nsteps; ++n) {
+      const double* dx = dout + (size_t)n * G;
+      double* dn = dout + (size_t)(n + 1) * G;
+      KL(launch_tz_stage(t, xa, xa, s1, 0.0, 1.0, ctx->st));
+      KL(launch_tz_tl_stage(t, xa, dx, dx, d1, 0.0, 1.0, ctx->st));
+      KL(launch_tz_stage(t, xa, s1, s2, 0.75, 0.25, ctx->st));
+      KL(launch_tz_tl_stage(t, s1, dx, d1, d2, 0.75, 0.25, ctx->st));
+      KL(launch_tz_stage(t, xa, s2, xb, 1.0 / 3.0, 2.0 / 3.0, ctx->st));
+      KL(launch_tz_tl_stage(t, s2, dx, d2, dn, 1.0 / 3.0, 2.0 / 3.0, ctx->st));
+      std::swap(xa, xb);
+    }
+    if (!device_ptrs) d2h(ctx, dtraj, dout, T * sizeof(double));
+    sync(ctx);
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_tz_adjoint(dd4dv_ctx* ctx, int p, int q, double alpha, const double* x0, const double* ytraj,
+                              double* dx0, int device_ptrs) {
+  return guard(ctx, [&] {
+    const TzArgs t = tz_args(ctx, p, q, alpha);
+    if (!x0 || !ytraj || !dx0) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    const size_t G = ctx->gstate, T = (size_t)(ctx->m.nsteps + 1) * G;
+    const int N = ctx->m.nsteps;
+    TzBufs b(ctx);
+    const double* xin = tz_in(ctx, b, x0, G, device_ptrs);
+    const double* y = tz_in(ctx, b, ytraj, T, device_ptrs);
+    double* traj = b.get(T);
+    double* w = b.get(6 * G);
+    double *s1 = w, *s2 = w + G, *lam = w + 2 * G, *mu2 = w + 3 * G, *mu1 = w + 4 * G, *g3 = w + 5 * G;
+    tz_run(ctx, t, xin, traj, s1, s2);
+    CK(cudaMemcpyAsync(lam, y + (size_t)N * G, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    for (int n = N - 1; n >= 0; --n) {
+      tz_adjoint_step(ctx, t, traj + (size_t)n * G, s1, s2, lam, mu2, mu1, g3);
+      KL(launch_tz_lincomb(lam, lam, y + (size_t)n * G, nullptr, 1.0, 1.0, 0.0, (long long)G, ctx->st));
+    }
+    if (device_ptrs) CK(cudaMemcpyAsync(dx0, lam, G * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    else d2h(ctx, dx0, lam, G * sizeof(double));
+    sync(ctx);
+    return DD4DV_OK;
+  });
+}
+
+dd4dv_status dd4dv_tz_eval(dd4dv_ctx* ctx, int p, int q, double alpha, const double* w_in, double* J_out,
+                           double* grad_out, int device_ptrs) {
+  return guard(ctx, [&] {
+    const TzArgs t = tz_args(ctx, p, q, alpha);
+    if (!w_in || !J_out) fail(ctx, DD4DV_EINVAL, "NULL argument");
+    if (!ctx->has_bg || !ctx->has_berr) fail(ctx, DD4DV_ESTATE, "set_background and set_background_error first");
+    if (ctx->corr_len > 0.0) fail(ctx, DD4DV_EINVAL, "dd4dv_tz_eval takes a diagonal B (corr_len_cells = 0)");
+    const size_t G = ctx->gstate, T = (size_t)(ctx->m.nsteps + 1) * G;
+    const int N = ctx->m.nsteps;
+    const long long plane = (long long)ctx->m.nlat * ctx->m.nlon;
+    TzBufs b(ctx);
+    const double* w = tz_in(ctx, b, w_in, G, device_ptrs);
+    double* traj = b.get(T);
+    double* work = b.get(7 * G + 2);
+    double *s1 = work, *s2 = work + G, *lam = work + 2 * G, *mu2 = work + 3 * G, *mu1 = work + 4 * G,
+           *g3 = work + 5 * G, *x0 = work + 6 * G, *Jd = work + 7 * G, *Jo = work + 7 * G + 1;
+    KL(launch_tz_scale_add(x0, ctx->xb0, w, ctx->sigma_d, plane, ctx->st));
+    tz_run(ctx, t, x0, traj, s1, s2);
+    // observations sorted by level, with the offsets of each level
+    const size_t nob = ctx->has_obs ? ctx->ob_level.size() : 0;
+    std::vector<size_t> ord(nob);
+    for (size_t k = 0; k < nob; ++k) ord[k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t c) { return ctx->ob_level[a] < ctx->ob_level[c]; });
+    std::vector<int> lv(nob), vr(nob);
+    std::vector<double> fi(nob), fj(nob), yv(nob), so(nob);
+    std::vector<long long> off(N + 2, 0);
+    for (size_t k = 0; k < nob; ++k) {
+      const size_t o = ord[k];
+      lv[k] = ctx->ob_level[o];
+      vr[k] = ctx->ob_var[o];
+      fi[k] = ctx->ob_fi[o];
+      fj[k] = ctx->ob_fj[o];
+      yv[k] = ctx->ob_val[o];
+      so[k] = ctx->ob_so[o];
+      off[lv[k] + 1] += 1;
+    }
+    for (int n = 0; n <= N; ++n) off[n + 1] += off[n];
+    const double* force = nullptr;
+    const int* lvd = nullptr;
+    const int* vrd = nullptr;
+    const double *fid = nullptr, *fjd = nullptr;
+    if (nob) {
+      double* dbl = b.get(5 * nob);
+      int* ints = reinterpret_cast<int*>(b.get(nob));   // 2 * nob ints
+      h2d(ctx, ints, lv.data(), nob * sizeof(int));
+      h2d(ctx, ints + nob, vr.data(), nob * sizeof(int));
+      h2d(ctx, dbl, fi.data(), nob * sizeof(double));
+      h2d(ctx, dbl + nob, fj.data(), nob * sizeof(double));
+      h2d(ctx, dbl + 2 * nob, yv.data(), nob * sizeof(double));
+      h2d(ctx, dbl + 3 * nob, so.data(), nob * sizeof(double));
+      lvd = ints;
+      vrd = ints + nob;
+      fid = dbl;
+      fjd = dbl + nob;
+      force = dbl + 4 * nob;
+      KL(launch_tz_obs_misfit(traj, (long long)nob, lvd, vrd, fid, fjd, dbl + 2 * nob, dbl + 3 * nob, ctx->m.nlon,
+                              ctx->m.nlat, 1.0, dbl + 4 * nob, Jo, ctx->st));
+    }
+    KL(launch_tz_finish_J(w, (long long)G, nob ? Jo : nullptr, Jd, ctx->st));
+    if (grad_out) {
+      CK(cudaMemsetAsync(lam, 0, G * sizeof(double), ctx->st));
+      if (nob) KL(launch_tz_obs_scatter(off[N], off[N + 1], vrd, fid, fjd, force, ctx->m.nlon, ctx->m.nlat, lam, ctx->st));
+      for (int n = N - 1; n >= 0; --n) {
+        tz_adjoint_step(ctx, t, traj + (size_t)n * G, s1, s2, lam, mu2, mu1, g3);
+        if (nob) KL(launch_tz_obs_scatter(off[n], off[n + 1], vrd, fid, fjd, force, ctx->m.nlon, ctx->m.nlat, lam,
+                                          ctx->st));
+      }
+      double* gd = device_ptrs ? grad_out : s1;
+      KL(launch_tz_scale_add(gd, w, lam, ctx->sigma_d, plane, ctx->st));
+      if (!device_ptrs) d2h(ctx, grad_out, gd, G * sizeof(double));
+    }
+    if (device_ptrs) CK(cudaMemcpyAsync(J_out, Jd, sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+    else d2h(ctx, J_out, Jd, sizeof(double));
+    sync(ctx);
+    return DD4DV_OK;
+  });
+}
+
+}  // extern "C"
+
 // Captures the work enqueued by f on the context stream into an executable
 // graph; *nk receives the number of this library's kernels in it.
 template <typename F>

@@ -246,4 +246,27 @@ cudaError_t launch_max_abs_diff(const double* a, const double* b, long long n, d
                                 cudaStream_t st);
 cudaError_t launch_finite_check(const double* a, long long n, int* flag, cudaStream_t st);
 
+// ---- Turkel-Zwas scheme on the whole sphere (tz.cu) ----
+struct TzArgs {
+  const RowConst* rows;       // [nlat]
+  int nlon, nlat, p, q;
+  double alpha, slon, slat, g, dt;
+};
+cudaError_t launch_tz_stage(const TzArgs& t, const double* X, const double* Y, double* out, double cx, double cy,
+                            cudaStream_t st);
+cudaError_t launch_tz_tl_stage(const TzArgs& t, const double* Y, const double* dX, const double* dY, double* dout,
+                               double cx, double cy, cudaStream_t st);
+cudaError_t launch_tz_adj_scatter(const TzArgs& t, const double* Y, const double* M, double* G, double scale,
+                                  cudaStream_t st);
+cudaError_t launch_tz_lincomb(double* out, const double* a, const double* b, const double* c, double ca, double cb,
+                              double cc, long long n, cudaStream_t st);
+cudaError_t launch_tz_scale_add(double* out, const double* a, const double* b, const double* sigma, long long plane,
+                                cudaStream_t st);
+cudaError_t launch_tz_obs_misfit(const double* traj, long long n, const int* level, const int* var, const double* fi,
+                                 const double* fj, const double* y, const double* so, int nlon, int nlat, double lam,
+                                 double* force, double* Jo, cudaStream_t st);
+cudaError_t launch_tz_obs_scatter(long long k0, long long k1, const int* var, const double* fi, const double* fj,
+                                  const double* force, int nlon, int nlat, double* lam, cudaStream_t st);
+cudaError_t launch_tz_finish_J(const double* w, long long n, const double* Jo, double* J, cudaStream_t st);
+
 }  // namespace dd4dv
