@@ -10,7 +10,8 @@ from the separate ``workloads`` module, which holds no method arithmetic.
 Plain, slow, FP64 PyTorch-CPU code written from the paper:
   swe.py            shallow-water model and SSP-RK3 step (Sec. 7)
   tz.py             the Turkel-Zwas stencil of Sec. 7 (p, q strides, alpha
-                    averaging), global domain only; no GPU counterpart yet
+                    averaging) and the global 4D-Var functional on it,
+                    global domain only
   decomposition.py  space-time decomposition, restriction weights (Sec. 3.1-3.2)
   bcov.py           B = V V^T, diagonal or recursive filter (Sec. 4, Eq. EqV)
   local.py          local functional J_s, gradient, TLM (Sec. 3.3, Alg. 6)

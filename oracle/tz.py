@@ -2,8 +2,9 @@
 model (Sec. 7, the scheme the paper names for its numerical model).
 
 TEST INFRASTRUCTURE ONLY.  Plain, slow FP64 PyTorch-CPU code; only tests may
-use it.  No GPU kernel implements this scheme yet (the hot path uses the
-centred p = q = 1, alpha = 0 member in its flux form, oracle/swe.py).
+use it.  It is the parity target of the library's Turkel-Zwas runs on the
+whole grid; the decomposed sweeps use the centred p = q = 1, alpha = 0 member
+in its flux form (oracle/swe.py).
 
 What the scheme computes, on the lon-lat grid of cell centres of oracle/swe.py
 (periodic in longitude, walls at the latitude edges): the Coriolis and
