@@ -387,12 +387,15 @@ def run_reference(args):
     return 0
 
 
-# Launch shapes for the large workload, as the autotuner picks them on its
+# Launch shapes for the large workload, the fastest of a shape search on its
 # boxes (forward cluster, forward threads, adjoint cluster, adjoint threads,
 # stored stage states, forward variant, adjoint variant; variant 1 = stripe
-# sweep, 0 = deep-halo FP32 sweep): the benchmark forces them instead of
-# spending ~80 evaluations of 0.7-3.5 s on tuning.
-DEFAULT_SHAPES = {("large", 0): "16,512,16,512,0", ("large", 1): "16,384,16,640,1,1,0"}
+# sweep, 0 = deep-halo FP32 sweep where it applies, 2 = four-buffer stripe
+# adjoint): the benchmark forces them instead of spending ~80 evaluations of
+# 0.4-2.6 s on tuning.  9-CTA clusters: a GPC of 18 or 20 SMs holds two of
+# them at one CTA per SM (135 of 152 SMs busy), but only one 16-CTA cluster
+# (112 SMs).
+DEFAULT_SHAPES = {("large", 0): "9,512,9,512,0,1,2", ("large", 1): "9,512,9,512,1,0,2"}
 
 
 def roofline_of(ctx, prec, reps=3):
@@ -615,11 +618,13 @@ def scaleup_workloads(qp, nsteps=16):
     return base, base.replace(name=f"scaleup_qp{qp}_undecomposed", P1=1, P2=1), lon_cuts, lat_cuts
 
 
-def scaleup_rows(torch, steps, warmup, autotune=True):
+def scaleup_rows(torch, steps, warmup, autotune=True, precision=0):
     """Measured scale-up of one outer iteration (Sec. 6-7, Eq. measurscale,
     Table 3), read as Sc_1,QP = T(undecomposed problem of size 3 n_loc^2 QP)
     / T(the same problem in QP subdomains), both on this GPU (all subdomains
-    of one problem in one launch per sweep)."""
+    of one problem in one launch per sweep), both in the given precision
+    (0 FP64, 1 FP32 state).  In FP64 the QP = 64 undecomposed box (192 x 200
+    points) fits no cluster's shared memory; in FP32 it does."""
     import paper_2205_06649_gb300 as dd
     rows = []
     for qp in sorted(SCALEUP_LAYOUT):
@@ -632,7 +637,7 @@ def scaleup_rows(torch, steps, warmup, autotune=True):
                 inp["lon_cuts"] = np.asarray(lon_cuts)
                 inp["lat_cuts"] = np.asarray(lat_cuts)
             try:
-                ctx, inp, truth, obs = build_problem(wl, 0, stream.cuda_stream, inputs=inp,
+                ctx, inp, truth, obs = build_problem(wl, precision, stream.cuda_stream, inputs=inp,
                                                      shape="" if autotune else "model")
             except dd.DD4DVError as e:   # one box larger than a 16-CTA cluster's shared memory
                 times[wl.P1 * wl.P2] = (None, str(e), 0)
@@ -651,15 +656,17 @@ def scaleup_rows(torch, steps, warmup, autotune=True):
         rows.append({"QP": qp, "problem_size": 3 * 32 * 32 * qp, "grid": [wl_dd.nlon, wl_dd.nlat],
                      "ms_undecomposed": t1, "ms_decomposed": tq, "scale_up": sc,
                      "shape_undecomposed": times[1][1], "shape_decomposed": times[qp][1]})
-        log(f"QP={qp}: T1 {t1} ms, TQP {tq} ms, Sc {sc}")
+        log(f"QP={qp} ({'f32' if precision else 'f64'}): T1 {t1} ms, TQP {tq} ms, Sc {sc}")
     return rows
 
 
 def scaleup_mode(args, torch):
-    rows = scaleup_rows(torch, args.steps, args.warmup)
+    prec = 0 if args.precision == "f64" else 1
+    rows = scaleup_rows(torch, args.steps, args.warmup, precision=prec)
     print(json.dumps({"metric": "measured scale-up Sc_1,QP of one DD-4DVar outer iteration (n_loc = 32)",
                       "unit": "ratio", "higher_is_better": True, "n_gpus": 1, "steps": args.steps,
-                      "warmup": args.warmup, "dtype": "f64", "data": "synthetic", "rows": rows}), flush=True)
+                      "warmup": args.warmup, "dtype": "f32 state" if prec else "f64", "data": "synthetic",
+                      "rows": rows}), flush=True)
     return 0
 
 
@@ -901,7 +908,8 @@ def main():
         extras["scaleup_table3"] = {
             "metric": "measured scale-up Sc_1,QP of one DD-4DVar outer iteration (n_loc = 32, Table 3)",
             "steps": min(args.steps, 5), "warmup": 2, "launch_shapes": "model-based (no autotuning)",
-            "rows": scaleup_rows(torch, min(args.steps, 5), 2, autotune=False)}
+            "rows": scaleup_rows(torch, min(args.steps, 5), 2, autotune=False),
+            "rows_fp32_state": scaleup_rows(torch, min(args.steps, 5), 2, autotune=False, precision=1)}
     if rank == 0:
         line = headline_line(args, wl, prec, leg, pts_all / (t_max / 1e3), t_max, world, extras,
                              cpu.result() if cpu else None)

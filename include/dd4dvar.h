@@ -417,15 +417,23 @@ dd4dv_status dd4dv_checkpoint_interval(const dd4dv_ctx* ctx, int* k, double* eva
  * run where every CTA stripe has at least 3 rows, a thread holds at most 4
  * own points and (adjoint) the stage states are stored (ckpt_k = 0, no
  * Gauss-Newton or external forcing).  Both give the same values bit for bit.
- * forward, adjoint: the variant of each sweep, 0 = deep-halo sweep wherever
- * it applies (default), 1 = stripe sweep only.  EINVAL for other values.  The
- * autotuner (cluster = -1 in dd4dv_decomp) times both forms wherever the
- * deep-halo form applies and keeps the faster one for each sweep;
- * dd4dv_sweep_kernels reports which run. */
+ * The stripe adjoint also has a four-buffer form (any precision): mu2 (the
+ * adjoint of the second RK3 stage) takes the buffer of x(n) and x(n) is read
+ * again from HBM for the last phase of the step, so a CTA needs four state
+ * buffers in shared memory instead of five; same values bit for bit, one more
+ * state read per step.  It lets larger stripes (fewer CTAs per subdomain) or
+ * more CTAs per SM fit.
+ * forward: 0 = deep-halo sweep wherever it applies (default), 1 = stripe
+ * sweep only.  adjoint: 0 and 1 as for the forward (the stripe adjoint takes
+ * its four-buffer form where five buffers do not fit), 2 = the four-buffer
+ * stripe adjoint.  EINVAL for other values.  The autotuner (cluster = -1 in
+ * dd4dv_decomp) times every form that applies and keeps the fastest one for
+ * each sweep; dd4dv_sweep_kernels reports which run. */
 dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int forward, int adjoint);
 
 /* Which kernels the current launch shapes run: kinds[0] forward, kinds[1]
- * adjoint; 1 = stripe sweep, 2 = deep-halo sweep. */
+ * adjoint; 1 = stripe sweep, 2 = deep-halo sweep, 3 = four-buffer stripe
+ * adjoint. */
 dd4dv_status dd4dv_sweep_kernels(const dd4dv_ctx* ctx, int* kinds);
 
 /* The cluster size (CTAs per subdomain) the sweeps use. */

@@ -22,6 +22,9 @@ __all__ = ["Context", "DD4DVError", "lib", "solver_defaults"]
 
 lib = _abi.load()
 
+# dd4dv_sweep_kernels codes
+KERNEL_NAMES = {1: "stripe", 2: "deep-halo", 3: "stripe-4buf"}
+
 
 class DD4DVError(RuntimeError):
     def __init__(self, status: int, msg: str):
@@ -178,12 +181,15 @@ class Context:
     # ---- queries ----
     def set_sweep_variant(self, forward: int, adjoint: int = None):
         """Per sweep: 0 = deep-halo FP32 sweep wherever it applies (default),
-        1 = stripe sweep only (adjoint defaults to the forward's value)."""
+        1 = stripe sweep only; the adjoint also takes 2 = the four-buffer
+        stripe adjoint (x(n) reloaded).  adjoint defaults to the forward's
+        value."""
         adjoint = forward if adjoint is None else adjoint
         self._check(lib.dd4dv_set_sweep_variant(self._h, int(forward), int(adjoint)))
 
     def sweep_kernels(self) -> dict:
-        """Kernels the current shapes run: 1 = stripe sweep, 2 = deep-halo sweep."""
+        """Kernels the current shapes run: 1 = stripe sweep, 2 = deep-halo
+        sweep, 3 = four-buffer stripe adjoint."""
         k = np.zeros(2, dtype=np.int32)
         self._check(lib.dd4dv_sweep_kernels(self._h, C.c_void_p(k.ctypes.data)))
         return {"forward": int(k[0]), "adjoint": int(k[1])}
@@ -204,8 +210,8 @@ class Context:
         kinds = self.sweep_kernels()
         return {"forward": [int(sh[0]), int(sh[1])], "adjoint": [int(sh[2]), int(sh[3])],
                 "stored_stages": bool(sh[4]), "eval_ms": ms.value, "ckpt_k": k.value,
-                "kernels": {"forward": "deep-halo" if kinds["forward"] == 2 else "stripe",
-                            "adjoint": "deep-halo" if kinds["adjoint"] == 2 else "stripe"}}
+                "kernels": {"forward": KERNEL_NAMES.get(kinds["forward"], "none"),
+                            "adjoint": KERNEL_NAMES.get(kinds["adjoint"], "none")}}
 
     def set_sweep_config(self, forward, adjoint, stored_stages: bool):
         """forward, adjoint: (cluster size, threads per CTA)."""

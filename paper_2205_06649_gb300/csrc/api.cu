@@ -386,7 +386,7 @@ void tlm_shape(dd4dv_ctx* ctx, int* cl, int* R) {
   for (int c = ctx->cl; c <= std::min(16, ctx->min_ny); ++c) {
     const int r = (ctx->max_ny + c - 1) / c;
     const size_t need = ctx->m.precision == 1 ? smem_tlm<float>(r, ctx->W) : smem_tlm<double>(r, ctx->W);
-    if (need <= 232448 && (c <= 8 || c == 16)) {
+    if (need <= 232448) {
       *cl = c;
       *R = r;
       return;
@@ -599,9 +599,10 @@ void free_dec_buffer(dd4dv_ctx* ctx, void*& p) {
 // for stored and for recomputed stage states, it times the forward and the
 // adjoint sweep separately (CUDA events around each launch, evaluation at
 // w = 0) and keeps the fastest shape of each sweep and the faster stage mode.
-// Thread counts include ones that divide a CTA's points evenly.  The search
-// stops early when it has used a time budget of 40 evaluations (at least
-// 2 s).  Results do not depend on the shapes except for the order of the
+// Thread counts include ones that divide a CTA's points evenly; FP32 sweeps
+// are timed in their stripe and deep-halo forms, the adjoint also in its
+// four-buffer form.  The search stops early when it has used a time budget of
+// 80 evaluations (at least 2 s).  Results do not depend on the shapes except for the order of the
 // per-CTA partial sums of J.
 void autotune(dd4dv_ctx* ctx) {
   const bool f32 = ctx->m.precision == 1;
@@ -647,9 +648,14 @@ void autotune(dd4dv_ctx* ctx) {
     return true;
   };
   std::vector<int> cls;
-  for (int c : {1, 2, 3, 4, 5, 6, 7, 8, 16})
-    if (c <= ctx->min_ny && (smem_a((ctx->max_ny + c - 1) / c) <= (size_t)cap || adj_kind_at(ctx, c, 512)))
-      cls.push_back(c);
+  {
+    const int va = ctx->variant_a;
+    ctx->variant_a = 2;   // the smallest footprint
+    for (int c : {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 16})
+      if (c <= ctx->min_ny && (smem_a((ctx->max_ny + c - 1) / c) <= (size_t)cap || adj_kind_at(ctx, c, 512)))
+        cls.push_back(c);
+    ctx->variant_a = va;
+  }
   // 640 and 576 threads only reach the deep-halo FP32 sweeps
   const int nts[] = {640, 576, 512, 448, 384, 320, 256, 192};
   // reference time of the starting shape sets the budget
@@ -668,7 +674,7 @@ void autotune(dd4dv_ctx* ctx) {
     ctx->use_stg = use;
     for (int c : cls)
       for (int nt : nts)
-        for (int var : {0, 1}) {
+        for (int var : {0, 1, 2}) {
           if (spent > budget_ms) break;
           if (var < var0) continue;
           ctx->variant_f = ctx->variant_a = var;
@@ -679,13 +685,21 @@ void autotune(dd4dv_ctx* ctx) {
             ctx->variant_f = ctx->variant_a = 1;
             if (!deep) continue;
           }
+          // the four-buffer adjoint (forward as for variant 1), where the
+          // other variants did not already fall back to it
+          if (var == 2) {
+            ctx->variant_f = ctx->variant_a = 1;
+            if (adj_kind_at(ctx, c, nt) == 3) continue;
+            ctx->variant_a = 2;
+            if (!adj_kind_at(ctx, c, nt)) continue;
+          }
           float tf = 0, ta = 0, tf2 = 0, ta2 = 0;
           if (!run(c, nt, &tf, &ta)) continue;
           if (!run(c, nt, &tf2, &ta2)) continue;
           spent += tf + ta + tf2 + ta2;
           tf = std::min(tf, tf2);
           ta = std::min(ta, ta2);
-          if (tf < best_f[use].t) best_f[use] = {tf, c, ctx->nt_f, var};
+          if (var != 2 && tf < best_f[use].t) best_f[use] = {tf, c, ctx->nt_f, var};
           if (ta < best_a[use].t) best_a[use] = {ta, c, nt, var};
         }
   }
@@ -1003,43 +1017,50 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
   const size_t smem_cap = 232448;
   const bool f32 = ctx->m.precision == 1;
   ctx->W = max_nx + 2;
-  auto smem_need = [&](int R) {
-    return f32 ? smem_adjoint<float>(R, ctx->W) : smem_adjoint<double>(R, ctx->W);
+  auto smem_need_min = [&](int R) {   // the four-buffer stripe adjoint
+    return f32 ? smem_adjoint_rl<float>(R, ctx->W) : smem_adjoint_rl<double>(R, ctx->W);
   };
   int cl = d.cluster;
   ctx->nthreads = 256;
   if (cl > 0) {
     if (cl > 16 || cl > min_ny) fail(ctx, DD4DV_EINVAL, "cluster size %d must be <= 16 and <= smallest box height %d", cl, min_ny);
     ctx->R = (max_ny + cl - 1) / cl;
-    if (smem_need(ctx->R) > smem_cap) fail(ctx, DD4DV_EINVAL, "cluster size %d needs too much shared memory", cl);
+    if (smem_need_min(ctx->R) > smem_cap) fail(ctx, DD4DV_EINVAL, "cluster size %d needs too much shared memory", cl);
   } else {
-    // Estimated time ~ waves of CTAs x rows per CTA: pick the smallest
-    // cluster that minimises it (fewer CTAs per subdomain = fewer barriers).
+    // Launch-shape model.  A cluster runs inside one GPC, so how many
+    // subdomains run at once depends on how the GPCs' SMs divide by the
+    // cluster size (asked of the runtime with the adjoint kernel's real
+    // footprint), not only on CTAs per SM.  Estimated time = waves of
+    // clusters x rows per CTA x CTAs sharing an SM (at least 1); the smallest
+    // cluster within 3 % of the best wins (fewer CTAs, fewer barriers).
+    // Threads: about 4 own points each, 128..512.
     int nsm = 152;
     int dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     double best = 1e300;
-    int best_cl = -1;
-    for (int c : {1, 2, 4, 8, 16}) {
+    int best_cl = -1, best_nt = 256;
+    for (int c = 1; c <= 16; ++c) {
       if (c > min_ny) break;
       const int R = (max_ny + c - 1) / c;
-      const size_t sm = smem_need(R);
-      if (sm > smem_cap) continue;
-      int per_sm = f32 ? occupancy_adjoint<float>(R, ctx->W, 256) : occupancy_adjoint<double>(R, ctx->W, 256);
-      if (per_sm < 1) continue;
-      const long long ctas = (long long)n_sub * c;
-      const double waves = std::ceil((double)ctas / ((double)nsm * per_sm));
-      const double cost = waves * R * (double)per_sm;
-      if (cost < best * 0.97) { best = cost; best_cl = c; }
+      if (smem_need_min(R) > smem_cap) continue;
+      const int nt = std::min(512, std::max(128, 32 * ((R * max_nx + 127) / 128)));
+      const int act = f32 ? active_clusters_adjoint<float>(R, ctx->W, c, nt)
+                          : active_clusters_adjoint<double>(R, ctx->W, c, nt);
+      if (act < 1) continue;
+      const double waves = std::ceil((double)n_sub / act);
+      const double share = std::max(1.0, (double)std::min(act, n_sub) * c / nsm);
+      const double cost = waves * R * share;
+      if (cost < best * 0.97) { best = cost; best_cl = c; best_nt = nt; }
     }
     if (best_cl < 0) fail(ctx, DD4DV_EINVAL, "subdomain boxes too large for the shared-memory sweep (max %dx%d)", max_nx, max_ny);
     cl = best_cl;
     ctx->R = (max_ny + cl - 1) / cl;
+    ctx->nthreads = best_nt;
   }
   ctx->cl = cl;
   ctx->cl_f = cl;
   ctx->R_f = ctx->R;
-  ctx->nt_f = ctx->nthreads;
+  ctx->nt_f = std::min(ctx->nthreads, f32 ? max_threads_forward<float>() : max_threads_forward<double>());
 
   // device tables and buffers
   ctx->free_dec();
@@ -2492,8 +2513,9 @@ dd4dv_status dd4dv_checkpoint_interval(const dd4dv_ctx* cctx, int* k, double* ev
 
 dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int forward, int adjoint) {
   return guard(ctx, [&] {
-    for (int v : {forward, adjoint})
-      if (v != 0 && v != 1) fail(ctx, DD4DV_EINVAL, "variants must be 0 (automatic) or 1 (stripe sweeps)");
+    if ((forward != 0 && forward != 1) || adjoint < 0 || adjoint > 2)
+      fail(ctx, DD4DV_EINVAL,
+           "variants: 0 (automatic) or 1 (stripe sweeps); the adjoint also 2 (four-buffer stripe adjoint)");
     ctx->variant_f = forward;
     ctx->variant_a = adjoint;
     ctx->drop_graphs();

@@ -104,7 +104,8 @@ struct SweepArgs {
                               // buffer of prefetched overlap targets (only if it still fits)
   int min_ny;                 // smallest box height of the decomposition
   int variant;                // 0: deep-halo FP32 sweeps where they apply, else the stripe
-                              // sweeps; 1: stripe sweeps only
+                              // sweeps; 1: stripe sweeps only; 2 (adjoint only): the stripe
+                              // adjoint with four state buffers, x(n) reloaded from HBM
 };
 
 // Largest CTA of the forward sweep: 384 threads on the FP32 path, whose
@@ -116,7 +117,7 @@ template <typename T> constexpr int max_threads_forward() { return sizeof(T) == 
 // Which kernel a sweep launch with cl CTAs per subdomain and nthreads threads
 // per CTA would run: 0 = none (shape not launchable), 1 = the stripe sweep
 // (one halo row per stage), 2 = the deep-halo FP32 sweep (three halo rows, one
-// exchange per step).
+// exchange per step), 3 = the stripe adjoint with four state buffers.
 template <typename T> int forward_kind(const SweepArgs<T>& a, int cl, int nthreads);
 template <typename T> int adjoint_kind(const SweepArgs<T>& a, int cl, int nthreads);
 template <typename T> cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);
@@ -124,9 +125,10 @@ template <typename T> cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, 
 template <typename T> cudaError_t launch_tlm(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);
 template <typename T> size_t smem_forward(int R, int W);
 template <typename T> size_t smem_adjoint(int R, int W);
+template <typename T> size_t smem_adjoint_rl(int R, int W);
 template <typename T> size_t smem_tlm(int R, int W);
-// resident CTAs per SM of the adjoint sweep (the largest of the three)
-template <typename T> int occupancy_adjoint(int R, int W, int nthreads);
+// resident clusters of the stripe adjoint sweep at cl CTAs per cluster
+template <typename T> int active_clusters_adjoint(int R, int W, int cl, int nthreads);
 
 // ---- auxiliary kernels (aux.cu) ----
 struct RFArgs {

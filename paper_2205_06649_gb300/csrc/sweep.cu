@@ -452,11 +452,11 @@ __device__ void load_state(const SweepArgs<T>& a, const Geo<T>& g, T* X, const T
   __syncthreads();
 }
 
-// Load three stored states at once (one pass, one barrier pair) so that
-// their global-load latencies overlap.  Same rules as load_state.
-template <typename T>
-__device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X, const T* const* src,
-                             const int* nA, const int* nB, const T* wA, const T* wB) {
+// Load NS stored states at once (one pass, one barrier pair) so that their
+// global-load latencies overlap.  Same rules as load_state.
+template <typename T, int NS>
+__device__ void load_states(const SweepArgs<T>& a, const Geo<T>& g, T* const* X, const T* const* src,
+                            const int* nA, const int* nB, const T* wA, const T* wB) {
   const int nx = g.nx;
   const int r_lo = (g.rank > 0) ? -1 : 0;
   const int r_hi = (g.rank < g.CL - 1) ? g.Rn + 1 : g.Rn;
@@ -468,19 +468,19 @@ __device__ void load_states3(const SweepArgs<T>& a, const Geo<T>& g, T* const* X
     const size_t go = (size_t)(g.R0 + rr) * g.d.nxp + k;
     const int o = pidx(g, rr, k);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
+    for (int b = 0; b < NS; ++b) {
       const T* s = src[b] + go;
       st3(X[b], o, g.P, s[0], s[pl], s[2 * pl]);
     }
   }
   if constexpr (sizeof(T) == 4) cp_async_wait_all();
   __syncthreads();
-  GhostSrc<T> gs[3];
+  GhostSrc<T> gs[NS];
 #pragma unroll
-  for (int b = 0; b < 3; ++b) gs[b] = ghost_src(g, nA[b], nB[b], wA[b], wB[b]);
+  for (int b = 0; b < NS; ++b) gs[b] = ghost_src(g, nA[b], nB[b], wA[b], wB[b]);
   for (int j = threadIdx.x; j < 2 * nx + 2 * g.Rn; j += blockDim.x) {
 #pragma unroll
-    for (int b = 0; b < 3; ++b) state_edges(a, g, X[b], j, gs[b]);
+    for (int b = 0; b < NS; ++b) state_edges(a, g, X[b], j, gs[b]);
   }
   __syncthreads();
 }
@@ -1310,7 +1310,19 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
 
 // Adjoint sweep: lambda(b) = forcing(b); lambda(n) = M_n^T lambda(n+1) + forcing(n),
 // the RK3 stages recomputed from the stored x(n).  Writes lambda(a) to lam_a.
-template <typename T>
+//
+// Buffer plans.  RL = false keeps x(n), x1, x2, lambda' and mu2 in five state
+// buffers.  RL = true needs four: mu2 takes x(n)'s buffer once both stage
+// states are formed, and x(n) is read again from HBM into x1's buffer after
+// mu1 (x1's last use), for the lambda(n) phase and the overlap forcing; with
+// stored stage states only x1 and x2 are loaded at the start of the step.
+// Same arithmetic, same results, one more state read per step; the smaller
+// footprint lets larger stripes or more CTAs per SM fit.  Writing mu2 into
+// x(n)'s buffer is safe under the pushed exchange: a neighbour pushes mu2 rows
+// into this CTA's halo only after this CTA arrived at the barrier of the
+// phase before (its edge rows, the only readers of halo rows, are done), and
+// the RL = true stored-stage step loads nothing into that buffer.
+template <typename T, bool RL>
 __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
@@ -1319,12 +1331,13 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   T* buf[5];
   RowSmem<T> rs;
   double* scratch;
-  carve(a, g, 5, buf, rs, &scratch, true);
+  carve(a, g, RL ? 4 : 5, buf, rs, &scratch, true);
   T* X = buf[0];
   T* X1 = buf[1];
   T* X2 = buf[2];   // also lambda_x1
   T* Lp = buf[3];
-  T* L2 = buf[4];
+  T* L2 = RL ? buf[0] : buf[4];
+  T* Xr = RL ? buf[1] : buf[0];   // x(n) in the lambda(n) phase
   load_rows(a, g, rs);
   ghost_prefetch(a, g, g.a + g.L);
   if (g.L > 0) ghost_prefetch(a, g, g.a + g.L - 1);
@@ -1374,7 +1387,15 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
   }
   for (int l = l1 - 1; l >= l0; --l) {
     const int n = g.a + l;
-    if (a.stg && !K) {   // x(n) and the stage states stored by the forward sweep
+    if (a.stg && !K && RL) {   // the stage states stored by the forward sweep
+      T* bufs[2] = {X1, X2};
+      const T* srcs[2] = {stage_ptr(a, g, l, 0), stage_ptr(a, g, l, 1)};
+      const int nA[2] = {n + 1, n};
+      const int nB[2] = {n + 1, n + 1};
+      const T wA[2] = {(T)1, (T)0.5};
+      const T wB[2] = {(T)0, (T)0.5};
+      load_states<T, 2>(a, g, bufs, srcs, nA, nB, wA, wB);
+    } else if (a.stg && !K) {   // x(n) and the stage states stored by the forward sweep
       T* bufs[3] = {X, X1, X2};
       const T* srcs[3] = {a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp,
                           stage_ptr(a, g, l, 0), stage_ptr(a, g, l, 1)};
@@ -1382,7 +1403,7 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       const int nB[3] = {n, n + 1, n + 1};
       const T wA[3] = {(T)1, (T)1, (T)0.5};
       const T wB[3] = {(T)0, (T)0, (T)0.5};
-      load_states3(a, g, bufs, srcs, nA, nB, wA, wB);
+      load_states<T, 3>(a, g, bufs, srcs, nA, nB, wA, wB);
     } else {       // recompute the stage states from x(n)
       load_state(a, g, X, level_src(l), n, n, (T)1, (T)0);
       stage_push<T, DEV>(cl, a, g, rs, X1, X, X, (T)0, (T)1, n + 1, n + 1, (T)1, (T)0);
@@ -1433,6 +1454,8 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       st3(L1, o, P, v0, v1, v2);
         },
         0);   // the prefetched targets land before the next phase reads them
+    // x(n) again, into x1's buffer (x1 is dead after mu1)
+    if constexpr (RL) load_state(a, g, Xr, level_src(l), n, n, (T)1, (T)0);
     // lambda(n)
     const auto lam_n = [&](int rr, int k, T& v0, T& v1, T& v2) {
       const int o = pidx(g, rr, k), ri = rr + 1;
@@ -1440,7 +1463,7 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
       T rc[8];
       load_rec8(rs.bw + 8 * ri, rc);
       Pt5<T> z, m;
-      load5(X, o, P, CS, g.RS, z);
+      load5(Xr, o, P, CS, g.RS, z);
       load5(L1, o, P, CS, g.RS, m);
       T ph, pu, pv, qh, qu, qv;
       ld3(Lp, o, P, ph, pu, pv);
@@ -1461,7 +1484,7 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
         lam_n(rr, k, v0, v1, v2);
         if (ovl) {
           const int c = overlap_count(g, l, g.R0 + rr, k);
-          if (c) overlap_force(a, g, X, tg, rr, k, c, v0, v1, v2);
+          if (c) overlap_force(a, g, Xr, tg, rr, k, c, v0, v1, v2);
         }
         st3(Lp, pidx(g, rr, k), P, v0, v1, v2);
       });
@@ -1473,7 +1496,7 @@ __global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
         st3(Lp, pidx(g, rr, k), P, v0, v1, v2);
       }
       __syncthreads();
-      add_forcing(a, g, Lp, X, l);
+      add_forcing(a, g, Lp, Xr, l);
       push_halos(cl, a, g, Lp, K_ADJ);
     }
   }
@@ -1591,7 +1614,7 @@ __global__ void __launch_bounds__(512) tlm_kernel(SweepArgs<T> a) {
       const int nB[3] = {n, n + 1, n + 1};
       const T wA[3] = {(T)1, (T)1, (T)0.5};
       const T wB[3] = {(T)0, (T)0, (T)0.5};
-      load_states3(a, g, bufs, srcs, nA, nB, wA, wB);
+      load_states<T, 3>(a, g, bufs, srcs, nA, nB, wA, wB);
       stage_tl<T, DEV>(a, g, rs, D1, D, X, D, (T)0, (T)1);
       complete_buf(cl, a, g, D1, K_DELTA, 0, 0, (T)1, (T)0);
       stage_tl<T, DEV>(a, g, rs, D2, D, S1, D1, (T)0.75, (T)0.25);
@@ -2466,17 +2489,39 @@ cudaError_t launch_cluster(K kernel, const SweepArgs<T>& a, int cl, int nthreads
 
 template <typename T> size_t smem_forward(int R, int W) { return smem_bytes<T>(3, R, W, true); }
 template <typename T> size_t smem_adjoint(int R, int W) { return smem_bytes<T>(5, R, W, true); }
+template <typename T> size_t smem_adjoint_rl(int R, int W) { return smem_bytes<T>(4, R, W, true); }
 template <typename T> size_t smem_tlm(int R, int W) { return smem_bytes<T>(6, R, W, false); }
 
+// Clusters of the stripe adjoint (five buffers where they fit, else four)
+// that can be resident at once with cl CTAs per subdomain and nthreads
+// threads per CTA: a cluster must sit inside one GPC, so the count depends on
+// how the GPCs' SMs divide by cl, not only on the CTAs per SM (0 when the
+// shape cannot run).
 template <typename T>
-int occupancy_adjoint(int R, int W, int nthreads) {
-  const size_t smem = smem_adjoint<T>(R, W);
-  if (raise_attributes(adj_kernel<T>) != cudaSuccess) {
+int active_clusters_adjoint(int R, int W, int cl, int nthreads) {
+  const bool five = smem_adjoint<T>(R, W) <= kSmemOptinMax;
+  const size_t smem = five ? smem_adjoint<T>(R, W) : smem_adjoint_rl<T>(R, W);
+  if (smem > kSmemOptinMax || nthreads > 512) return 0;
+  cudaError_t e = five ? raise_attributes(adj_kernel<T, false>) : raise_attributes(adj_kernel<T, true>);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)cl, 1, 1);
+  cfg.blockDim = dim3((unsigned)nthreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cl;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adj_kernel<T>, nthreads, smem) != cudaSuccess) {
+  e = five ? cudaOccupancyMaxActiveClusters(&n, adj_kernel<T, false>, &cfg)
+           : cudaOccupancyMaxActiveClusters(&n, adj_kernel<T, true>, &cfg);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -2501,12 +2546,16 @@ int forward_kind(const SweepArgs<T>& a, int cl, int nthreads) {
   return 1;
 }
 // The deep-halo adjoint covers evaluations with stored stage states (no
-// checkpoints, no external or Gauss-Newton forcing).
+// checkpoints, no external or Gauss-Newton forcing).  Variant 2 selects the
+// stripe adjoint with four state buffers (x(n) reloaded; kind 3); the other
+// variants fall back to it where five buffers do not fit.
 template <typename T>
 int adjoint_kind(const SweepArgs<T>& a, int cl, int nthreads) {
+  const bool rl_fits = nthreads <= 512 && smem_adjoint_rl<T>(a.R, a.W) <= kSmemOptinMax;
+  if (a.variant == 2) return rl_fits ? 3 : 0;
   if (a.stg && a.ckpt == 0 && !a.yforce && !a.gn_dx && deep_fits(a, cl, nthreads, 5)) return 2;
-  if (nthreads > 512 || smem_adjoint<T>(a.R, a.W) > kSmemOptinMax) return 0;
-  return 1;
+  if (nthreads <= 512 && smem_adjoint<T>(a.R, a.W) <= kSmemOptinMax) return 1;
+  return rl_fits ? 3 : 0;
 }
 
 template <typename T>
@@ -2521,13 +2570,17 @@ cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStre
 }
 template <typename T>
 cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
+  const int kind = adjoint_kind(a, cl, nthreads);
   if constexpr (sizeof(T) == 4) {
-    if (adjoint_kind(a, cl, nthreads) == 2)
-      return launch_cluster(adj_deep_kernel, a, cl, nthreads, smem_deep(5, a.R, a.W), st);
+    if (kind == 2) return launch_cluster(adj_deep_kernel, a, cl, nthreads, smem_deep(5, a.R, a.W), st);
   }
   SweepArgs<T> b = a;
+  if (kind == 3) {
+    b.tgb_on = use_target_buffer<T>(4, a.R, a.W, true) ? 1 : 0;
+    return launch_cluster(adj_kernel<T, true>, b, cl, nthreads, smem_adjoint_rl<T>(a.R, a.W), st);
+  }
   b.tgb_on = use_target_buffer<T>(5, a.R, a.W, true) ? 1 : 0;
-  return launch_cluster(adj_kernel<T>, b, cl, nthreads, smem_adjoint<T>(a.R, a.W), st);
+  return launch_cluster(adj_kernel<T, false>, b, cl, nthreads, smem_adjoint<T>(a.R, a.W), st);
 }
 template <typename T>
 cudaError_t launch_tlm(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
@@ -2539,8 +2592,9 @@ cudaError_t launch_tlm(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t
   template int adjoint_kind<T>(const SweepArgs<T>&, int, int);                               \
   template size_t smem_forward<T>(int, int);                                                 \
   template size_t smem_adjoint<T>(int, int);                                                 \
+  template size_t smem_adjoint_rl<T>(int, int);                                              \
   template size_t smem_tlm<T>(int, int);                                                     \
-  template int occupancy_adjoint<T>(int, int, int);                                          \
+  template int active_clusters_adjoint<T>(int, int, int, int);                               \
   template cudaError_t launch_forward<T>(const SweepArgs<T>&, int, int, cudaStream_t);       \
   template cudaError_t launch_adjoint<T>(const SweepArgs<T>&, int, int, cudaStream_t);       \
   template cudaError_t launch_tlm<T>(const SweepArgs<T>&, int, int, cudaStream_t);

@@ -238,3 +238,57 @@ def test_autotuned_checkpoint_interval_matches_oracle(precision):
         _check(ctx, w, ref, FP64_BARS if precision == 0 else FP32_BARS, ("ckpt-tuned", precision, cfg))
     finally:
         ctx.destroy()
+
+
+@pytest.mark.parametrize("precision,ckpt_k,stored", [
+    (0, 0, True), (0, 0, False), (0, -1, False), (0, 5, False), (1, 0, True), (1, 16, False),
+])
+def test_four_buffer_adjoint_matches_five_buffer_adjoint_and_oracle(precision, ckpt_k, stored):
+    """The stripe adjoint in its four-buffer form (mu2 in x(n)'s buffer, x(n)
+    read again from HBM for the lambda(n) phase) gives the five-buffer form's
+    gradient bit for bit and matches the oracle, with stored, recomputed and
+    checkpointed stage states, in 2-, 9- and 16-CTA clusters (ragged
+    workload: stripes of 1-11 rows, walls and frozen edges)."""
+    wl, st, inp, w, ref = _problem("ragged")
+    bars = FP64_BARS if precision == 0 else FP32_BARS
+    ctx = _ctx(wl, st, inp, precision, ckpt_k=ckpt_k)
+    nt_f = 512 if precision == 0 else 384
+    try:
+        for cl in (2, 9, 16):
+            ctx.set_sweep_variant(1, 1)
+            ctx.set_sweep_config((cl, nt_f), (cl, 256), stored)
+            assert ctx.sweep_kernels()["adjoint"] == 1
+            J5, g5 = _check(ctx, w, ref, bars, ("5buf", precision, ckpt_k, cl))
+            ctx.set_sweep_variant(1, 2)
+            ctx.set_sweep_config((cl, nt_f), (cl, 256), stored)
+            assert ctx.sweep_kernels()["adjoint"] == 3
+            J4, g4 = _check(ctx, w, ref, bars, ("4buf", precision, ckpt_k, cl))
+            assert np.array_equal(g4, g5), (precision, ckpt_k, cl)
+            assert np.array_equal(J4, J5), (precision, ckpt_k, cl)
+    finally:
+        ctx.destroy()
+
+
+def test_four_buffer_adjoint_in_gauss_newton_products_and_outer_loop():
+    """Gauss-Newton products (adjoint forced by the tangent-linear dx) and
+    Algorithm 1 end to end give the same results with the four-buffer adjoint
+    as with the five-buffer one."""
+    import paper_2205_06649_gb300 as dd
+    wl = workloads.preset("ragged")
+    st, inp, _ = oracle.build_setup(wl)
+    out = []
+    for var in (1, 2):
+        ctx = _ctx(wl, st, inp, 0, ckpt_k=0)
+        ctx.set_sweep_variant(1, var)
+        ctx.set_sweep_config((4, 256), (4, 256), True)
+        rng = np.random.default_rng(5)
+        w = rng.standard_normal(ctx.ctrl_total) * 0.2
+        p = rng.standard_normal(ctx.ctrl_total)
+        hv = ctx.gn_hessvec(w, p)
+        sv = dd.solver_defaults(max_local_iters=5, max_outer=2, eps_outer=0.0)
+        xa, _, _ = ctx.run(sv)
+        out.append((np.asarray(hv), np.asarray(xa), ctx.sweep_kernels()["adjoint"]))
+        ctx.destroy()
+    assert out[0][2] == 1 and out[1][2] == 3
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
