@@ -395,7 +395,7 @@ def run_reference(args):
 # 0.4-2.6 s on tuning.  9-CTA clusters: a GPC of 18 or 20 SMs holds two of
 # them at one CTA per SM (135 of 152 SMs busy), but only one 16-CTA cluster
 # (112 SMs).
-DEFAULT_SHAPES = {("large", 0): "9,512,9,512,0,1,2", ("large", 1): "9,512,9,512,1,0,2"}
+DEFAULT_SHAPES = {("large", 0): "9,512,9,1024,0,1,2", ("large", 1): "9,512,9,1024,1,0,1"}
 
 
 def roofline_of(ctx, prec, reps=3):

@@ -396,8 +396,8 @@ dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* ctx, int* shape, double* eval_m
 
 /* Force launch shapes (e.g. ones an earlier autotuning run reported), same
  * layout as dd4dv_sweep_config: cluster sizes 1..16 (<= smallest box height),
- * threads a multiple of 32 in 64..640 (the stripe sweeps take at most 512,
- * 384 for the FP32-state forward; more need the deep-halo FP32 sweeps, see
+ * threads a multiple of 32 in 64..1024 (the stripe sweeps take at most 1024,
+ * 384 for the FP32-state forward; the deep-halo FP32 sweeps at most 640, see
  * dd4dv_set_sweep_variant), stored stages 1 only with ckpt_k = 0 and the
  * stage buffer present; DD4DV_EINVAL for a shape no kernel can run.  Results
  * are the same for every shape up to the order of the partial sums of J. */

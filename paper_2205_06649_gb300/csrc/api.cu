@@ -656,8 +656,9 @@ void autotune(dd4dv_ctx* ctx) {
         cls.push_back(c);
     ctx->variant_a = va;
   }
-  // 640 and 576 threads only reach the deep-halo FP32 sweeps
-  const int nts[] = {640, 576, 512, 448, 384, 320, 256, 192};
+  // 1024 and 768 threads reach the FP64 forward and the stripe adjoints, 640
+  // and 576 also the deep-halo FP32 sweeps
+  const int nts[] = {1024, 768, 640, 576, 512, 448, 384, 320, 256, 192};
   // reference time of the starting shape sets the budget
   float tf0 = 0, ta0 = 0;
   const int c0 = ctx->cl, n0 = ctx->nthreads;
@@ -2480,7 +2481,7 @@ dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape) {
       if (c < 1 || c > 16 || c > ctx->min_ny)
         fail(ctx, DD4DV_EINVAL, "cluster sizes must be 1..16 and <= the smallest box height %d", ctx->min_ny);
     for (int t : {tf, ta})
-      if (t < 64 || t > 640 || t % 32) fail(ctx, DD4DV_EINVAL, "threads must be a multiple of 32 in 64..640");
+      if (t < 64 || t > 1024 || t % 32) fail(ctx, DD4DV_EINVAL, "threads must be a multiple of 32 in 64..1024");
     if (sg && !ctx->stg) fail(ctx, DD4DV_EINVAL, "no stage buffer (ckpt_k != 0 or freed by the autotuner)");
     const int Rf = (ctx->max_ny + cf - 1) / cf, Ra = (ctx->max_ny + ca - 1) / ca;
     const bool stg0 = ctx->use_stg;
@@ -2490,7 +2491,7 @@ dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape) {
     if (!kf || !ka)
       fail(ctx, DD4DV_EINVAL,
            "%s sweep shape cannot run: too much shared memory, or more threads than the stripe sweep allows "
-           "(FP32 forward 384, else 512) where the deep-halo FP32 sweep does not apply (it needs stripes of "
+           "(FP32 forward 384, else 1024) where the deep-halo FP32 sweep does not apply (it needs stripes of "
            ">= 3 rows, <= 4 own points per thread and <= 640 threads)",
            !kf ? "forward" : "adjoint");
     ctx->cl_f = cf; ctx->nt_f = tf; ctx->R_f = Rf;

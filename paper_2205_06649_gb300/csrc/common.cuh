@@ -108,10 +108,13 @@ struct SweepArgs {
                               // adjoint with four state buffers, x(n) reloaded from HBM
 };
 
-// Largest CTA of the forward sweep: 384 threads on the FP32 path, whose
-// forward kernel is compiled for up to 80 registers (2 CTAs of 384 threads
-// per SM), 512 on the FP64 path (64 registers).
-template <typename T> constexpr int max_threads_forward() { return sizeof(T) == 4 ? 384 : 512; }
+// Largest CTA of the stripe forward sweep: 384 threads on the FP32 path,
+// whose forward kernel is compiled for up to 80 registers (2 CTAs of 384
+// threads per SM), 1024 on the FP64 path (64 registers, one CTA of 1024 or two
+// of 512 per SM).  The stripe adjoint takes up to 1024 threads (64 registers).
+template <typename T> constexpr int max_threads_forward() { return sizeof(T) == 4 ? 384 : 1024; }
+template <typename T> constexpr int min_blocks_forward() { return sizeof(T) == 4 ? 2 : 1; }
+constexpr int kStripeAdjThreads = 1024;
 
 // ---- launchers (sweep.cu) ----
 // Which kernel a sweep launch with cl CTAs per subdomain and nthreads threads

@@ -1174,7 +1174,7 @@ size_t smem_bytes(int nbuf, int R, int W, bool cache) {
 // Forward sweep: x(a) (stored at level 0 by the init kernel) -> x(a+1..b),
 // trajectory stored at every level, J_o and J_mu partial sums per CTA.
 template <typename T>
-__global__ void __launch_bounds__(max_threads_forward<T>(), 2) fwd_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(max_threads_forward<T>(), min_blocks_forward<T>()) fwd_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;
@@ -1323,7 +1323,7 @@ __device__ void add_forcing(const SweepArgs<T>& a, const Geo<T>& g, T* Lb, const
 // phase before (its edge rows, the only readers of halo rows, are done), and
 // the RL = true stored-stage step loads nothing into that buffer.
 template <typename T, bool RL>
-__global__ void __launch_bounds__(512, 2) adj_kernel(SweepArgs<T> a) {
+__global__ void __launch_bounds__(kStripeAdjThreads, 1) adj_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
   Geo<T> g;
@@ -2501,7 +2501,7 @@ template <typename T>
 int active_clusters_adjoint(int R, int W, int cl, int nthreads) {
   const bool five = smem_adjoint<T>(R, W) <= kSmemOptinMax;
   const size_t smem = five ? smem_adjoint<T>(R, W) : smem_adjoint_rl<T>(R, W);
-  if (smem > kSmemOptinMax || nthreads > 512) return 0;
+  if (smem > kSmemOptinMax || nthreads > kStripeAdjThreads) return 0;
   cudaError_t e = five ? raise_attributes(adj_kernel<T, false>) : raise_attributes(adj_kernel<T, true>);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -2551,10 +2551,10 @@ int forward_kind(const SweepArgs<T>& a, int cl, int nthreads) {
 // variants fall back to it where five buffers do not fit.
 template <typename T>
 int adjoint_kind(const SweepArgs<T>& a, int cl, int nthreads) {
-  const bool rl_fits = nthreads <= 512 && smem_adjoint_rl<T>(a.R, a.W) <= kSmemOptinMax;
+  const bool rl_fits = nthreads <= kStripeAdjThreads && smem_adjoint_rl<T>(a.R, a.W) <= kSmemOptinMax;
   if (a.variant == 2) return rl_fits ? 3 : 0;
   if (a.stg && a.ckpt == 0 && !a.yforce && !a.gn_dx && deep_fits(a, cl, nthreads, 5)) return 2;
-  if (nthreads <= 512 && smem_adjoint<T>(a.R, a.W) <= kSmemOptinMax) return 1;
+  if (nthreads <= kStripeAdjThreads && smem_adjoint<T>(a.R, a.W) <= kSmemOptinMax) return 1;
   return rl_fits ? 3 : 0;
 }
 
@@ -2582,9 +2582,11 @@ cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, int nthreads, cudaStre
   b.tgb_on = use_target_buffer<T>(5, a.R, a.W, true) ? 1 : 0;
   return launch_cluster(adj_kernel<T, false>, b, cl, nthreads, smem_adjoint<T>(a.R, a.W), st);
 }
+// The tangent-linear kernel is compiled for at most 512 threads (its loops
+// are strided, so any CTA size gives the same result).
 template <typename T>
 cudaError_t launch_tlm(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {
-  return launch_cluster(tlm_kernel<T>, a, cl, nthreads, smem_tlm<T>(a.R, a.W), st);
+  return launch_cluster(tlm_kernel<T>, a, cl, std::min(nthreads, 512), smem_tlm<T>(a.R, a.W), st);
 }
 
 #define DD4DV_INST(T)                                                                        \

@@ -119,10 +119,10 @@ def test_gpu_outer_loop_reaches_blue_closed_form():
 
 def test_sweep_shape_limits():
     """Launch shapes no kernel can run are refused with EINVAL: the stripe
-    sweeps take at most 384 (FP32-state forward) / 512 threads, the deep-halo
-    FP32 sweeps at most 640 and need stripes of >= 3 rows (and, for the
-    adjoint, stored stage states).  A shape at a limit gives the autotuned
-    result up to the order of J's partial sums."""
+    sweeps take at most 384 (FP32-state forward) / 1024 threads, the
+    deep-halo FP32 sweeps at most 640 and need stripes of >= 3 rows (and, for
+    the adjoint, stored stage states).  A shape at a limit gives the
+    autotuned result up to the order of J's partial sums."""
     import paper_2205_06649_gb300 as dd
     wl = workloads.preset("ragged")
     st, inp, _ = oracle.build_setup(wl)
@@ -131,7 +131,7 @@ def test_sweep_shape_limits():
     J0, g0 = ctx.eval(w)
     bad = [(0, (8, 416), (2, 256)),     # stripes of 2 rows: no deep-halo sweep, stripe limit 384
            (1, (2, 416), (2, 256)),     # stripe sweeps requested
-           (0, (2, 256), (2, 544)),     # recomputed stages: stripe adjoint, limit 512
+           (0, (2, 256), (2, 1056)),    # above every kernel's limit
            (0, (2, 672), (2, 256)),     # above the deep-halo limit
            (0, (17, 256), (2, 256)), (0, (2, 100), (2, 256))]
     for variant, fwd, adj in bad:
@@ -146,6 +146,10 @@ def test_sweep_shape_limits():
     ctx.set_sweep_variant(0)
     ctx.set_sweep_config((2, 640), (2, 512), False)
     assert ctx.sweep_kernels() == {"forward": 2, "adjoint": 1}
+    J, g = ctx.eval(w)
+    assert rel(J, J0) <= 1e-6 and np.array_equal(g, g0)
+    ctx.set_sweep_variant(1)
+    ctx.set_sweep_config((2, 384), (2, 1024), False)   # the stripe adjoint's limit
     J, g = ctx.eval(w)
     assert rel(J, J0) <= 1e-6 and np.array_equal(g, g0)
     ctx.destroy()

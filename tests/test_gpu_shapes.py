@@ -292,3 +292,35 @@ def test_four_buffer_adjoint_in_gauss_newton_products_and_outer_loop():
     assert out[0][2] == 1 and out[1][2] == 3
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_thousand_thread_stripe_sweeps_match_oracle(precision):
+    """The stripe sweeps at their thread limit (1024 for the FP64 forward and
+    every stripe adjoint; the FP32 forward stops at 384), with the five- and
+    four-buffer adjoint, in 2- and 9-CTA clusters, against the oracle; the
+    gradient does not depend on the thread count."""
+    wl, st, inp, w, ref = _problem("ragged")
+    bars = FP64_BARS if precision == 0 else FP32_BARS
+    ctx = _ctx(wl, st, inp, precision, ckpt_k=0)
+    nt_f = 1024 if precision == 0 else 384
+    try:
+        for cl in (2, 9):
+            grads = []
+            for va, nt in ((1, 256), (1, 1024), (2, 1024)):
+                ctx.set_sweep_variant(1, va)
+                ctx.set_sweep_config((cl, nt_f), (cl, nt), False)
+                _, g = _check(ctx, w, ref, bars, ("1024", precision, cl, va, nt))
+                grads.append(g)
+            assert all(np.array_equal(grads[0], g) for g in grads[1:]), (precision, cl)
+        # the tangent-linear sweep (at most 512 threads) runs under a
+        # 1024-thread adjoint shape and gives the same result
+        dw = np.random.default_rng(3).standard_normal(ctx.ctrl_total)
+        dx = []
+        for nt in (256, 1024):
+            ctx.set_sweep_variant(1, 1)
+            ctx.set_sweep_config((2, nt_f), (2, nt), False)
+            dx.append(np.asarray(ctx.tlm(w, dw)))
+        assert np.array_equal(dx[0], dx[1])
+    finally:
+        ctx.destroy()
