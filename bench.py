@@ -390,12 +390,13 @@ def run_reference(args):
 # Launch shapes for the large workload, the fastest of a shape search on its
 # boxes (forward cluster, forward threads, adjoint cluster, adjoint threads,
 # stored stage states, forward variant, adjoint variant; variant 1 = stripe
-# sweep, 0 = deep-halo FP32 sweep where it applies, 2 = four-buffer stripe
-# adjoint): the benchmark forces them instead of spending ~80 evaluations of
-# 0.4-2.6 s on tuning.  9-CTA clusters: a GPC of 18 or 20 SMs holds two of
-# them at one CTA per SM (135 of 152 SMs busy), but only one 16-CTA cluster
-# (112 SMs).
-DEFAULT_SHAPES = {("large", 0): "9,512,9,1024,0,1,2", ("large", 1): "9,512,9,1024,1,0,1"}
+# sweep, 0 = deep-halo FP32 sweep where it applies, 2 = two-buffer stripe
+# forward / four-buffer stripe adjoint): the benchmark forces them instead of
+# spending ~80 evaluations of 0.4-2.6 s on tuning.  9-CTA clusters for the
+# adjoint: a GPC of 18 or 20 SMs holds two of them at one CTA per SM (135 of
+# 152 SMs busy), but only one 16-CTA cluster (112 SMs).  The two-buffer
+# forward fits two CTAs per SM in 10- (FP64) or 12-CTA (FP32) clusters.
+DEFAULT_SHAPES = {("large", 0): "10,384,9,1024,0,2,2", ("large", 1): "12,384,9,1024,1,2,1"}
 
 
 def roofline_of(ctx, prec, reps=3):

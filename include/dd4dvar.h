@@ -423,9 +423,14 @@ dd4dv_status dd4dv_checkpoint_interval(const dd4dv_ctx* ctx, int* k, double* eva
  * buffers in shared memory instead of five; same values bit for bit, one more
  * state read per step.  It lets larger stripes (fewer CTAs per subdomain) or
  * more CTAs per SM fit.
+ * The stripe forward also has a two-buffer form: x2 is written over x(n)
+ * and the last stage reads x(n) from the trajectory level stored the step
+ * before (every level stored, ckpt_k 0 or -1), so two CTAs per SM fit where
+ * three buffers fit one; same values bit for bit.
  * forward: 0 = deep-halo sweep wherever it applies (default), 1 = stripe
- * sweep only.  adjoint: 0 and 1 as for the forward (the stripe adjoint takes
- * its four-buffer form where five buffers do not fit), 2 = the four-buffer
+ * sweep only, 2 = the two-buffer stripe forward where it applies (else as
+ * 1).  adjoint: 0 and 1 as for the forward (the stripe adjoint takes its
+ * four-buffer form where five buffers do not fit), 2 = the four-buffer
  * stripe adjoint.  EINVAL for other values.  The autotuner (cluster = -1 in
  * dd4dv_decomp) times every form that applies and keeps the fastest one for
  * each sweep; dd4dv_sweep_kernels reports which run. */
@@ -433,7 +438,7 @@ dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int forward, int adjoint);
 
 /* Which kernels the current launch shapes run: kinds[0] forward, kinds[1]
  * adjoint; 1 = stripe sweep, 2 = deep-halo sweep, 3 = four-buffer stripe
- * adjoint. */
+ * adjoint, 4 = two-buffer stripe forward. */
 dd4dv_status dd4dv_sweep_kernels(const dd4dv_ctx* ctx, int* kinds);
 
 /* The cluster size (CTAs per subdomain) the sweeps use. */

@@ -23,7 +23,7 @@ __all__ = ["Context", "DD4DVError", "lib", "solver_defaults"]
 lib = _abi.load()
 
 # dd4dv_sweep_kernels codes
-KERNEL_NAMES = {1: "stripe", 2: "deep-halo", 3: "stripe-4buf"}
+KERNEL_NAMES = {1: "stripe", 2: "deep-halo", 3: "stripe-4buf", 4: "stripe-2buf"}
 
 
 class DD4DVError(RuntimeError):
@@ -181,15 +181,16 @@ class Context:
     # ---- queries ----
     def set_sweep_variant(self, forward: int, adjoint: int = None):
         """Per sweep: 0 = deep-halo FP32 sweep wherever it applies (default),
-        1 = stripe sweep only; the adjoint also takes 2 = the four-buffer
-        stripe adjoint (x(n) reloaded).  adjoint defaults to the forward's
-        value."""
+        1 = stripe sweep only, 2 = the two-buffer stripe forward (x(n) read
+        from the stored level) / the four-buffer stripe adjoint (x(n)
+        reloaded).  adjoint defaults to the forward's value."""
         adjoint = forward if adjoint is None else adjoint
         self._check(lib.dd4dv_set_sweep_variant(self._h, int(forward), int(adjoint)))
 
     def sweep_kernels(self) -> dict:
         """Kernels the current shapes run: 1 = stripe sweep, 2 = deep-halo
-        sweep, 3 = four-buffer stripe adjoint."""
+        sweep, 3 = four-buffer stripe adjoint, 4 = two-buffer stripe
+        forward."""
         k = np.zeros(2, dtype=np.int32)
         self._check(lib.dd4dv_sweep_kernels(self._h, C.c_void_p(k.ctypes.data)))
         return {"forward": int(k[0]), "adjoint": int(k[1])}

@@ -686,13 +686,18 @@ void autotune(dd4dv_ctx* ctx) {
             ctx->variant_f = ctx->variant_a = 1;
             if (!deep) continue;
           }
-          // the four-buffer adjoint (forward as for variant 1), where the
-          // other variants did not already fall back to it
+          // the two-buffer forward and the four-buffer adjoint, where they
+          // apply and the other variants did not already fall back to them
+          bool new_f = false, new_a = false;
           if (var == 2) {
             ctx->variant_f = ctx->variant_a = 1;
-            if (adj_kind_at(ctx, c, nt) == 3) continue;
-            ctx->variant_a = 2;
-            if (!adj_kind_at(ctx, c, nt)) continue;
+            const bool a3 = adj_kind_at(ctx, c, nt) == 3;
+            ctx->variant_f = ctx->variant_a = 2;
+            new_f = fwd_kind_at(ctx, c, std::min(nt, f32 ? max_threads_forward<float>()
+                                                       : max_threads_forward<double>())) == 4;
+            new_a = !a3 && adj_kind_at(ctx, c, nt) == 3;
+            if (!new_f) ctx->variant_f = 1;
+            if (!new_f && !new_a) continue;
           }
           float tf = 0, ta = 0, tf2 = 0, ta2 = 0;
           if (!run(c, nt, &tf, &ta)) continue;
@@ -700,8 +705,8 @@ void autotune(dd4dv_ctx* ctx) {
           spent += tf + ta + tf2 + ta2;
           tf = std::min(tf, tf2);
           ta = std::min(ta, ta2);
-          if (var != 2 && tf < best_f[use].t) best_f[use] = {tf, c, ctx->nt_f, var};
-          if (ta < best_a[use].t) best_a[use] = {ta, c, nt, var};
+          if ((var != 2 || new_f) && tf < best_f[use].t) best_f[use] = {tf, c, ctx->nt_f, var};
+          if ((var != 2 || new_a) && ta < best_a[use].t) best_a[use] = {ta, c, nt, var};
         }
   }
   for (auto& e : ev) cudaEventDestroy(e);
@@ -2514,9 +2519,10 @@ dd4dv_status dd4dv_checkpoint_interval(const dd4dv_ctx* cctx, int* k, double* ev
 
 dd4dv_status dd4dv_set_sweep_variant(dd4dv_ctx* ctx, int forward, int adjoint) {
   return guard(ctx, [&] {
-    if ((forward != 0 && forward != 1) || adjoint < 0 || adjoint > 2)
+    if (forward < 0 || forward > 2 || adjoint < 0 || adjoint > 2)
       fail(ctx, DD4DV_EINVAL,
-           "variants: 0 (automatic) or 1 (stripe sweeps); the adjoint also 2 (four-buffer stripe adjoint)");
+           "variants: 0 (automatic), 1 (stripe sweeps) or 2 (two-buffer stripe forward, four-buffer stripe "
+           "adjoint)");
     ctx->variant_f = forward;
     ctx->variant_a = adjoint;
     ctx->drop_graphs();

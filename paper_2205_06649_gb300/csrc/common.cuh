@@ -104,8 +104,9 @@ struct SweepArgs {
                               // buffer of prefetched overlap targets (only if it still fits)
   int min_ny;                 // smallest box height of the decomposition
   int variant;                // 0: deep-halo FP32 sweeps where they apply, else the stripe
-                              // sweeps; 1: stripe sweeps only; 2 (adjoint only): the stripe
-                              // adjoint with four state buffers, x(n) reloaded from HBM
+                              // sweeps; 1: stripe sweeps only; 2: the stripe adjoint with
+                              // four state buffers (x(n) reloaded from HBM), the stripe
+                              // forward with two (x(n) read from the stored level)
 };
 
 // Largest CTA of the stripe forward sweep: 384 threads on the FP32 path,
@@ -120,7 +121,8 @@ constexpr int kStripeAdjThreads = 1024;
 // Which kernel a sweep launch with cl CTAs per subdomain and nthreads threads
 // per CTA would run: 0 = none (shape not launchable), 1 = the stripe sweep
 // (one halo row per stage), 2 = the deep-halo FP32 sweep (three halo rows, one
-// exchange per step), 3 = the stripe adjoint with four state buffers.
+// exchange per step), 3 = the stripe adjoint with four state buffers, 4 =
+// the stripe forward with two state buffers.
 template <typename T> int forward_kind(const SweepArgs<T>& a, int cl, int nthreads);
 template <typename T> int adjoint_kind(const SweepArgs<T>& a, int cl, int nthreads);
 template <typename T> cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st);

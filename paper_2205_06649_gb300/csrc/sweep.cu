@@ -668,6 +668,37 @@ __device__ __forceinline__ int overlap_count(const Geo<T>& g, int l, int r, int 
 
 // Observation misfit of the observations of level l whose lower corner row
 // is one of this CTA's rows: J_o += 1/2 w d^2, obs_force = lambda w d.
+// Observation term of one record with explicit rounding, so that every
+// sweep kernel that evaluates it rounds alike: the bilinear value of the
+// corner values x00, x01 (i + 1), x10 (j + 1), x11 (only the corners with
+// non-zero weight are used), d = H x - y, J_o += 1/2 w d^2; returns the
+// forcing lambda w d.
+__device__ __forceinline__ double obs_term(const ObsRec& ob, double x00, double x01, double x10, double x11,
+                                           double lam, double& Jo) {
+  const double wj0 = __dsub_rn(1.0, ob.dj), wi0 = __dsub_rn(1.0, ob.di);
+  double acc = __dmul_rn(__dmul_rn(wj0, wi0), x00);
+  if (ob.di != 0.0) acc = __fma_rn(__dmul_rn(wj0, ob.di), x01, acc);
+  if (ob.dj != 0.0) {
+    acc = __fma_rn(__dmul_rn(ob.dj, wi0), x10, acc);
+    if (ob.di != 0.0) acc = __fma_rn(__dmul_rn(ob.dj, ob.di), x11, acc);
+  }
+  const double d = __dsub_rn(acc, ob.y);
+  Jo = __fma_rn(__dmul_rn(__dmul_rn(0.5, ob.w), d), d, Jo);
+  return __dmul_rn(__dmul_rn(lam, ob.w), d);
+}
+
+// Overlap misfit of one point with overlap count c, explicitly rounded:
+// part + c ((x0 - t0)^2 i0 + (x1 - t1)^2 i1 + (x2 - t2)^2 i2).
+template <typename T>
+__device__ __forceinline__ T overlap_term(T part, int c, T x0, T x1, T x2, T t0, T t1, T t2, T i0, T i1,
+                                          T i2) {
+  const T e0 = xsub(x0, t0), e1 = xsub(x1, t1), e2 = xsub(x2, t2);
+  T sq = xmul(xmul(e0, e0), i0);
+  sq = xfma(xmul(e1, e1), i1, sq);
+  sq = xfma(xmul(e2, e2), i2, sq);
+  return xfma((T)c, sq, part);
+}
+
 template <typename T>
 __device__ void obs_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, int l, double& Jo) {
   const int o0 = a.lvl_obs[g.d.obs_lvl + l], o1 = a.lvl_obs[g.d.obs_lvl + l + 1];
@@ -677,17 +708,11 @@ __device__ void obs_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X, in
     const ObsRec ob = a.obs[o];
     const int rr = ob.r0 - g.R0;
     if (rr < 0 || rr >= g.Rn) continue;
-    double acc = 0.0;
-    const double wj0 = 1.0 - ob.dj, wi0 = 1.0 - ob.di;
-    acc += (wj0 * wi0) * (double)X[off(g, ob.var, rr, ob.k0)];
-    if (ob.di != 0.0) acc += (wj0 * ob.di) * (double)X[off(g, ob.var, rr, ob.k1)];
-    if (ob.dj != 0.0) {
-      acc += (ob.dj * wi0) * (double)X[off(g, ob.var, rr + 1, ob.k0)];
-      if (ob.di != 0.0) acc += (ob.dj * ob.di) * (double)X[off(g, ob.var, rr + 1, ob.k1)];
-    }
-    const double d = acc - ob.y;
-    Jo += 0.5 * ob.w * d * d;
-    a.obs_force[o] = a.lam * ob.w * d;
+    const double x00 = (double)X[off(g, ob.var, rr, ob.k0)];
+    const double x01 = ob.di != 0.0 ? (double)X[off(g, ob.var, rr, ob.k1)] : 0.0;
+    const double x10 = ob.dj != 0.0 ? (double)X[off(g, ob.var, rr + 1, ob.k0)] : 0.0;
+    const double x11 = (ob.dj != 0.0 && ob.di != 0.0) ? (double)X[off(g, ob.var, rr + 1, ob.k1)] : 0.0;
+    a.obs_force[o] = obs_term(ob, x00, x01, x10, x11, a.lam, Jo);
   }
 }
 
@@ -790,10 +815,7 @@ __device__ void overlap_level(const SweepArgs<T>& a, const Geo<T>& g, const T* X
       t1 = tg[go + pl];
       t2 = tg[go + 2 * pl];
     }
-    const T e0 = x0 - t0;
-    const T e1 = x1 - t1;
-    const T e2 = x2 - t2;
-    part += (T)c * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
+    part = overlap_term(part, c, x0, x1, x2, t0, t1, t2, i0, i1, i2);
   });
   Jm += (double)part;
 }
@@ -1173,7 +1195,17 @@ size_t smem_bytes(int nbuf, int R, int W, bool cache) {
 // ---------------------------------------------------------------------------
 // Forward sweep: x(a) (stored at level 0 by the init kernel) -> x(a+1..b),
 // trajectory stored at every level, J_o and J_mu partial sums per CTA.
-template <typename T>
+//
+// TB = true: two state buffers instead of three.  x2 is written over x(n) in
+// place (each point reads x(n) only at itself), and the last stage reads
+// x(n) point by point from the trajectory level stored the step before
+// (needs every level stored: ckpt 0).  Same arithmetic on the same values,
+// so the same results; the smaller footprint fits two CTAs per SM where three
+// buffers fit one.  The buffers swap roles every step.  Writing x2 over
+// x(n) is safe under the pushed exchange: x(n)'s halo rows are read only by
+// the first stage's edge rows, before this CTA's arrive, and a neighbour
+// pushes x2 rows only after that arrive.
+template <typename T, bool TB>
 __global__ void __launch_bounds__(max_threads_forward<T>(), min_blocks_forward<T>()) fwd_kernel(SweepArgs<T> a) {
   constexpr bool DEV = sizeof(T) == 4;
   cg::cluster_group cl = cg::this_cluster();
@@ -1182,10 +1214,10 @@ __global__ void __launch_bounds__(max_threads_forward<T>(), min_blocks_forward<T
   T* buf[3];
   RowSmem<T> rs;
   double* scratch;
-  carve(a, g, 3, buf, rs, &scratch, true);
+  carve(a, g, TB ? 2 : 3, buf, rs, &scratch, true);
   T* X = buf[0];
   T* S1 = buf[1];
-  T* S2 = buf[2];
+  T* S2 = TB ? nullptr : buf[2];
   load_rows(a, g, rs);
   ghost_prefetch(a, g, g.a);
   if (g.L > 0) ghost_prefetch(a, g, g.a + 1);
@@ -1207,9 +1239,32 @@ __global__ void __launch_bounds__(max_threads_forward<T>(), min_blocks_forward<T
     if (n + 2 <= g.d.b) ghost_prefetch(a, g, n + 2);
     prefetch_targets(a, g, l + 1);
     cp_async_commit();
-    stage_push<T, DEV>(cl, a, g, rs, S2, X, S1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5, 1);
-    if (a.stg) store_block(g, S2, stage_ptr(a, g, l, 1));
-    stage_push<T, DEV>(cl, a, g, rs, X, X, S2, (T)(1.0 / 3.0), (T)(2.0 / 3.0), n + 1, n + 1, (T)1, (T)0);
+    if constexpr (TB) {
+      // x2 over x(n), then x(n+1) = 1/3 x(n) + 2/3 (x2 + dt F(x2)) into x1's
+      // buffer with x(n) read from the stored level l
+      stage_push<T, DEV>(cl, a, g, rs, X, X, S1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5, 1);
+      if (a.stg) store_block(g, X, stage_ptr(a, g, l, 1));
+      const T* xs = a.traj + g.d.traj_off + (size_t)l * 3 * g.ny * g.d.nxp;
+      const size_t pl = (size_t)g.ny * g.d.nxp;
+      phase_push(cl, a, g, S1, K_STATE, n + 1, n + 1, (T)1, (T)0, [&](int rr, int k, T& o0, T& o1, T& o2) {
+        const int o = pidx(g, rr, k);
+        T rc[8];
+        load_rec8(rs.fw + 8 * (rr + 1), rc);
+        Pt5<T> y;
+        load5(X, o, g.P, Lay<T>::CS, g.RS, y);
+        const T* q = xs + (size_t)(g.R0 + rr) * g.d.nxp + k;
+        stage_math<T, DEV>(y, rc, a.dt_s, a.Bth_s, a.gBth_s, a.href_s, (T)(1.0 / 3.0), (T)(2.0 / 3.0), q[0],
+                           q[pl], q[2 * pl], o0, o1, o2);
+        st3(S1, o, g.P, o0, o1, o2);
+      });
+      T* t = X;
+      X = S1;
+      S1 = t;
+    } else {
+      stage_push<T, DEV>(cl, a, g, rs, S2, X, S1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5, 1);
+      if (a.stg) store_block(g, S2, stage_ptr(a, g, l, 1));
+      stage_push<T, DEV>(cl, a, g, rs, X, X, S2, (T)(1.0 / 3.0), (T)(2.0 / 3.0), n + 1, n + 1, (T)1, (T)0);
+    }
     if (a.ckpt == 0 || (l + 1) % a.ckpt == 0) store_level(a, g, X, l + 1);
     obs_level(a, g, X, l + 1, Jo);
     overlap_level(a, g, X, l + 1, Jm);
@@ -2026,17 +2081,11 @@ __device__ void obs_level2(const SweepArgs<float>& a, const G2& g, const float* 
     const ObsRec ob = a.obs[o];
     const int rr = ob.r0 - g.R0;
     if (rr < 0 || rr >= g.Rn) continue;
-    double acc = 0.0;
-    const double wj0 = 1.0 - ob.dj, wi0 = 1.0 - ob.di;
-    acc += (wj0 * wi0) * (double)X[p2(g, rr, ob.k0) + ob.var];
-    if (ob.di != 0.0) acc += (wj0 * ob.di) * (double)X[p2(g, rr, ob.k1) + ob.var];
-    if (ob.dj != 0.0) {
-      acc += (ob.dj * wi0) * (double)X[p2(g, rr + 1, ob.k0) + ob.var];
-      if (ob.di != 0.0) acc += (ob.dj * ob.di) * (double)X[p2(g, rr + 1, ob.k1) + ob.var];
-    }
-    const double d = acc - ob.y;
-    Jo += 0.5 * ob.w * d * d;
-    a.obs_force[o] = a.lam * ob.w * d;
+    const double x00 = (double)X[p2(g, rr, ob.k0) + ob.var];
+    const double x01 = ob.di != 0.0 ? (double)X[p2(g, rr, ob.k1) + ob.var] : 0.0;
+    const double x10 = ob.dj != 0.0 ? (double)X[p2(g, rr + 1, ob.k0) + ob.var] : 0.0;
+    const double x11 = (ob.dj != 0.0 && ob.di != 0.0) ? (double)X[p2(g, rr + 1, ob.k1) + ob.var] : 0.0;
+    a.obs_force[o] = obs_term(ob, x00, x01, x10, x11, a.lam, Jo);
   }
 }
 
@@ -2124,8 +2173,7 @@ __global__ void __launch_bounds__(kDeepThreads, 1) fwd_deep_kernel(SweepArgs<flo
         const int rr = mdiv(idx, g.mnx), k = idx - rr * g.nx;
         float x0, x1, x2;
         ld3(X, p2(g, rr, k), 1, x0, x1, x2);
-        const float e0 = x0 - tv[i][0], e1 = x1 - tv[i][1], e2 = x2 - tv[i][2];
-        part += (float)cv[i] * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
+        part = overlap_term(part, cv[i], x0, x1, x2, tv[i][0], tv[i][1], tv[i][2], i0, i1, i2);
       }
     }
     Jm += (double)part;
@@ -2179,8 +2227,7 @@ __global__ void __launch_bounds__(kDeepThreads, 1) fwd_deep_kernel(SweepArgs<flo
         publish2(g, X, true, rr, k, o0, o1, o2);
         push2(g, hxS, hxN, rr, k, o0, o1, o2);
         if (cv[i]) {
-          const float e0 = o0 - tv[i][0], e1 = o1 - tv[i][1], e2 = o2 - tv[i][2];
-          part += (float)cv[i] * (e0 * e0 * i0 + e1 * e1 * i1 + e2 * e2 * i2);
+          part = overlap_term(part, cv[i], o0, o1, o2, tv[i][0], tv[i][1], tv[i][2], i0, i1, i2);
         }
       }
     }
@@ -2488,6 +2535,7 @@ cudaError_t launch_cluster(K kernel, const SweepArgs<T>& a, int cl, int nthreads
 }  // namespace
 
 template <typename T> size_t smem_forward(int R, int W) { return smem_bytes<T>(3, R, W, true); }
+template <typename T> size_t smem_forward2(int R, int W) { return smem_bytes<T>(2, R, W, true); }
 template <typename T> size_t smem_adjoint(int R, int W) { return smem_bytes<T>(5, R, W, true); }
 template <typename T> size_t smem_adjoint_rl(int R, int W) { return smem_bytes<T>(4, R, W, true); }
 template <typename T> size_t smem_tlm(int R, int W) { return smem_bytes<T>(6, R, W, false); }
@@ -2533,14 +2581,20 @@ int active_clusters_adjoint(int R, int W, int cl, int nthreads) {
 // the threads fit its register budget and its shared memory fits.
 template <typename T>
 bool deep_fits(const SweepArgs<T>& a, int cl, int nthreads, int nbuf) {
-  if (sizeof(T) != 4 || a.variant == 1 || cl < 1) return false;
+  if (sizeof(T) != 4 || a.variant != 0 || cl < 1) return false;
   if (a.min_ny < kH * cl || nthreads > kDeepThreads || nthreads < 64 || nthreads % 32) return false;
   if ((long long)a.R * (a.W - 2) > (long long)kMaxP * nthreads) return false;
   return smem_deep(nbuf, a.R, a.W) <= kSmemOptinMax;
 }
 
+// Forward variant 2 selects the two-buffer stripe forward (kind 4), which
+// needs every trajectory level stored (ckpt 0); otherwise it acts as
+// variant 1.
 template <typename T>
 int forward_kind(const SweepArgs<T>& a, int cl, int nthreads) {
+  if (a.variant == 2 && a.ckpt == 0 && nthreads <= max_threads_forward<T>() &&
+      smem_forward2<T>(a.R, a.W) <= kSmemOptinMax)
+    return 4;
   if (deep_fits(a, cl, nthreads, 3)) return 2;
   if (nthreads > max_threads_forward<T>() || smem_forward<T>(a.R, a.W) > kSmemOptinMax) return 0;
   return 1;
@@ -2565,8 +2619,12 @@ cudaError_t launch_forward(const SweepArgs<T>& a, int cl, int nthreads, cudaStre
       return launch_cluster(fwd_deep_kernel, a, cl, nthreads, smem_deep(3, a.R, a.W), st);
   }
   SweepArgs<T> b = a;
+  if (forward_kind(a, cl, nthreads) == 4) {
+    b.tgb_on = use_target_buffer<T>(2, a.R, a.W, true) ? 1 : 0;
+    return launch_cluster(fwd_kernel<T, true>, b, cl, nthreads, smem_forward2<T>(a.R, a.W), st);
+  }
   b.tgb_on = use_target_buffer<T>(3, a.R, a.W, true) ? 1 : 0;
-  return launch_cluster(fwd_kernel<T>, b, cl, nthreads, smem_forward<T>(a.R, a.W), st);
+  return launch_cluster(fwd_kernel<T, false>, b, cl, nthreads, smem_forward<T>(a.R, a.W), st);
 }
 template <typename T>
 cudaError_t launch_adjoint(const SweepArgs<T>& a, int cl, int nthreads, cudaStream_t st) {

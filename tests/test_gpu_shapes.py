@@ -324,3 +324,41 @@ def test_thousand_thread_stripe_sweeps_match_oracle(precision):
         assert np.array_equal(dx[0], dx[1])
     finally:
         ctx.destroy()
+
+
+@pytest.mark.parametrize("precision,stored", [(0, False), (0, True), (1, True), (1, False)])
+def test_two_buffer_forward_matches_three_buffer_forward_and_oracle(precision, stored):
+    """The stripe forward in its two-buffer form (x2 written over x(n), the
+    last stage reading x(n) from the stored trajectory level) gives the
+    three-buffer form's J and gradient bit for bit and matches the oracle, in
+    2-, 9- and 12-CTA clusters, with stage states stored or recomputed."""
+    wl, st, inp, w, ref = _problem("ragged")
+    bars = FP64_BARS if precision == 0 else FP32_BARS
+    ctx = _ctx(wl, st, inp, precision, ckpt_k=0)
+    nt_f = 512 if precision == 0 else 384
+    try:
+        for cl in (2, 9, 12):
+            out = []
+            for vf in (1, 2):
+                ctx.set_sweep_variant(vf, 1)
+                ctx.set_sweep_config((cl, nt_f), (cl, 256), stored)
+                assert ctx.sweep_kernels()["forward"] == (4 if vf == 2 else 1)
+                out.append(_check(ctx, w, ref, bars, ("2buf", precision, stored, cl, vf)))
+            assert np.array_equal(out[0][0], out[1][0]), (precision, stored, cl)
+            assert np.array_equal(out[0][1], out[1][1]), (precision, stored, cl)
+    finally:
+        ctx.destroy()
+
+
+def test_two_buffer_forward_falls_back_under_checkpoints():
+    """With k-step checkpoints not every level is stored, so forward variant 2
+    runs the three-buffer forward (kind 1) and still matches the oracle."""
+    wl, st, inp, w, ref = _problem("ragged")
+    ctx = _ctx(wl, st, inp, 0, ckpt_k=5)
+    try:
+        ctx.set_sweep_variant(2, 2)
+        ctx.set_sweep_config((4, 512), (4, 512), False)
+        assert ctx.sweep_kernels() == {"forward": 1, "adjoint": 3}
+        _check(ctx, w, ref, FP64_BARS, ("2buf-ckpt",))
+    finally:
+        ctx.destroy()
