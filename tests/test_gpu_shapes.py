@@ -1,17 +1,19 @@
-"""GPU parity in the launch shapes the big workloads run: 8- and 16-CTA
-clusters, 384 and 512 threads per CTA, stage states stored by the forward
-sweep or recomputed in the adjoint, and k-step checkpoints.  The batching and
-large workloads are too big for the oracle, so their shapes run here on
-workloads the oracle evaluates: every subdomain of the ragged workload
-(boxes of 20-22 rows, so a 16-CTA cluster gives stripes of one and two rows)
-and sampled subdomains of the medium workload at full size.
+"""GPU parity in the launch shapes and kernel forms the big workloads run:
+8-, 9-, 12- and 16-CTA clusters, 256 to 1024 threads per CTA, stage states
+stored by the forward sweep or recomputed in the adjoint, k-step checkpoints,
+the deep-halo FP32 sweeps, the two-buffer forward and the four-buffer
+adjoint.  The batching and large workloads are too big for the oracle, so
+their shapes run here on workloads the oracle evaluates: every subdomain of
+the ragged workload (boxes of 20-22 rows, so a 16-CTA cluster gives stripes
+of one and two rows) and sampled subdomains of the medium workload at full
+size.
 
 Bars: FP64 J within 1e-11 relative, grad J within 1e-9 relative (2-norm);
 FP32-state path J within 1e-5 relative and grad J within 2e-3 relative (the
 state arithmetic is FP32; the gradient of a functional evaluated in FP32
 carries its rounding).  The FP32 path's analysis RMSE must also stay within
-1 % of the FP64 oracle's analysis RMSE (spec gate), checked on the
-small workload through Algorithm 1 end to end.
+1 % of the FP64 oracle's analysis RMSE (the accuracy gate of the FP32-state
+path), checked on the small workload through Algorithm 1 end to end.
 """
 import numpy as np
 import pytest
@@ -124,7 +126,7 @@ def test_recomputed_and_checkpointed_adjoint_at_big_clusters(name, precision, ck
 
 
 def test_fp32_analysis_rmse_within_one_percent_of_fp64_oracle():
-    """North-star gate of the FP32-state path: Algorithm 1 end to end on the
+    """Accuracy gate of the FP32-state path: Algorithm 1 end to end on the
     small workload (batched device L-BFGS, Exchange, Gather); the analysis
     RMSE of h at t0 against the truth is within 1 % of that of the FP64
     oracle's own outer loop with the same settings, and both improve on the
