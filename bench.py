@@ -287,11 +287,22 @@ def _cpu_baseline_child(conn, wl_name, y, so, budget_s):
             if time.perf_counter() - t0 > budget_s:
                 break
         dt = time.perf_counter() - t0
-        conn.send({"value": pts / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+        cores = torch.get_num_threads()
+        # the same oracle on one thread: the first sampled subdomain
+        torch.set_num_threads(1)
+        lp = st.locals[0]
+        t1 = time.perf_counter()
+        lp.J_and_grad(torch.zeros(lp.nctrl, dtype=torch.float64), st.xb_traj, prev)
+        dt1 = time.perf_counter() - t1
+        pts1 = lp.sub.nx * lp.sub.ny * (lp.sub.b - lp.sub.a)
+        conn.send({"value": pts / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"J and grad J at w = 0 of {done} of the {n_all} subdomains (the first of "
                              f"the first time window, index order), {pts} pt-steps in {dt:.1f} s; "
                              f"FP64 PyTorch-CPU oracle, autograd adjoint; set up in {setup_s:.0f} s "
-                             f"beside the GPU legs, timed alone"})
+                             f"beside the GPU legs, timed alone",
+                   "single_thread": {"value": pts1 / dt1, "unit": UNIT, "cores": 1,
+                                     "sample": f"the first of those subdomains, {pts1} pt-steps in "
+                                               f"{dt1:.1f} s"}})
     except Exception as e:   # reported in the line, never fatal to the GPU measurement
         conn.send({"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                    "sample": f"failed: {type(e).__name__}: {e}"})
