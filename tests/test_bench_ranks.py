@@ -38,3 +38,29 @@ def test_replica_aggregation_world_size_2():
 def test_single_process_aggregation_is_identity():
     import bench
     assert bench.aggregate_ranks(3.0, 7.0, "cpu") == (3.0, 7.0)
+
+
+def test_cpu_baseline_leg_reports_all_core_and_single_thread_timings():
+    """The CPU oracle leg of bench.py (run here in a thread instead of a
+    spawned process) sets up its sample, waits for "go", then reports the
+    all-core rate and a single-thread rate of the same oracle."""
+    import multiprocessing
+    import threading
+    import numpy as np
+    import bench
+    import workloads
+    wl = workloads.preset("small")
+    inp = workloads.generate(wl)
+    so = np.asarray(wl.sigma_o)[inp["obs_var"]]
+    nthreads = torch.get_num_threads()   # the leg sets one thread for its second timing
+    parent, child = multiprocessing.Pipe()
+    th = threading.Thread(target=bench._cpu_baseline_child, args=(child, "small", np.zeros(len(so)), so, 1.0))
+    th.start()
+    tag, setup_s = parent.recv()
+    assert tag == "ready" and setup_s >= 0.0
+    parent.send("go")
+    res = parent.recv()
+    th.join()
+    torch.set_num_threads(nthreads)
+    assert res["kind"] == "oracle" and res["value"] > 0 and res["cores"] >= 1
+    assert res["single_thread"]["cores"] == 1 and res["single_thread"]["value"] > 0
