@@ -53,6 +53,10 @@ VALUES_PER_PTSTEP = {"forward": 3.0, "adjoint": 3.0}
 # adjoint loads them instead of recomputing two stages (2 RHS + 21 = 91 flops).
 FLOPS_STORED = {"forward": 141.0, "adjoint": 228.0}
 VALUES_STORED = {"forward": 9.0, "adjoint": 9.0}
+# With x1 alone stored (for a share f of the pt-steps) the adjoint skips the
+# first stage there (one RHS + 3 FMAs = 41 flops) and both sweeps move 3 more
+# values per pt-step.
+FLOPS_X1_STAGE = 41.0
 # FP64 on GB300: 2 FMA / clock / SM (the nominal 1.25 TFLOP/s over 152 SMs at
 # 2070 MHz); FP32: 128 FMA lanes / SM.
 N_SM = 152
@@ -421,9 +425,14 @@ def roofline_of(ctx, prec, reps=3):
     peaks, peaks_kind = measured_peaks()
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     tsize = 8 if prec == 0 else 4
-    stored = ctx.sweep_config()["stored_stages"]
-    fl = FLOPS_STORED if stored else FLOPS
-    vals = VALUES_STORED if stored else VALUES_PER_PTSTEP
+    cfg = ctx.sweep_config()
+    stored = cfg["stored_stages"]
+    fl = dict(FLOPS_STORED if stored else FLOPS)
+    vals = dict(VALUES_STORED if stored else VALUES_PER_PTSTEP)
+    x1 = 0.0 if stored else cfg["x1_stored"]["pt_step_share"]
+    if x1 > 0.0:
+        fl["adjoint"] -= FLOPS_X1_STAGE * x1
+        vals = {k: v + 3.0 * x1 for k, v in vals.items()}
     flops = fl[kern] * pts_eval / t_k
     bytes_ = vals[kern] * tsize * pts_eval / t_k
     hbm_peak = float(peaks["hbm_gbs"]) * 1e9

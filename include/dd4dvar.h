@@ -103,8 +103,12 @@ typedef struct {
  * loads them (three times the memory of the states alone; on GB300 this
  * trades FP64 arithmetic for otherwise idle HBM bandwidth) -- the stage buffer
  * is allocated only if it leaves 4 GB + 5 % of the device memory free, else
- * the adjoint recomputes the stages as with -1; -1 = store every
- * level, the adjoint recomputes the stage states; k > 0 = checkpointing:
+ * the first stage state alone is stored as with -3; -1 = store every
+ * level, the adjoint recomputes the stage states; -3 = store every level and
+ * the first RK3 stage state x1 of every step, for as many subdomains as fit
+ * (longest first, same 4 GB + 5 % reserve; dd4dv_stage1_stored reports
+ * them), whose adjoint then recomputes only x2 (the others recompute both);
+ * k > 0 = checkpointing:
  * evaluations store only the levels 0, k, 2k, ... and the adjoint
  * recomputes each k-step segment from its checkpoint before running back
  * through it (the exchange and dd4dv_trajectories still store every level);
@@ -404,10 +408,17 @@ dd4dv_status dd4dv_sweep_config(const dd4dv_ctx* ctx, int* shape, double* eval_m
 dd4dv_status dd4dv_set_sweep_config(dd4dv_ctx* ctx, const int* shape);
 
 /* Trajectory storage the evaluations use: *k = 0 stored stage states,
- * -1 stages recomputed, k > 0 checkpoints every k levels (ckpt_k of
- * dd4dv_decomp, or the choice made for ckpt_k = -2); eval_ms (may be NULL)
- * = the evaluation time measured for that choice (0 unless ckpt_k = -2). */
+ * -1 stages recomputed, -3 x1 stored for some or all subdomains, k > 0
+ * checkpoints every k levels (ckpt_k of dd4dv_decomp, or the choice made for
+ * ckpt_k = -2); eval_ms (may be NULL) = the evaluation time measured for that
+ * choice (0 unless ckpt_k = -2). */
 dd4dv_status dd4dv_checkpoint_interval(const dd4dv_ctx* ctx, int* k, double* eval_ms);
+
+/* Subdomains whose first RK3 stage state is stored (ckpt_k = -3, or 0 when
+ * both stage states do not fit), and their share of the pt-steps of an
+ * evaluation; 0 and 0.0 otherwise.  Either pointer may be NULL.  ESTATE
+ * before dd4dv_set_decomposition. */
+dd4dv_status dd4dv_stage1_stored(const dd4dv_ctx* ctx, int* n_subs, double* pt_step_share);
 
 /* Sweep kernels (FP32-state path).  The library has two forms of the forward
  * and adjoint sweeps.  The stripe sweeps exchange one halo row between the

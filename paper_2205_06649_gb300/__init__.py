@@ -209,8 +209,12 @@ class Context:
         kms = C.c_double()
         self._check(lib.dd4dv_checkpoint_interval(self._h, C.byref(k), C.byref(kms)))
         kinds = self.sweep_kernels()
+        n1 = C.c_int()
+        f1 = C.c_double()
+        self._check(lib.dd4dv_stage1_stored(self._h, C.byref(n1), C.byref(f1)))
         return {"forward": [int(sh[0]), int(sh[1])], "adjoint": [int(sh[2]), int(sh[3])],
                 "stored_stages": bool(sh[4]), "eval_ms": ms.value, "ckpt_k": k.value,
+                "x1_stored": {"subdomains": n1.value, "pt_step_share": f1.value},
                 "kernels": {"forward": KERNEL_NAMES.get(kinds["forward"], "none"),
                             "adjoint": KERNEL_NAMES.get(kinds["adjoint"], "none")}}
 

@@ -92,6 +92,7 @@ PROTOTYPES = {
     "dd4dv_tz_adjoint": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_double, _P, _P, _P, C.c_int]),
     "dd4dv_tz_eval": (C.c_int, [_CTX, C.c_int, C.c_int, C.c_double, _P, _P, _P, C.c_int]),
     "dd4dv_checkpoint_interval": (C.c_int, [_CTX, c_int_p, c_double_p]),
+    "dd4dv_stage1_stored": (C.c_int, [_CTX, c_int_p, c_double_p]),
     "dd4dv_local_solve": (C.c_int, [_CTX, C.POINTER(dd4dv_solver), C.POINTER(dd4dv_stats)]),
     "dd4dv_sweep_kernels": (C.c_int, [_CTX, _P]),
     "dd4dv_forward_noalloc": (C.c_int, [C.POINTER(dd4dv_model), _P, _P, C.c_void_p]),

@@ -83,6 +83,9 @@ struct dd4dv_ctx {
   int ckpt = 0;
   void* stg = nullptr;        // RK3 stage states (nullptr: the adjoint recomputes them)
   long long stg_elems = 0;
+  void* stg1 = nullptr;       // x1 alone for some subdomains (see stg1_off), when stg is absent
+  int stg1_subs = 0;          // subdomains with x1 stored
+  double stg1_frac = 0.0;     // their share of the pt-steps
   bool use_stg = false;
   void* tgt = nullptr;
   void* bnd = nullptr;
@@ -245,6 +248,7 @@ SweepArgs<T> sweep_args(dd4dv_ctx* ctx) {
   a.n_sub = ctx->n_sub;
   a.traj = static_cast<T*>(ctx->traj);
   a.stg = ctx->use_stg ? static_cast<T*>(ctx->stg) : nullptr;
+  a.stg1 = ctx->use_stg ? nullptr : static_cast<T*>(ctx->stg1);
   a.ckpt = ctx->ckpt;
   a.seg = static_cast<T*>(ctx->seg);
   a.tgt = static_cast<const T*>(ctx->tgt);
@@ -358,6 +362,7 @@ void forward_sweep(dd4dv_ctx* ctx, const int* active, int av, bool full = false)
   if (full) {
     a.ckpt = 0;
     a.stg = nullptr;
+    a.stg1 = nullptr;
   }
   a.R = ctx->R_f;
   a.variant = ctx->variant_f;
@@ -834,7 +839,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
       const int core = ctx->t_cuts[k + 1] - ctx->t_cuts[k];
       if (core < 2 * d.o_t + 1) fail(ctx, DD4DV_EINVAL, "time core block %d (%d) < 2*o_t+1", k, core);
     }
-  if (d.ckpt_k < -2) fail(ctx, DD4DV_EINVAL, "ckpt_k must be >= -2");
+  if (d.ckpt_k < -3) fail(ctx, DD4DV_EINVAL, "ckpt_k must be >= -3");
   // ckpt_k = -2: the segment buffers are sized for the largest interval tried
   const int seg_k = d.ckpt_k > 0 ? d.ckpt_k : (d.ckpt_k == -2 ? kTunedCkpt[2] : 0);
 
@@ -878,6 +883,7 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
         s.traj_off = trj;
         s.ptraj_off = ptrj;
         s.stg_off = stgl;
+        s.stg1_off = -1;
         stgl += (long long)L * 2 * 3 * s.ny * s.nxp;
         s.seg_off = segl;
         if (seg_k > 0) segl += (long long)(std::min(seg_k, std::max(L, 1)) + 1) * 3 * s.ny * s.nxp;
@@ -1148,6 +1154,34 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
       ctx->stg_elems = stgl;
       ctx->stg = dalloc<unsigned char>(ctx, std::max<long long>(1, stgl) * ctx->tsize, &L);
       ctx->use_stg = true;
+    }
+  }
+  // Where both stage states do not fit (ckpt_k = 0), or on request (ckpt_k =
+  // -3), the first stage state x1 alone is stored for as many subdomains as
+  // fit in the same reserve, longest first; their adjoint then recomputes only
+  // x2.  Results are the same either way.
+  ctx->stg1 = nullptr;
+  ctx->stg1_subs = 0;
+  ctx->stg1_frac = 0.0;
+  if (!ctx->stg && (d.ckpt_k == 0 || d.ckpt_k == -3)) {
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    const double reserve = 4.0 * (1ull << 30) + 0.05 * (double)total_b;
+    const double budget = ((double)free_b - reserve) / (double)ctx->tsize;
+    long long used = 0, pts_in = 0;
+    for (int idx : order) {
+      SubDesc& sd = subs[idx];
+      const long long need = (long long)(sd.b - sd.a) * 3 * sd.ny * sd.nxp;
+      if (need > 0 && (double)(used + need) <= budget) {
+        sd.stg1_off = used;
+        used += need;
+        pts_in += (long long)sd.nx * sd.ny * (sd.b - sd.a);
+        ++ctx->stg1_subs;
+      }
+    }
+    if (used > 0) {
+      ctx->stg1 = dalloc<unsigned char>(ctx, used * ctx->tsize, &L);
+      ctx->stg1_frac = pts > 0 ? (double)pts_in / (double)pts : 0.0;
     }
   }
   h2d(ctx, ctx->subs_d, subs.data(), subs.size() * sizeof(SubDesc));
@@ -2512,8 +2546,18 @@ dd4dv_status dd4dv_checkpoint_interval(const dd4dv_ctx* cctx, int* k, double* ev
   auto* ctx = const_cast<dd4dv_ctx*>(cctx);
   if (!ctx) return DD4DV_EINVAL;
   if (!ctx->has_dec) return DD4DV_ESTATE;
-  if (k) *k = ctx->use_stg ? 0 : (ctx->ckpt > 0 ? ctx->ckpt : -1);
+  if (k) *k = ctx->use_stg ? 0 : (ctx->ckpt > 0 ? ctx->ckpt : (ctx->stg1 ? -3 : -1));
   if (eval_ms) *eval_ms = ctx->ckpt_ms;
+  return DD4DV_OK;
+}
+
+dd4dv_status dd4dv_stage1_stored(const dd4dv_ctx* cctx, int* n_subs, double* pt_step_share) {
+  auto* ctx = const_cast<dd4dv_ctx*>(cctx);
+  if (!ctx) return DD4DV_EINVAL;
+  if (!ctx->has_dec) return DD4DV_ESTATE;
+  const bool on = ctx->stg1 && !ctx->use_stg;
+  if (n_subs) *n_subs = on ? ctx->stg1_subs : 0;
+  if (pt_step_share) *pt_step_share = on ? ctx->stg1_frac : 0.0;
   return DD4DV_OK;
 }
 

@@ -36,6 +36,7 @@ struct SubDesc {
   long long traj_off;         // trajectory offset (elements of T)
   long long ptraj_off;        // packed public trajectory offset (doubles, pitch nx)
   long long stg_off;          // stage-state offset (elements of T): [L][2][3][ny][nxp]
+  long long stg1_off;         // offset of x1 alone (elements of T): [L][3][ny][nxp]; -1: not stored
   long long seg_off;          // checkpoint-segment buffer offset (elements of T): [k+1][3][ny][nxp]
 };
 
@@ -63,6 +64,8 @@ struct SweepArgs {
   int n_sub;
   T* traj;
   T* stg;                     // RK3 stage states x1, x2 of every step, or nullptr (recompute)
+  T* stg1;                    // with stg == nullptr: x1 of every step of the subdomains whose
+                              // stg1_off >= 0 (x2 recomputed), or nullptr
   int ckpt;                   // 0: every level stored; k > 0: levels 0, k, 2k, ... stored and
                               // each k-step segment recomputed in the adjoint
   T* seg;                     // per-subdomain segment buffers for the recomputation

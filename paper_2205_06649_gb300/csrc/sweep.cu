@@ -1232,7 +1232,10 @@ __global__ void __launch_bounds__(max_threads_forward<T>(), min_blocks_forward<T
     const int n = g.a + l;
     stage_push<T, DEV>(cl, a, g, rs, S1, X, X, (T)0, (T)1, n + 1, n + 1, (T)1, (T)0);
     // stores read the buffer with another thread mapping: after the barrier
-    if (a.stg) store_block(g, S1, stage_ptr(a, g, l, 0));
+    if (a.stg)
+      store_block(g, S1, stage_ptr(a, g, l, 0));
+    else if (a.stg1 && g.d.stg1_off >= 0)
+      store_block(g, S1, a.stg1 + g.d.stg1_off + (size_t)l * 3 * g.ny * g.d.nxp);
     // after that barrier, level l's targets have been read and the ghost slot
     // of level n - 1 is free: prefetch the ghosts of the next step and the
     // targets of level l + 1, consumed after the third stage
@@ -1459,6 +1462,15 @@ __global__ void __launch_bounds__(kStripeAdjThreads, 1) adj_kernel(SweepArgs<T> 
       const T wA[3] = {(T)1, (T)1, (T)0.5};
       const T wB[3] = {(T)0, (T)0, (T)0.5};
       load_states<T, 3>(a, g, bufs, srcs, nA, nB, wA, wB);
+    } else if (!K && a.stg1 && g.d.stg1_off >= 0) {   // x(n) and the stored x1; x2 recomputed
+      T* bufs[2] = {X, X1};
+      const T* srcs[2] = {level_src(l), a.stg1 + g.d.stg1_off + (size_t)l * lvl_sz};
+      const int nA[2] = {n, n + 1};
+      const int nB[2] = {n, n + 1};
+      const T wA[2] = {(T)1, (T)1};
+      const T wB[2] = {(T)0, (T)0};
+      load_states<T, 2>(a, g, bufs, srcs, nA, nB, wA, wB);
+      stage_push<T, DEV>(cl, a, g, rs, X2, X, X1, (T)0.75, (T)0.25, n, n + 1, (T)0.5, (T)0.5);
     } else {       // recompute the stage states from x(n)
       load_state(a, g, X, level_src(l), n, n, (T)1, (T)0);
       stage_push<T, DEV>(cl, a, g, rs, X1, X, X, (T)0, (T)1, n + 1, n + 1, (T)1, (T)0);
@@ -2581,7 +2593,7 @@ int active_clusters_adjoint(int R, int W, int cl, int nthreads) {
 // the threads fit its register budget and its shared memory fits.
 template <typename T>
 bool deep_fits(const SweepArgs<T>& a, int cl, int nthreads, int nbuf) {
-  if (sizeof(T) != 4 || a.variant != 0 || cl < 1) return false;
+  if (sizeof(T) != 4 || a.variant != 0 || cl < 1 || a.stg1) return false;
   if (a.min_ny < kH * cl || nthreads > kDeepThreads || nthreads < 64 || nthreads % 32) return false;
   if ((long long)a.R * (a.W - 2) > (long long)kMaxP * nthreads) return false;
   return smem_deep(nbuf, a.R, a.W) <= kSmemOptinMax;

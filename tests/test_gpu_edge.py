@@ -51,7 +51,7 @@ def test_call_order_and_argument_errors():
     for kw in (dict(P1=2, P2=2, Q=2, o_lon=9, o_lat=2, o_t=2),     # core 16 < 2 o
                dict(P1=2, P2=2, Q=2, o_lon=0, o_lat=2, o_t=2),     # split without overlap
                dict(P1=2, P2=2, Q=2, o_lon=2, o_lat=2, o_t=4),     # time core 8 < 2 o_t + 1
-               dict(P1=2, P2=2, Q=2, o_lon=2, o_lat=2, o_t=2, ckpt_k=-3)):
+               dict(P1=2, P2=2, Q=2, o_lon=2, o_lat=2, o_t=2, ckpt_k=-4)):
         with pytest.raises(dd.DD4DVError) as e:
             ctx.set_decomposition(**kw)
         assert e.value.status == -1, kw

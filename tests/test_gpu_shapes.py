@@ -364,3 +364,39 @@ def test_two_buffer_forward_falls_back_under_checkpoints():
         _check(ctx, w, ref, FP64_BARS, ("2buf-ckpt",))
     finally:
         ctx.destroy()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_stored_first_stage_matches_recomputed_stages_and_oracle(precision):
+    """ckpt_k = -3: the forward stores x1 of every step (here for every
+    subdomain, which all fit) and the adjoint recomputes only x2.  J and the
+    gradient equal those of fully recomputed stages (ckpt_k = -1) bit for bit
+    and match the oracle, with the five- and four-buffer adjoint and the two-
+    and three-buffer forward, in 2- and 9-CTA clusters."""
+    wl, st, inp, w, ref = _problem("ragged")
+    bars = FP64_BARS if precision == 0 else FP32_BARS
+    nt_f = 512 if precision == 0 else 384
+    res = {}
+    for ck in (-1, -3):
+        ctx = _ctx(wl, st, inp, precision, ckpt_k=ck)
+        try:
+            cfg = ctx.sweep_config()
+            if ck == -3:
+                assert cfg["ckpt_k"] == -3, cfg
+                assert cfg["x1_stored"]["subdomains"] == ctx.n_sub
+                assert abs(cfg["x1_stored"]["pt_step_share"] - 1.0) < 1e-12
+            else:
+                assert cfg["x1_stored"]["subdomains"] == 0
+            for cl in (2, 9):
+                for vf, va in ((1, 1), (2, 2)):
+                    ctx.set_sweep_variant(vf, va)
+                    ctx.set_sweep_config((cl, nt_f), (cl, 512), False)
+                    res[(ck, cl, vf, va)] = _check(ctx, w, ref, bars, ("x1", precision, ck, cl, vf, va))
+        finally:
+            ctx.destroy()
+    for cl in (2, 9):
+        for vf, va in ((1, 1), (2, 2)):
+            J1, g1 = res[(-1, cl, vf, va)]
+            J3, g3 = res[(-3, cl, vf, va)]
+            assert np.array_equal(g1, g3), (precision, cl, vf, va)
+            assert np.array_equal(J1, J3), (precision, cl, vf, va)
