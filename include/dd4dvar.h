@@ -104,10 +104,11 @@ typedef struct {
  * trades FP64 arithmetic for otherwise idle HBM bandwidth) -- the stage buffer
  * is allocated only if it leaves 4 GB + 5 % of the device memory free, else
  * the first stage state alone is stored as with -3; -1 = store every
- * level, the adjoint recomputes the stage states; -3 = store every level and
- * the first RK3 stage state x1 of every step, for as many subdomains as fit
- * (longest first, same 4 GB + 5 % reserve; dd4dv_stage1_stored reports
- * them), whose adjoint then recomputes only x2 (the others recompute both);
+ * level, the adjoint recomputes the stage states; -3 (FP64 path; as -1 on
+ * the FP32-state path) = store every level and the first RK3 stage state x1
+ * of every step, for as many subdomains as fit (longest first, same 4 GB +
+ * 5 % reserve; dd4dv_stage1_stored reports them), whose adjoint then
+ * recomputes only x2 (the others recompute both);
  * k > 0 = checkpointing:
  * evaluations store only the levels 0, k, 2k, ... and the adjoint
  * recomputes each k-step segment from its checkpoint before running back

@@ -1156,14 +1156,16 @@ void build_decomposition(dd4dv_ctx* ctx, const dd4dv_decomp& d) {
       ctx->use_stg = true;
     }
   }
-  // Where both stage states do not fit (ckpt_k = 0), or on request (ckpt_k =
-  // -3), the first stage state x1 alone is stored for as many subdomains as
-  // fit in the same reserve, longest first; their adjoint then recomputes only
-  // x2.  Results are the same either way.
+  // FP64 path: where both stage states do not fit (ckpt_k = 0), or on
+  // request (ckpt_k = -3), the first stage state x1 alone is stored for as
+  // many subdomains as fit in the same reserve, longest first; their adjoint
+  // then recomputes only x2.  Results are the same either way.  (The FP32
+  // sweeps are compiled without this mode: the FP32 states are half the size
+  // and both stage states fit where x1 alone would be needed in FP64.)
   ctx->stg1 = nullptr;
   ctx->stg1_subs = 0;
   ctx->stg1_frac = 0.0;
-  if (!ctx->stg && (d.ckpt_k == 0 || d.ckpt_k == -3)) {
+  if (!f32 && !ctx->stg && (d.ckpt_k == 0 || d.ckpt_k == -3)) {
     size_t free_b = 0, total_b = 0;
     CK(cudaMemGetInfo(&free_b, &total_b));
     const double reserve = 4.0 * (1ull << 30) + 0.05 * (double)total_b;

@@ -1232,10 +1232,11 @@ __global__ void __launch_bounds__(max_threads_forward<T>(), min_blocks_forward<T
     const int n = g.a + l;
     stage_push<T, DEV>(cl, a, g, rs, S1, X, X, (T)0, (T)1, n + 1, n + 1, (T)1, (T)0);
     // stores read the buffer with another thread mapping: after the barrier
-    if (a.stg)
-      store_block(g, S1, stage_ptr(a, g, l, 0));
-    else if (a.stg1 && g.d.stg1_off >= 0)
-      store_block(g, S1, a.stg1 + g.d.stg1_off + (size_t)l * 3 * g.ny * g.d.nxp);
+    if (a.stg) store_block(g, S1, stage_ptr(a, g, l, 0));
+    if constexpr (sizeof(T) == 8) {   // x1 alone: FP64 path only
+      if (!a.stg && a.stg1 && g.d.stg1_off >= 0)
+        store_block(g, S1, a.stg1 + g.d.stg1_off + (size_t)l * 3 * g.ny * g.d.nxp);
+    }
     // after that barrier, level l's targets have been read and the ghost slot
     // of level n - 1 is free: prefetch the ghosts of the next step and the
     // targets of level l + 1, consumed after the third stage
@@ -1462,7 +1463,7 @@ __global__ void __launch_bounds__(kStripeAdjThreads, 1) adj_kernel(SweepArgs<T> 
       const T wA[3] = {(T)1, (T)1, (T)0.5};
       const T wB[3] = {(T)0, (T)0, (T)0.5};
       load_states<T, 3>(a, g, bufs, srcs, nA, nB, wA, wB);
-    } else if (!K && a.stg1 && g.d.stg1_off >= 0) {   // x(n) and the stored x1; x2 recomputed
+    } else if (sizeof(T) == 8 && !K && a.stg1 && g.d.stg1_off >= 0) {   // x(n) and the stored x1 (FP64)
       T* bufs[2] = {X, X1};
       const T* srcs[2] = {level_src(l), a.stg1 + g.d.stg1_off + (size_t)l * lvl_sz};
       const int nA[2] = {n, n + 1};
