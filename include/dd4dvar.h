@@ -437,7 +437,7 @@ dd4dv_status dd4dv_stage1_stored(const dd4dv_ctx* ctx, int* n_subs, double* pt_s
  * more CTAs per SM fit.
  * The stripe forward also has a two-buffer form: x2 is written over x(n)
  * and the last stage reads x(n) from the trajectory level stored the step
- * before (every level stored, ckpt_k 0 or -1), so two CTAs per SM fit where
+ * before (every level stored: ckpt_k 0, -1 or -3), so two CTAs per SM fit where
  * three buffers fit one; same values bit for bit.
  * forward: 0 = deep-halo sweep wherever it applies (default), 1 = stripe
  * sweep only, 2 = the two-buffer stripe forward where it applies (else as
